@@ -1,0 +1,81 @@
+"""Seeded synthetic RSKA problems (inputs only; no solver arithmetic here).
+
+Shared by the tests, the benchmark, the oracle side and the CUDA side, which
+otherwise share nothing.  The recipe follows the paper's Sec. 5 (Tondji &
+Lorenz, arXiv 2203.10838): A has i.i.d. N(0, 1) entries, the solution xhat has
+s nonzeros at positions drawn uniformly without replacement with N(0, 1)
+values, b = A xhat, and a noisy right-hand side adds a vector drawn uniformly
+on the sphere of radius ell * ||A xhat|| (the "relative noise level" ell of
+the noisy-case experiments).  Everything comes from numpy's PCG64 generator
+seeded by the caller.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Problem:
+    A: np.ndarray       # (m, lda) float32, row-major; columns >= n are padding (zeros)
+    b: np.ndarray       # (m,) float32 right-hand side handed to both sides
+    xhat: np.ndarray    # (n,) float64 planted sparse solution
+    n: int
+    b64: np.ndarray     # (m,) float64 right-hand side before rounding to float32
+
+    @property
+    def m(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def lda(self) -> int:
+        return self.A.shape[1]
+
+
+def round_up(v: int, k: int) -> int:
+    return ((v + k - 1) // k) * k
+
+
+def gaussian_problem(m: int, n: int, s: int, seed: int, noise: float = 0.0,
+                     lda: int | None = None, scale: float = 1.0) -> Problem:
+    """A ~ N(0, scale^2) i.i.d. (float32), s-sparse xhat, b = A xhat (+ noise).
+
+    ``lda`` defaults to n rounded up to a multiple of 4 (16-byte rows); padding
+    columns are zero.  ``noise`` is the relative level ell: b gets
+    ell * ||A xhat|| * g / ||g|| added with g ~ N(0, I_m).
+    """
+    if lda is None:
+        lda = round_up(n, 4)
+    rng = np.random.default_rng(seed)
+    A = np.zeros((m, lda), dtype=np.float32)
+    A[:, :n] = rng.standard_normal((m, n), dtype=np.float32)
+    if scale != 1.0:
+        A[:, :n] *= np.float32(scale)
+    xhat = np.zeros(n, dtype=np.float64)
+    s = min(s, n)
+    support = rng.choice(n, size=s, replace=False)
+    xhat[support] = rng.standard_normal(s)
+    b64 = A[:, :n].astype(np.float64) @ xhat
+    if noise > 0.0:
+        g = rng.standard_normal(m)
+        b64 = b64 + noise * np.linalg.norm(b64) * g / np.linalg.norm(g)
+    return Problem(A=A, b=b64.astype(np.float32), xhat=xhat, n=n, b64=b64)
+
+
+def batched_sizes(P: int, seed: int, m_lo: int = 200, m_hi: int = 4000):
+    """m_p log-uniform in [m_lo, m_hi], n_p = m_p/2 rounded to a multiple of 8."""
+    rng = np.random.default_rng(seed)
+    logm = rng.uniform(np.log(m_lo), np.log(m_hi), size=P)
+    m = np.clip(np.rint(np.exp(logm)).astype(np.int64), m_lo, m_hi)
+    n = np.maximum(8, np.rint(m / 2.0 / 8.0).astype(np.int64) * 8)
+    return m, n
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round float32 values to the nearest bfloat16 (ties to even), returned as
+    float32 holding exactly the bfloat16 value."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)

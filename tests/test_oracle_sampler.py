@@ -1,0 +1,195 @@
+"""Pins for the oracle's sampler: Philox4x32-10, row norms, alias table, draws.
+
+The paper (Algorithm 1; Sec. 5 variants v1/v2) fixes only the distribution
+p_i = ||a_i||^2 / ||A||_F^2 with replacement; the counter/key layout and the
+alias construction are this library's index contract.  These tests tie the
+oracle's implementation to things outside itself: an independent Philox4x32-10
+(Triton's, run in its CPU interpreter), exact probability bookkeeping of the
+alias table, closed-form norms and chi-square frequency tests.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from synth import gaussian_problem
+
+_TRITON_SCRIPT = r"""
+import json, os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def _k(out, ctr, seed, N: tl.constexpr):
+    offs = tl.arange(0, N)
+    c0 = tl.load(ctr + offs * 4 + 0)
+    c1 = tl.load(ctr + offs * 4 + 1)
+    c2 = tl.load(ctr + offs * 4 + 2)
+    c3 = tl.load(ctr + offs * 4 + 3)
+    a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
+    tl.store(out + offs * 4 + 0, a.to(tl.int32, bitcast=True))
+    tl.store(out + offs * 4 + 1, b.to(tl.int32, bitcast=True))
+    tl.store(out + offs * 4 + 2, c.to(tl.int32, bitcast=True))
+    tl.store(out + offs * 4 + 3, d.to(tl.int32, bitcast=True))
+
+req = json.loads(sys.stdin.read())
+res = []
+for seed, ctrs in req:
+    ctr = torch.tensor(np.array(ctrs, dtype=np.uint32).view(np.int32))
+    out = torch.zeros_like(ctr)
+    _k[(1,)](out, ctr, seed, N=len(ctrs) // 4)
+    res.append([int(v) & 0xFFFFFFFF for v in out.tolist()])
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_independent_implementation(orc):
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    seeds = [0, 1, 0xFFFFFFFF, 0x123456789ABCDEF0, int(rng.integers(0, 2**63))]
+    req = []
+    for seed in seeds:
+        ctrs = rng.integers(0, 2**32, size=(16, 4), dtype=np.uint64).astype(np.uint32)
+        ctrs[0] = 0
+        ctrs[1] = 0xFFFFFFFF
+        req.append([seed, [int(v) for v in ctrs.ravel()]])
+    proc = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(req),
+                          capture_output=True, text=True, timeout=600)
+    if proc.returncode != 0:
+        pytest.skip("Triton interpreter unavailable: " + proc.stderr[-300:])
+    got = json.loads(proc.stdout.strip().splitlines()[-1])
+    for (seed, ctrs), ref in zip(req, got):
+        key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+        ctrs = np.array(ctrs, dtype=np.uint32).reshape(-1, 4)
+        ref = np.array(ref, dtype=np.uint32).reshape(-1, 4)
+        for c, r in zip(ctrs, ref):
+            np.testing.assert_array_equal(orc.philox4x32_10(c, key), r)
+
+
+def test_philox_changes_with_every_word(orc):
+    base = orc.philox4x32_10([1, 2, 3, 4], [5, 6])
+    for pos in range(4):
+        c = [1, 2, 3, 4]
+        c[pos] ^= 1
+        assert not np.array_equal(orc.philox4x32_10(c, [5, 6]), base)
+    for pos in range(2):
+        k = [5, 6]
+        k[pos] ^= 1
+        assert not np.array_equal(orc.philox4x32_10([1, 2, 3, 4], k), base)
+
+
+def _bucket_probs(thr, alias):
+    """Exact probability that a draw lands on each row, from the table alone."""
+    m = thr.shape[0]
+    keep = thr.astype(np.float64) / 2.0**32
+    prob = np.zeros(m)
+    np.add.at(prob, np.arange(m), keep / m)
+    np.add.at(prob, alias.astype(np.int64), (1.0 - keep) / m)
+    return prob
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 7, 64, 1000])
+def test_alias_reconstructs_probabilities(orc, m):
+    rng = np.random.default_rng(m)
+    nu = rng.exponential(size=m) ** 3 + 1e-3
+    thr, alias = orc.alias_build(nu)
+    p = nu / nu.sum()
+    prob = _bucket_probs(thr, alias)
+    # each bucket's threshold is truncated to 2^-32; every row gets its own
+    # bucket plus the buckets aliased to it
+    counts = np.bincount(alias, minlength=m) + 1
+    np.testing.assert_array_less(np.abs(prob - p), counts * 2.0**-32 / m + 1e-13)
+    assert np.all((alias >= 0) & (alias < m))
+
+
+def test_alias_skewed_and_single_heavy_row(orc):
+    nu = np.array([1e6] + [1e-6] * 99)
+    thr, alias = orc.alias_build(nu)
+    prob = _bucket_probs(thr, alias)
+    p = nu / nu.sum()
+    np.testing.assert_allclose(prob, p, atol=101 * 2.0**-32)
+
+
+def test_alias_uniform_norms_are_all_full(orc):
+    thr, alias = orc.alias_build(np.full(37, 2.5))
+    assert np.all(thr == 0xFFFFFFFF)
+    np.testing.assert_array_equal(alias, np.arange(37))
+
+
+def test_alias_rejects_zero_and_nonfinite_rows(orc):
+    with pytest.raises(ValueError):
+        orc.alias_build(np.array([1.0, 0.0, 2.0]))
+    with pytest.raises(ValueError):
+        orc.alias_build(np.array([1.0, np.inf]))
+    with pytest.raises(ValueError):
+        orc.alias_build(np.array([1.0, np.nan]))
+
+
+def test_row_norms_closed_form(orc):
+    rng = np.random.default_rng(3)
+    A = rng.integers(-50, 51, size=(9, 77)).astype(np.float32)   # exact sums
+    np.testing.assert_array_equal(orc.row_norms(A), (A.astype(np.float64) ** 2).sum(axis=1))
+    B = rng.standard_normal((5, 1000)).astype(np.float32)
+    np.testing.assert_allclose(orc.row_norms(B), (B.astype(np.float64) ** 2).sum(axis=1),
+                               rtol=1e-14)
+    C = np.zeros((2, 3), np.float32)
+    C[0, 1] = 3.0
+    C[1, :] = [1.0, 2.0, 2.0]
+    np.testing.assert_array_equal(orc.row_norms(C), [9.0, 9.0])
+
+
+def test_draws_follow_row_norm_distribution(orc):
+    prob = gaussian_problem(50, 20, 3, seed=11)
+    A = prob.A.copy()
+    A[7] *= 4.0       # make the distribution visibly non-uniform
+    A[8] *= 0.1
+    nu = orc.row_norms(A)
+    thr, alias = orc.alias_build(nu)
+    draws = orc.sample(thr, alias, seed=123, eta=64, k0=0, K=4000).ravel()
+    counts = np.bincount(draws, minlength=50)
+    expected = nu / nu.sum() * draws.size
+    chi2, pval = stats.chisquare(counts, expected)
+    assert pval > 1e-4, (chi2, pval)
+    assert counts[7] > 5 * counts.mean()
+
+
+def test_uniform_table_draws_are_uniform(orc):
+    m = 4096
+    thr, alias = orc.alias_build(np.ones(m))
+    draws = orc.sample(thr, alias, seed=99, eta=256, k0=0, K=4096).ravel()
+    counts = np.bincount(draws, minlength=m)
+    chi2, pval = stats.chisquare(counts)
+    assert pval > 1e-4, (chi2, pval)
+
+
+def test_sample_is_a_pure_function_of_seed_and_iteration(orc):
+    thr, alias = orc.alias_build(np.arange(1, 31, dtype=np.float64))
+    full = orc.sample(thr, alias, seed=5, eta=7, k0=0, K=10)
+    part = orc.sample(thr, alias, seed=5, eta=7, k0=4, K=3)
+    np.testing.assert_array_equal(full[4:7], part)
+    other = orc.sample(thr, alias, seed=6, eta=7, k0=0, K=10)
+    assert not np.array_equal(full, other)
+    prob1 = orc.sample(thr, alias, seed=5, eta=7, k0=0, K=10, problem=1)
+    assert not np.array_equal(full, prob1)
+    # odd eta: the last slot of a pair uses words 0,1 only; eta+1 extends it
+    wider = orc.sample(thr, alias, seed=5, eta=8, k0=0, K=10)
+    np.testing.assert_array_equal(wider[:, :7], full)
+
+
+def test_sample_words_follow_contract(orc):
+    """Slot s of iteration k draws from Philox(key=seed, ctr=(k, 0, s/2, problem))."""
+    m = 13
+    thr, alias = orc.alias_build(np.linspace(1.0, 3.0, m))
+    seed, k, problem = 0x0123456789ABCDEF, 5, 3
+    got = orc.sample(thr, alias, seed=seed, eta=6, k0=k, K=1, problem=problem)[0]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for s in range(6):
+        u = orc.philox4x32_10([k, 0, s // 2, problem], key)
+        ub, ua = (u[0], u[1]) if s % 2 == 0 else (u[2], u[3])
+        c = (int(ub) * m) >> 32
+        want = c if int(ua) < int(thr[c]) else int(alias[c])
+        assert got[s] == want
