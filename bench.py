@@ -1,0 +1,408 @@
+"""Benchmark of the RSKA hot path on one GB300 (or N independent replicas).
+
+Workload (the paper's Sec. 5 recipe at scale): A 20000 x 10000 i.i.d. N(0,1)
+float32 (800 MB, larger than L2), xhat with 200 N(0,1) nonzeros, b = A xhat
+plus noise uniform on the sphere of radius 1% of ||A xhat||, lambda = 2,
+eta = 1024, t = alpha^*(eta) (Corollary 1, uniform weights, sigma_max from
+the Marchenko-Pastur edge).  One step = one solve from z = 0 for 300
+iterations (one persistent kernel launch, past the noise plateau).
+
+Metric: row-updates/s = eta * iterations / second (duplicates counted),
+whole job.  Also reported: the roofline of the persistent kernel against the
+measured HBM copy bandwidth, the end-to-end rate through the public API with
+host buffers, a naive per-iteration PyTorch RSKA on the same GPU, time to
+1e-6 relative error on the 1000 x 500 configuration, and the FP64 CPU oracle
+timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, S, ETA, LAM, NOISE, ITERS = 20000, 10000, 200, 1024, 2.0, 0.01, 300
+PSEED, SEED = 1001, 0
+WORKLOAD = "rska_single_20000x10000_eta1024"
+METRIC = "RSKA row-updates/s (20000x10000 Gaussian, eta=1024, t=alpha*)"
+UNIT = "row-updates/s"
+
+
+def alpha_star_mp(m, n, eta):
+    s2 = (np.sqrt(m) + np.sqrt(n)) ** 2
+    return float(eta / (1.0 + (eta - 1) * s2 / (m * n)))
+
+
+T_STEP = alpha_star_mp(M, N, ETA)
+
+
+def config_dict():
+    return {"workload": WORKLOAD, "m": M, "n": N, "nnz": S, "noise": NOISE, "lambda": LAM,
+            "eta": ETA, "t": round(T_STEP, 4), "iters_per_step": ITERS,
+            "l2": "inputs larger than L2 (A is 800 MB; rows are sampled at random)",
+            "parallelism": "replicas"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2203_10838_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the persistent kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "rska_persistent_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle as it stands
+# --------------------------------------------------------------------------
+def oracle_rate(prob, seconds=10.0, max_iters=300, chunk=5):
+    """Time the oracle on a bounded sample of the workload: iterations of the
+    same problem from z = 0 until `seconds` have passed."""
+    import oracle
+    A = prob.A[:, :N]
+    b = prob.b.astype(np.float64)
+    t0 = time.perf_counter()
+    nu = oracle.row_norms(A)
+    thr, alias = oracle.alias_build(nu)
+    setup_s = time.perf_counter() - t0
+    z = np.zeros(N)
+    done = 0
+    t0 = time.perf_counter()
+    while done < max_iters:
+        z = oracle.rska(A, b, LAM, ETA, T_STEP, SEED, chunk, k0=done, z0=z, tables=(nu, thr, alias))
+        done += chunk
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return ETA * done / el, done, el, setup_s
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from synth import gaussian_problem
+    prob = gaussian_problem(M, N, S, seed=PSEED, noise=NOISE)
+    per_step = []
+    total_iters = 0
+    for i in range(args.warmup + args.steps):
+        secs = args.ref_seconds if i >= args.warmup else min(1.0, args.ref_seconds)
+        rate, iters, el, _ = oracle_rate(prob, seconds=secs, max_iters=ITERS)
+        if i >= args.warmup:
+            per_step.append((rate, iters, el))
+            total_iters += iters
+    tot_time = sum(el for _, _, el in per_step)
+    value = ETA * total_iters / tot_time
+    sample = (f"{total_iters} iterations of the {M}x{N} eta={ETA} workload over {args.steps} "
+              f"steps (~{args.ref_seconds:.0f} s each, bounded sample of the {ITERS}-iteration "
+              f"step)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tot_time / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def naive_torch_rska(torch, A, b, tau, lam, t, eta, n):
+    """Plain per-iteration PyTorch RSKA (index_select + mv + where): the
+    'plain RSKA on the same GPU' comparator.  Not the product path."""
+    nu = (A[:, :n].double() ** 2).sum(1).float()
+    z = torch.zeros(n, device=A.device)
+    for k in range(tau.shape[0]):
+        x = torch.sign(z) * torch.clamp(z.abs() - lam, min=0.0)
+        rows = A.index_select(0, tau[k])[:, :n]
+        r = rows @ x - b.index_select(0, tau[k])
+        c = (t / eta) * r / nu.index_select(0, tau[k])
+        z = z - rows.t() @ c
+    return z
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2203_10838_gb300 import build
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2203_10838_gb300.rska import Solver
+    from synth import gaussian_problem
+
+    prob = gaussian_problem(M, N, S, seed=PSEED + rank, noise=NOISE)
+    A_host = torch.from_numpy(prob.A).pin_memory()
+    b_host = torch.from_numpy(prob.b).pin_memory()
+    A = A_host.to(dev)
+    b = b_host.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sol = Solver(A, b, LAM, ETA, T_STEP, SEED, n=N, stream=stream)
+
+    def step():
+        sol.reset()
+        sol.solve(ITERS)
+
+    # warm-up
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # timed region: per-launch events around the persistent kernel
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        sol.reset()
+        ev[i][0].record(stream)
+        sol.solve(ITERS)
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(bq) for a, bq in ev]
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    updates = ETA * ITERS * args.steps * world
+    value = updates / (total_ms / 1000.0)
+
+    # final accuracy of the timed solve (FP64 on the device)
+    xh = torch.from_numpy(prob.xhat.astype(np.float32)).to(dev)
+    rel_res, rel_err = sol.metrics(xh)
+
+    # roofline of the dominant kernel
+    hbm_peak, peak_kind = load_peaks()
+    alg_bytes = ITERS * ETA * (4.0 * N + 12.0) + 8.0 * N
+    avg_launch_s = statistics.mean(launch_ms) / 1000.0
+    achieved = alg_bytes / avg_launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": committed_traffic(),
+            "peak_kind": f"{peak_kind} (copy bandwidth)", "kernel": "rska_persistent_kernel",
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1000.0,
+            "grid": sol.query("grid"), "rows_resident": sol.query("rows_resident")}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    e2e_steps = 0 if args.skip_e2e else max(2, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    x_host = torch.empty(N, dtype=torch.float32).pin_memory()
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Ad = A_host.to(dev, non_blocking=True)
+        bd = b_host.to(dev, non_blocking=True)
+        with Solver(Ad, bd, LAM, ETA, T_STEP, SEED, n=N, stream=stream) as s2:
+            s2.solve(ITERS)
+            xd, _ = s2.get_x()
+            x_host.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    if e2e_steps:
+        e2e_s = (time.perf_counter() - e0) / e2e_steps
+        e2e = {"value": ETA * ITERS * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(A_host.numel() * 4 + b_host.numel() * 4),
+               "d2h_bytes_per_step": int(N * 4),
+               "includes": "H2D of A and b, setup (FP64 norms + alias table), solve, D2H of x"}
+
+    # plain per-iteration PyTorch RSKA on the same GPU (comparator)
+    plain = None
+    if not args.skip_plain:
+        K_plain = 50
+        tau = sol.get_indices(0, K_plain).long()
+        naive_torch_rska(torch, A, b, tau[:3], LAM, T_STEP, ETA, N)
+        torch.cuda.synchronize(dev)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        naive_torch_rska(torch, A, b, tau, LAM, T_STEP, ETA, N)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_rate = ETA * K_plain / (p0.elapsed_time(p1) / 1000.0)
+        plain = {"value": plain_rate, "unit": UNIT, "impl": "torch index_select+mv loop",
+                 "speedup_of_fused": (value / world) / plain_rate}
+
+    # time to 1e-6 relative error on the 1000 x 500 configuration
+    tta = None
+    if not args.skip_tta:
+        p1c = gaussian_problem(1000, 500, 25, seed=1000)
+        A1 = torch.from_numpy(p1c.A).to(dev)
+        b1 = torch.from_numpy(p1c.b).to(dev)
+        xh1 = torch.from_numpy(p1c.xhat.astype(np.float32)).to(dev)
+        t1 = alpha_star_mp(1000, 500, 10)
+        with Solver(A1, b1, 1.0, 10, t1, 0, n=500, stream=stream) as s1:
+            s1.solve_until(20000, 100, 1e-6, xhat=xh1)   # warm-up
+            s1.reset()
+            torch.cuda.synchronize(dev)
+            c0 = time.perf_counter()
+            iters, err = s1.solve_until(200000, 100, 1e-6, xhat=xh1)
+            tt_s = time.perf_counter() - c0
+        tta = {"config": "1000x500, 25 nnz, lambda=1, eta=10, t=alpha*", "tol": 1e-6,
+               "iterations": iters, "ms": tt_s * 1000.0, "rel_err": err,
+               "check_every": 100}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        rate, iters, el, _ = oracle_rate(prob, seconds=args.ref_seconds, max_iters=ITERS)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{iters} iterations of this workload from z=0 ({el:.1f} s, FP64, "
+                         "single thread)"}
+
+    sol.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup),
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": 2 * args.steps,
+                "accuracy": {"rel_residual": rel_res, "rel_error": rel_err,
+                             "after_iterations": ITERS},
+                "plain_rska_gpu": plain, "time_to_accuracy": tta}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ref-seconds", type=float, default=5.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-tta", action="store_true")
+    ap.add_argument("--mode", default="full", choices=["full", "kernel"],
+                    help="kernel: only the timed persistent-kernel steps (for profiling)")
+    ap.add_argument("--iters", type=int, default=None,
+                    help="iterations per step (default 300; profiling uses fewer)")
+    args = ap.parse_args()
+    global ITERS
+    if args.iters is not None:
+        ITERS = args.iters
+    if args.mode == "kernel":
+        args.skip_cpu = args.skip_plain = args.skip_tta = args.skip_e2e = True
+    else:
+        args.skip_e2e = False
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * rska.h -- C ABI of librska, a GB300 (sm_103a) implementation of randomized
+ * sparse Kaczmarz with averaging (RSKA), Tondji & Lorenz, "Faster Randomized
+ * Block Sparse Kaczmarz by Averaging" (arXiv 2203.10838).
+ *
+ * The method (eq. rska, Algorithm 1), with uniform weights w_i = t (variant
+ * v2 of Sec. 5 with alpha = t; t = 1 is variant v1):
+ *
+ *     tau_k    = eta row indices drawn i.i.d. with replacement,
+ *                P(i) = ||a_i||^2 / ||A||_F^2
+ *     x_k      = S_lambda(z_k),     S_lambda(v) = max(|v| - lambda, 0) sign(v)
+ *     z_{k+1}  = z_k - (t/eta) sum_{i in tau_k} (<a_i, x_k> - b_i)/||a_i||^2 a_i
+ *
+ * starting from z_0 = x_0 = 0 (z is the paper's x^*).  For consistent systems
+ * the iterates approach the solution of min lambda||x||_1 + 1/2||x||^2 subject
+ * to Ax = b (eq. RBPP).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named A, b, x_out, z_out, z_in, xhat and the table pointers are
+ *    DEVICE pointers (cudaMalloc'd or equivalent) unless a comment says HOST.
+ *  - A is row-major m x n with leading dimension lda (elements): lda >= n,
+ *    lda a multiple of 4 and A 16-byte aligned, so that every row starts on a
+ *    16-byte boundary.  Columns n..lda-1 are never used in arithmetic.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work is ordered on it; calls that return host
+ *    values synchronize it.
+ *  - Return value: RSKA_OK (0) or one of the RSKA_E* codes below.  A device
+ *    fault or watchdog timeout is sticky: every later call on the context
+ *    returns the same code until rska_reset() clears it (a CUDA error that
+ *    corrupted the CUDA context cannot be cleared).
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Index contract (bit-exact; the paper only fixes the distribution):
+ *  - nu_i = ||a_i||^2 in FP64, summed as 32 partial sums (partial L takes the
+ *    columns j = L mod 32 in ascending j) folded pairwise p_L + p_{L xor o}
+ *    for o = 16, 8, 4, 2, 1; the result is partial 0.
+ *  - Alias table (Walker/Vose) for p_i = nu_i / sum nu, built sequentially in
+ *    FP64: W = sum nu in ascending i; q_i = (nu_i m)/W; LIFO stacks "small"
+ *    (q < 1) and "large" filled in ascending i; each step pops l (small) and
+ *    g (large): thr[l] = trunc(q_l 2^32) (0 if q_l <= 0), alias[l] = g,
+ *    q_g = (q_g + q_l) - 1, g is pushed back to small if q_g < 1 else to
+ *    large; buckets left over get thr = 2^32-1 and alias = self.
+ *  - Slot s of iteration k: Philox4x32-10 with key (lo32(seed), hi32(seed))
+ *    and counter (lo32(k), hi32(k), s/2, problem); even s uses words 0 and 1,
+ *    odd s words 2 and 3.  Bucket c = (word_a * m) >> 32; the draw is c if
+ *    word_b < thr[c], else alias[c].  problem = 0 for a single system.
+ */
+#ifndef RSKA_H
+#define RSKA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSKA_OK 0
+#define RSKA_EINVAL 1        /* bad argument: size, pointer, alignment, parameter range */
+#define RSKA_EZEROROW 2      /* some row a_i is zero (Algorithm 1 requires a_i != 0) */
+#define RSKA_ENONFINITE 3    /* A or b holds Inf or NaN */
+#define RSKA_ENOMEM 4        /* device allocation failed */
+#define RSKA_ECUDA 5         /* a CUDA runtime call failed */
+#define RSKA_ETIMEOUT 6      /* a device-side wait exceeded its limit; kernel returned early */
+#define RSKA_EUNSUPPORTED 7  /* valid but outside this build's limits (e.g. n too large) */
+
+typedef struct rska_ctx rska_ctx;
+
+/*
+ * rska_setup -- validate the problem, compute FP64 row norms ||a_i||^2
+ * (Definition 1, matrix D), build the alias table for p_i (Sec. 5, v1/v2) and
+ * set z = 0, k = 0 (Algorithm 1, "starting points x_0 = x^*_0 = 0").
+ *   out     HOST pointer receiving the new context (set to NULL on failure).
+ *   A, b    device, borrowed: they must stay valid and unmodified until
+ *           rska_destroy.  A: m x n, leading dimension lda.  b: m floats.
+ *   lambda  >= 0, the shrinkage threshold of S_lambda.
+ *   eta     batch size |tau_k|, 1 <= eta <= 4096.
+ *   t       > 0, the uniform weight w_i = t (relaxation alpha of Sec. 4).
+ *   seed    Philox key of the index contract.
+ * Synchronizes `stream`.  Errors: EINVAL, EZEROROW, ENONFINITE, ENOMEM, ECUDA,
+ * EUNSUPPORTED (n above the kernel's column capacity).
+ */
+int rska_setup(rska_ctx **out, const float *A, int64_t m, int64_t n, int64_t lda,
+               const float *b, float lambda, int32_t eta, float t, uint64_t seed,
+               void *stream);
+
+/*
+ * rska_solve -- run K iterations of Algorithm 1 (k -> k + K) in one persistent
+ * kernel launch on the context's stream.  Asynchronous; K = 0 is a no-op.
+ * Errors: EINVAL (K < 0), a sticky code.
+ */
+int rska_solve(rska_ctx *ctx, int64_t K);
+
+/*
+ * rska_solve_until -- the stopping rule of Algorithm 1 ("until a stopping
+ * criterion is satisfied"): run chunks of `check_every` iterations; after each
+ * chunk compute in FP64 either the relative error ||x - xhat|| / ||xhat|| (xhat
+ * given, device, n floats) or the relative residual ||Ax - b|| / ||b|| (xhat
+ * NULL), and stop once it is <= tol or max_iters iterations have run.  All
+ * chunks are enqueued at once; a device flag makes the chunks after the stop
+ * return immediately.  Synchronizes.  iters_out (HOST, nullable) receives the
+ * iterations actually run by this call; metric_out (HOST, nullable) the last
+ * measured value.
+ */
+int rska_solve_until(rska_ctx *ctx, int64_t max_iters, int64_t check_every, double tol,
+                     const float *xhat, int64_t *iters_out, double *metric_out);
+
+/*
+ * rska_get_x -- copy x = S_lambda(z) (x_out) and/or z = x^* (z_out), n floats
+ * each (device pointers, either may be NULL).  Synchronizes.
+ */
+int rska_get_x(rska_ctx *ctx, float *x_out, float *z_out);
+
+/*
+ * rska_set_state -- restore a checkpoint: z <- z_in (device, n floats) and the
+ * iteration counter k <- k.  tau_k depends only on (seed, k), so a restored
+ * run continues the same index sequence.  Synchronizes.
+ */
+int rska_set_state(rska_ctx *ctx, const float *z_in, int64_t k);
+
+/* rska_iteration -- HOST: the iteration counter k (iterations applied so far). */
+int rska_iteration(rska_ctx *ctx, int64_t *k_out);
+
+/*
+ * rska_get_indices -- write tau_{k0} .. tau_{k0+K-1} (eta*K int32, row-major
+ * [k][slot]) to `out` (device) using the same device sampler as the solver.
+ * Synchronizes.
+ */
+int rska_get_indices(rska_ctx *ctx, int64_t k0, int64_t K, int32_t *out);
+
+/*
+ * rska_get_tables -- copy the FP64 row norms (m doubles), alias thresholds (m
+ * uint32) and aliases (m int32) to device buffers (each may be NULL).
+ */
+int rska_get_tables(rska_ctx *ctx, double *nu_out, uint32_t *thr_out, int32_t *alias_out);
+
+/*
+ * rska_metrics -- FP64 relative residual ||Ax - b|| / ||b|| and, when xhat
+ * (device, n floats) is given, relative error ||x - xhat|| / ||xhat|| of the
+ * current x = S_lambda(z) (Sec. 5 metrics).  HOST outputs; synchronizes.
+ * A zero denominator is replaced by 1e-30.
+ */
+int rska_metrics(rska_ctx *ctx, const float *xhat, double *rel_res, double *rel_err);
+
+/* rska_reset -- z = 0, k = 0 and clear a sticky error.  Synchronizes. */
+int rska_reset(rska_ctx *ctx);
+
+/* rska_destroy -- free the context's device memory (A and b are not touched). */
+int rska_destroy(rska_ctx *ctx);
+
+/*
+ * rska_query -- HOST: launch facts of the solver for this context:
+ *   what = 0: CTAs in the persistent grid      1: threads per CTA
+ *          2: rows of tau_k kept in shared memory per iteration
+ *          3: float4 columns owned by the widest CTA
+ *          4: dynamic shared memory bytes per CTA
+ */
+int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
+
+/*
+ * rska_set_option -- tuning knobs, applied from the next solve:
+ *   what = 0: CTAs in the persistent grid (0 = automatic)
+ *          1: watchdog limit of each device-side wait, in microseconds
+ *             (default 2,000,000)
+ */
+int rska_set_option(rska_ctx *ctx, int what, int64_t value);
+
+/* rska_strerror -- static English text for a return code. */
+const char *rska_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSKA_H */

@@ -1,0 +1,383 @@
+// rska_api.cu -- the C ABI of librska (declared in include/rska.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "rska_internal.h"
+
+using rska::Ctx;
+
+struct rska_ctx {
+  Ctx c;
+};
+
+namespace {
+
+int cuda_fail(Ctx* c, cudaError_t e) {
+  if (e == cudaSuccess) return RSKA_OK;
+  if (c) c->sticky = RSKA_ECUDA;
+  return (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+void free_all(Ctx* c) {
+  cudaFree(c->nu);
+  cudaFree(c->inv_nu);
+  cudaFree(c->thr);
+  cudaFree(c->alias);
+  cudaFree(c->z);
+  cudaFree(c->x);
+  cudaFree(c->racc);
+  cudaFree(c->bar);
+  cudaFree(c->status);
+  cudaFree(c->kdev);
+  cudaFree(c->stop);
+  cudaFree(c->macc);
+  cudaFree(c->scratch);
+  c->nu = nullptr;
+  c->inv_nu = nullptr;
+  c->thr = nullptr;
+  c->alias = nullptr;
+  c->z = c->x = c->racc = nullptr;
+  c->bar = nullptr;
+  c->status = nullptr;
+  c->kdev = nullptr;
+  c->stop = nullptr;
+  c->macc = nullptr;
+  c->scratch = nullptr;
+}
+
+int64_t n_padded(int64_t n) { return ((n + 3) / 4) * 4; }
+
+// Read the device status word; map it to a return code and make it sticky.
+int check_status(Ctx* c) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  if (st != 0) c->sticky = st;
+  return st;
+}
+
+int plan(Ctx* c) {
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  if (!rska::plan_solve(c->n, c->eta, c->num_sms, c->grid_override, (size_t)optin, &c->geom))
+    return RSKA_EUNSUPPORTED;
+  return RSKA_OK;
+}
+
+rska::SolveArgs solve_args(Ctx* c, int64_t K, const int* stop) {
+  rska::SolveArgs a;
+  a.A = c->A;
+  a.lda = c->lda;
+  a.m = c->m;
+  a.n = c->n;
+  a.b = c->b;
+  a.inv_nu = c->inv_nu;
+  a.thr = c->thr;
+  a.alias = c->alias;
+  a.lambda = c->lambda;
+  a.coef = c->t / (float)c->eta;
+  a.eta = c->eta;
+  a.seed = c->seed;
+  a.problem = 0;
+  a.z = c->z;
+  a.x = c->x;
+  a.racc = c->racc;
+  a.bar = c->bar;
+  a.status = c->status;
+  a.kdev = c->kdev;
+  a.stop = stop;
+  a.K = K;
+  a.limit_ns = c->limit_ns;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rska_strerror(int code) {
+  switch (code) {
+    case RSKA_OK: return "ok";
+    case RSKA_EINVAL: return "invalid argument";
+    case RSKA_EZEROROW: return "matrix has a zero row";
+    case RSKA_ENONFINITE: return "matrix or right-hand side holds Inf or NaN";
+    case RSKA_ENOMEM: return "device allocation failed";
+    case RSKA_ECUDA: return "CUDA runtime error";
+    case RSKA_ETIMEOUT: return "device-side wait timed out";
+    case RSKA_EUNSUPPORTED: return "problem outside this build's limits";
+    default: return "unknown error";
+  }
+}
+
+int rska_setup(rska_ctx** out, const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
+               float lambda, int32_t eta, float t, uint64_t seed, void* stream) {
+  if (out == nullptr) return RSKA_EINVAL;
+  *out = nullptr;
+  if (A == nullptr || b == nullptr || m < 1 || n < 1 || lda < n || (lda % 4) != 0 ||
+      (reinterpret_cast<uintptr_t>(A) % 16) != 0 || m > 0x7fffffffLL || eta < 1 ||
+      eta > rska::kMaxEta || !(lambda >= 0.f) || !std::isfinite(lambda) || !(t > 0.f) ||
+      !std::isfinite(t))
+    return RSKA_EINVAL;
+  rska_ctx* h = new (std::nothrow) rska_ctx;
+  if (!h) return RSKA_ENOMEM;
+  Ctx* c = &h->c;
+  c->A = A;
+  c->b = b;
+  c->m = m;
+  c->n = n;
+  c->lda = lda;
+  c->lambda = lambda;
+  c->t = t;
+  c->eta = eta;
+  c->seed = seed;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return RSKA_ECUDA;
+  }
+  int rc = plan(c);
+  if (rc != RSKA_OK) {
+    delete h;
+    return rc;
+  }
+  const int64_t np = n_padded(n);
+  if ((e = dalloc(&c->nu, m)) != cudaSuccess || (e = dalloc(&c->inv_nu, m)) != cudaSuccess ||
+      (e = dalloc(&c->thr, m)) != cudaSuccess || (e = dalloc(&c->alias, m)) != cudaSuccess ||
+      (e = dalloc(&c->z, np)) != cudaSuccess || (e = dalloc(&c->x, np)) != cudaSuccess ||
+      (e = dalloc(&c->racc, 3 * (size_t)eta)) != cudaSuccess ||
+      (e = dalloc(&c->bar, 1)) != cudaSuccess || (e = dalloc(&c->status, 1)) != cudaSuccess ||
+      (e = dalloc(&c->kdev, 1)) != cudaSuccess || (e = dalloc(&c->stop, 1)) != cudaSuccess ||
+      (e = dalloc(&c->macc, 8)) != cudaSuccess ||
+      (e = cudaMalloc(&c->scratch, (size_t)m * (sizeof(double) + sizeof(int32_t)))) !=
+          cudaSuccess) {
+    free_all(c);
+    delete h;
+    return (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+  }
+  cudaStream_t s = c->stream;
+  e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->kdev, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stop, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->macc, 0, 8 * sizeof(double), s);
+  if (e == cudaSuccess) e = rska::launch_fill_shrink(c->z, c->x, nullptr, n, np, lambda, s);
+  if (e == cudaSuccess)
+    e = rska::launch_row_norms(A, m, n, lda, b, c->nu, c->inv_nu, c->status, s);
+  double* q = static_cast<double*>(c->scratch);
+  int32_t* stk = reinterpret_cast<int32_t*>(q + m);
+  if (e == cudaSuccess)
+    e = rska::launch_alias_build(c->nu, m, c->thr, c->alias, q, stk, c->status, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete h;
+    return RSKA_ECUDA;
+  }
+  rc = check_status(c);
+  if (rc != RSKA_OK) {
+    free_all(c);
+    delete h;
+    return rc;
+  }
+  cudaFree(c->scratch);
+  c->scratch = nullptr;
+  *out = h;
+  return RSKA_OK;
+}
+
+int rska_solve(rska_ctx* h, int64_t K) {
+  if (!h || K < 0) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky) return c->sticky;
+  if (K == 0) return RSKA_OK;
+  rska::SolveArgs a = solve_args(c, K, nullptr);
+  cudaError_t e = rska::launch_solve(a, c->geom, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  c->k_host += K;
+  return RSKA_OK;
+}
+
+int rska_solve_until(rska_ctx* h, int64_t max_iters, int64_t check_every, double tol,
+                     const float* xhat, int64_t* iters_out, double* metric_out) {
+  if (!h || max_iters < 0 || check_every < 1) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky) return c->sticky;
+  cudaStream_t s = c->stream;
+  const int64_t k_start = c->k_host;
+  cudaError_t e = cudaMemsetAsync(c->stop, 0, sizeof(int), s);
+  int64_t* k_stop = reinterpret_cast<int64_t*>(c->macc + 6);
+  if (e == cudaSuccess) e = cudaMemsetAsync(k_stop, 0xff, sizeof(int64_t), s);
+  for (int64_t done = 0; e == cudaSuccess && done < max_iters; done += check_every) {
+    const int64_t K = (max_iters - done < check_every) ? (max_iters - done) : check_every;
+    rska::SolveArgs a = solve_args(c, K, c->stop);
+    e = rska::launch_solve(a, c->geom, s);
+    if (e == cudaSuccess)
+      e = rska::launch_metrics(c->A, c->m, c->n, c->lda, c->b, c->z, c->lambda, xhat, c->macc,
+                               c->stop, s);
+    if (e == cudaSuccess)
+      e = rska::launch_metrics_finish(c->macc, xhat != nullptr, tol, c->stop, k_stop, c->kdev, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  double res[2];
+  int64_t kd = 0;
+  e = cudaMemcpyAsync(res, c->macc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&kd, c->kdev, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  int rc = check_status(c);
+  c->k_host = kd;
+  if (iters_out) *iters_out = kd - k_start;
+  if (metric_out) *metric_out = xhat ? res[1] : res[0];
+  return rc;
+}
+
+int rska_get_x(rska_ctx* h, float* x_out, float* z_out) {
+  if (!h) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky) return c->sticky;
+  cudaError_t e = cudaSuccess;
+  if (x_out)
+    e = cudaMemcpyAsync(x_out, c->x, sizeof(float) * c->n, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && z_out)
+    e = cudaMemcpyAsync(z_out, c->z, sizeof(float) * c->n, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  return check_status(c);
+}
+
+int rska_set_state(rska_ctx* h, const float* z_in, int64_t k) {
+  if (!h || k < 0) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky) return c->sticky;
+  cudaError_t e = rska::launch_fill_shrink(c->z, c->x, z_in, c->n, n_padded(c->n), c->lambda,
+                                           c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->kdev, &k, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  c->k_host = k;
+  return RSKA_OK;
+}
+
+int rska_iteration(rska_ctx* h, int64_t* k_out) {
+  if (!h || !k_out) return RSKA_EINVAL;
+  *k_out = h->c.k_host;
+  return RSKA_OK;
+}
+
+int rska_get_indices(rska_ctx* h, int64_t k0, int64_t K, int32_t* out) {
+  if (!h || k0 < 0 || K < 0 || (K > 0 && !out)) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  cudaError_t e = rska::launch_indices(c->thr, c->alias, c->m, c->seed, 0, k0, K, c->eta, out,
+                                       c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_fail(c, e);
+}
+
+int rska_get_tables(rska_ctx* h, double* nu_out, uint32_t* thr_out, int32_t* alias_out) {
+  if (!h) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  cudaError_t e = cudaSuccess;
+  if (nu_out)
+    e = cudaMemcpyAsync(nu_out, c->nu, sizeof(double) * c->m, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && thr_out)
+    e = cudaMemcpyAsync(thr_out, c->thr, sizeof(uint32_t) * c->m, cudaMemcpyDeviceToDevice,
+                        c->stream);
+  if (e == cudaSuccess && alias_out)
+    e = cudaMemcpyAsync(alias_out, c->alias, sizeof(int32_t) * c->m, cudaMemcpyDeviceToDevice,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_fail(c, e);
+}
+
+int rska_metrics(rska_ctx* h, const float* xhat, double* rel_res, double* rel_err) {
+  if (!h) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky) return c->sticky;
+  cudaError_t e = rska::launch_metrics(c->A, c->m, c->n, c->lda, c->b, c->z, c->lambda, xhat,
+                                       c->macc, nullptr, c->stream);
+  if (e == cudaSuccess)
+    e = rska::launch_metrics_finish(c->macc, 0, -1.0, nullptr, nullptr, c->kdev, c->stream);
+  double res[2];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(res, c->macc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  if (rel_res) *rel_res = res[0];
+  if (rel_err && xhat) *rel_err = res[1];
+  return check_status(c);
+}
+
+int rska_reset(rska_ctx* h) {
+  if (!h) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky == RSKA_ECUDA) return RSKA_ECUDA;
+  cudaStream_t s = c->stream;
+  cudaError_t e = rska::launch_fill_shrink(c->z, c->x, nullptr, c->n, n_padded(c->n), c->lambda, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->kdev, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stop, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  c->k_host = 0;
+  c->sticky = RSKA_OK;
+  return RSKA_OK;
+}
+
+int rska_destroy(rska_ctx* h) {
+  if (!h) return RSKA_EINVAL;
+  cudaStreamSynchronize(h->c.stream);
+  free_all(&h->c);
+  delete h;
+  return RSKA_OK;
+}
+
+int rska_query(rska_ctx* h, int what, int64_t* value_out) {
+  if (!h || !value_out) return RSKA_EINVAL;
+  const rska::SolveGeometry& g = h->c.geom;
+  switch (what) {
+    case 0: *value_out = g.grid; return RSKA_OK;
+    case 1: *value_out = rska::kSolveThreads; return RSKA_OK;
+    case 2: *value_out = g.rows_res; return RSKA_OK;
+    case 3: *value_out = g.w4max; return RSKA_OK;
+    case 4: *value_out = (int64_t)g.smem; return RSKA_OK;
+    default: return RSKA_EINVAL;
+  }
+}
+
+int rska_set_option(rska_ctx* h, int what, int64_t value) {
+  if (!h) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  switch (what) {
+    case 0: {
+      if (value < 0 || value > c->num_sms) return RSKA_EINVAL;
+      const int old = c->grid_override;
+      c->grid_override = (int)value;
+      int rc = plan(c);
+      if (rc != RSKA_OK) {
+        c->grid_override = old;
+        plan(c);
+      }
+      return rc;
+    }
+    case 1:
+      if (value < 1) return RSKA_EINVAL;
+      c->limit_ns = (uint64_t)value * 1000ull;
+      return RSKA_OK;
+    default:
+      return RSKA_EINVAL;
+  }
+}
+
+}  // extern "C"

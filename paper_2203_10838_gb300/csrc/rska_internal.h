@@ -1,0 +1,101 @@
+// rska_internal.h -- host-side context and kernel launchers of librska.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rska.h"
+
+namespace rska {
+
+constexpr int kSolveThreads = 512;      // threads per CTA of the persistent solver
+constexpr int kMaxEta = 4096;           // largest batch size eta
+constexpr int kMaxColsPerLane = 8;      // float4 columns per lane in the dot phase
+
+// Launch geometry of the persistent single-system solver.
+struct SolveGeometry {
+  int grid = 0;          // CTAs (one per SM at most; all co-resident)
+  int w4max = 0;         // float4 columns of the widest CTA
+  int cpl = 1;           // float4 columns per lane in the dot phase (1, 2, 4, 8)
+  int rows_res = 0;      // rows of tau_k kept in shared memory
+  size_t smem = 0;       // dynamic shared memory per CTA
+};
+
+struct SolveArgs {
+  const float* A;
+  int64_t lda;
+  int64_t m, n;
+  const float* b;
+  const float* inv_nu;         // 1/||a_i||^2 in FP32 (from the FP64 norms)
+  const uint32_t* thr;
+  const int32_t* alias;
+  float lambda;
+  float coef;                  // t / eta
+  int32_t eta;
+  uint64_t seed;
+  uint32_t problem;
+  float* z;                    // x^*, n floats (padded to a multiple of 4)
+  float* x;                    // S_lambda(z), n floats (padded)
+  float* racc;                 // 3 * eta partial-dot accumulators
+  unsigned long long* bar;     // grid barrier arrival counter
+  int* status;
+  int64_t* kdev;               // iteration counter
+  const int* stop;             // nullable: skip the launch when *stop != 0
+  int64_t K;
+  uint64_t limit_ns;
+};
+
+struct Ctx {
+  // problem (borrowed)
+  const float* A = nullptr;
+  const float* b = nullptr;
+  int64_t m = 0, n = 0, lda = 0;
+  float lambda = 0.f, t = 1.f;
+  int32_t eta = 1;
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  // owned device memory
+  double* nu = nullptr;
+  float* inv_nu = nullptr;
+  uint32_t* thr = nullptr;
+  int32_t* alias = nullptr;
+  float* z = nullptr;
+  float* x = nullptr;
+  float* racc = nullptr;
+  unsigned long long* bar = nullptr;
+  int* status = nullptr;
+  int64_t* kdev = nullptr;
+  int* stop = nullptr;
+  double* macc = nullptr;      // metric accumulators and results
+  void* scratch = nullptr;     // alias-build scratch (freed after setup)
+  // host mirrors
+  int64_t k_host = 0;
+  int sticky = RSKA_OK;
+  int grid_override = 0;
+  uint64_t limit_ns = 2000000000ull;
+  SolveGeometry geom;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_row_norms(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
+                             double* nu, float* inv_nu, int* status, cudaStream_t s);
+cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,
+                               double* q_scratch, int32_t* stack_scratch, int* status,
+                               cudaStream_t s);
+cudaError_t launch_indices(const uint32_t* thr, const int32_t* alias, int64_t m, uint64_t seed,
+                           uint32_t problem, int64_t k0, int64_t K, int32_t eta, int32_t* out,
+                           cudaStream_t s);
+bool plan_solve(int64_t n, int32_t eta, int num_sms, int grid_override, size_t smem_optin,
+                SolveGeometry* g);
+cudaError_t launch_solve(const SolveArgs& a, const SolveGeometry& g, cudaStream_t s);
+cudaError_t launch_metrics(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
+                           const float* z, float lambda, const float* xhat, double* acc,
+                           const int* stop, cudaStream_t s);
+cudaError_t launch_metrics_finish(double* acc, int use_err, double tol, int* stop,
+                                  int64_t* iters_at_stop, const int64_t* kdev, cudaStream_t s);
+cudaError_t launch_fill_shrink(float* z, float* x, const float* z_in, int64_t n, int64_t n_pad,
+                               float lambda, cudaStream_t s);
+
+}  // namespace rska

@@ -1,0 +1,176 @@
+// rska_setup.cu -- one-time setup kernels: FP64 row norms ||a_i||^2
+// (Definition 1, matrix D), the alias table for p_i = ||a_i||^2/||A||_F^2
+// (Sec. 5, variants v1/v2), index retrieval, and state fill.
+#include "rska_device.cuh"
+#include "rska_internal.h"
+
+namespace rska {
+
+// One warp per row.  Lane L sums a_ij^2 for j = L mod 32 in ascending j (the
+// squares of FP32 values are exact in FP64), then the 32 partials are folded
+// pairwise with xor offsets 16, 8, 4, 2, 1; the value lands in every lane.
+// Flags a zero row (Algorithm 1 requires a_i != 0) and non-finite A or b.
+__global__ void row_norms_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                 const float* __restrict__ b, double* __restrict__ nu,
+                                 float* __restrict__ inv_nu, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < m; i += nwarps) {
+    const float* row = A + i * lda;
+    double p = 0.0;
+    bool finite = true;
+    for (int64_t j = lane; j < n; j += 32) {
+      const float a = __ldg(row + j);
+      finite = finite && isfinite(a);
+      const double ad = (double)a;
+      p = __dadd_rn(p, __dmul_rn(ad, ad));
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+    finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) {
+      const float bi = __ldg(b + i);
+      if (!finite || !isfinite(bi) || !isfinite(p)) {
+        atomicCAS(status, kStatusOk, kStatusNonFinite);
+      } else if (p == 0.0) {
+        atomicCAS(status, kStatusOk, kStatusZeroRow);
+      }
+      nu[i] = p;
+      inv_nu[i] = (p > 0.0) ? (float)__ddiv_rn(1.0, p) : 0.0f;
+    }
+  }
+}
+
+// Sequential Vose construction in FP64 by one thread (the canonical order of
+// the index contract).  `stk` holds both LIFO stacks: "small" grows up from
+// index 0, "large" grows down from index m-1; together they never hold more
+// than m entries.
+__device__ void alias_build_one(const double* __restrict__ nu, int64_t m, uint32_t* thr,
+                                int32_t* alias, double* q, int32_t* stk) {
+  double W = 0.0;
+  for (int64_t i = 0; i < m; ++i) W = __dadd_rn(W, nu[i]);
+  int64_t ns = 0, nl = 0;
+  const double md = (double)m;
+  for (int64_t i = 0; i < m; ++i) {
+    const double qi = __ddiv_rn(__dmul_rn(nu[i], md), W);
+    q[i] = qi;
+    if (qi < 1.0) {
+      stk[ns++] = (int32_t)i;
+    } else {
+      stk[m - 1 - nl] = (int32_t)i;
+      ++nl;
+    }
+  }
+  while (ns > 0 && nl > 0) {
+    const int32_t l = stk[--ns];
+    --nl;
+    const int32_t g = stk[m - 1 - nl];
+    const double ql = q[l];
+    const double scaled = __dmul_rn(ql, 4294967296.0);
+    uint32_t t;
+    if (ql <= 0.0) {
+      t = 0u;
+    } else if (scaled >= 4294967295.0) {
+      t = 4294967295u;
+    } else {
+      t = __double2uint_rz(scaled);
+    }
+    thr[l] = t;
+    alias[l] = g;
+    const double qg = __dsub_rn(__dadd_rn(q[g], ql), 1.0);
+    q[g] = qg;
+    if (qg < 1.0) {
+      stk[ns++] = g;
+    } else {
+      stk[m - 1 - nl] = g;
+      ++nl;
+    }
+  }
+  for (int64_t s = 0; s < ns; ++s) {
+    const int32_t l = stk[s];
+    thr[l] = 4294967295u;
+    alias[l] = l;
+  }
+  for (int64_t s = 0; s < nl; ++s) {
+    const int32_t g = stk[m - 1 - s];
+    thr[g] = 4294967295u;
+    alias[g] = g;
+  }
+}
+
+__global__ void alias_build_kernel(const double* __restrict__ nu, int64_t m, uint32_t* thr,
+                                   int32_t* alias, double* q, int32_t* stk, const int* status) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (*status != kStatusOk) return;
+  alias_build_one(nu, m, thr, alias, q, stk);
+}
+
+__global__ void indices_kernel(const uint32_t* __restrict__ thr, const int32_t* __restrict__ alias,
+                               uint32_t m, uint64_t seed, uint32_t problem, int64_t k0, int64_t K,
+                               int32_t eta, int32_t* __restrict__ out) {
+  const int64_t npairs = (eta + 1) / 2;
+  const int64_t total = K * npairs;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kk = e / npairs;
+    const uint32_t q = (uint32_t)(e % npairs);
+    int32_t i0, i1;
+    draw_pair(seed, k0 + kk, q, problem, thr, alias, m, &i0, &i1);
+    int32_t* o = out + kk * eta;
+    o[2 * q] = i0;
+    if (2 * q + 1 < (uint32_t)eta) o[2 * q + 1] = i1;
+  }
+}
+
+// z <- z_in (or 0), x <- S_lambda(z); entries n .. n_pad-1 are zero.
+__global__ void fill_shrink_kernel(float* __restrict__ z, float* __restrict__ x,
+                                   const float* __restrict__ z_in, int64_t n, int64_t n_pad,
+                                   float lambda) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pad;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const float v = (j < n && z_in != nullptr) ? z_in[j] : 0.0f;
+    z[j] = v;
+    x[j] = soft_shrink(v, lambda);
+  }
+}
+
+cudaError_t launch_row_norms(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
+                             double* nu, float* inv_nu, int* status, cudaStream_t s) {
+  const int threads = 256;
+  int64_t blocks = (m + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  row_norms_kernel<<<(unsigned)blocks, threads, 0, s>>>(A, m, n, lda, b, nu, inv_nu, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,
+                               double* q_scratch, int32_t* stack_scratch, int* status,
+                               cudaStream_t s) {
+  alias_build_kernel<<<1, 32, 0, s>>>(nu, m, thr, alias, q_scratch, stack_scratch, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_indices(const uint32_t* thr, const int32_t* alias, int64_t m, uint64_t seed,
+                           uint32_t problem, int64_t k0, int64_t K, int32_t eta, int32_t* out,
+                           cudaStream_t s) {
+  const int64_t total = K * ((eta + 1) / 2);
+  if (total <= 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  indices_kernel<<<(unsigned)blocks, 256, 0, s>>>(thr, alias, (uint32_t)m, seed, problem, k0, K,
+                                                   eta, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_shrink(float* z, float* x, const float* z_in, int64_t n, int64_t n_pad,
+                               float lambda, cudaStream_t s) {
+  int64_t blocks = (n_pad + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  fill_shrink_kernel<<<(unsigned)blocks, 256, 0, s>>>(z, x, z_in, n, n_pad, lambda);
+  return cudaGetLastError();
+}
+
+}  // namespace rska

@@ -1,0 +1,152 @@
+"""Thin Python binding of the librska C ABI (include/rska.h) over torch tensors.
+
+Argument marshalling only: torch provides device memory and the CUDA stream;
+every step of RSKA (eq. rska, Algorithm 1 of Tondji & Lorenz, arXiv
+2203.10838) runs in librska's kernels.  Names mirror the C entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib import check, lib
+
+QUERY = {"grid": 0, "threads": 1, "rows_resident": 2, "w4max": 3, "smem": 4}
+OPTION = {"grid": 0, "watchdog_us": 1}
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("librska takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One RSKA problem: rska_setup on construction, rska_destroy on close().
+
+    A: (m, lda) float32 CUDA tensor, row-major, lda a multiple of 4; the first
+    n columns are the matrix (n defaults to lda).  b: (m,) float32 CUDA tensor.
+    A and b are borrowed by the library and kept alive here.
+    """
+
+    def __init__(self, A: torch.Tensor, b: torch.Tensor, lam: float, eta: int, t: float,
+                 seed: int, n: int | None = None, stream: torch.cuda.Stream | None = None):
+        if A.dtype != torch.float32 or b.dtype != torch.float32:
+            raise ValueError("A and b must be float32")
+        if A.dim() != 2 or b.dim() != 1 or b.shape[0] != A.shape[0]:
+            raise ValueError("A must be (m, lda) and b (m,)")
+        self.A, self.b = A, b
+        self.m, self.lda = A.shape
+        self.n = self.lda if n is None else int(n)
+        self.eta, self.lam, self.t, self.seed = int(eta), float(lam), float(t), int(seed)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = A.device
+        h = ctypes.c_void_p()
+        check(lib().rska_setup(ctypes.byref(h), _dptr(A), self.m, self.n, self.lda, _dptr(b),
+                               self.lam, self.eta, self.t, self.seed, _stream_ptr(self.stream)),
+              "rska_setup")
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rska_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- entry points -----------------------------------------------------
+    def solve(self, K: int):
+        check(lib().rska_solve(self._h, int(K)), "rska_solve")
+
+    def solve_until(self, max_iters: int, check_every: int, tol: float,
+                    xhat: torch.Tensor | None = None):
+        it = ctypes.c_int64()
+        met = ctypes.c_double()
+        check(lib().rska_solve_until(self._h, int(max_iters), int(check_every), float(tol),
+                                     _dptr(xhat), ctypes.byref(it), ctypes.byref(met)),
+              "rska_solve_until")
+        return it.value, met.value
+
+    def get_x(self):
+        x = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        z = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        check(lib().rska_get_x(self._h, _dptr(x), _dptr(z)), "rska_get_x")
+        return x, z
+
+    def set_state(self, z: torch.Tensor, k: int):
+        check(lib().rska_set_state(self._h, _dptr(z), int(k)), "rska_set_state")
+
+    @property
+    def iteration(self) -> int:
+        k = ctypes.c_int64()
+        check(lib().rska_iteration(self._h, ctypes.byref(k)), "rska_iteration")
+        return k.value
+
+    def get_indices(self, k0: int, K: int) -> torch.Tensor:
+        out = torch.empty((K, self.eta), dtype=torch.int32, device=self.device)
+        check(lib().rska_get_indices(self._h, int(k0), int(K), _dptr(out)), "rska_get_indices")
+        return out
+
+    def get_tables(self):
+        nu = torch.empty(self.m, dtype=torch.float64, device=self.device)
+        thr = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        alias = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        check(lib().rska_get_tables(self._h, _dptr(nu), _dptr(thr), _dptr(alias)),
+              "rska_get_tables")
+        return nu, thr, alias
+
+    def metrics(self, xhat: torch.Tensor | None = None):
+        rr = ctypes.c_double()
+        re = ctypes.c_double(float("nan"))
+        check(lib().rska_metrics(self._h, _dptr(xhat), ctypes.byref(rr), ctypes.byref(re)),
+              "rska_metrics")
+        return rr.value, (re.value if xhat is not None else None)
+
+    def reset(self):
+        check(lib().rska_reset(self._h), "rska_reset")
+
+    def query(self, what: str) -> int:
+        v = ctypes.c_int64()
+        check(lib().rska_query(self._h, QUERY[what], ctypes.byref(v)), "rska_query")
+        return v.value
+
+    def set_option(self, what: str, value: int):
+        check(lib().rska_set_option(self._h, OPTION[what], int(value)), "rska_set_option")
+
+
+def rska_setup(A, b, lam, eta, t, seed, n=None, stream=None) -> Solver:
+    return Solver(A, b, lam, eta, t, seed, n=n, stream=stream)
+
+
+def rska_solve(solver: Solver, K: int):
+    solver.solve(K)
+
+
+def rska_get_x(solver: Solver):
+    return solver.get_x()
+
+
+def rska_destroy(solver: Solver):
+    solver.close()

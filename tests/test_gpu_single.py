@@ -1,0 +1,191 @@
+"""GPU parity of the single-system solver (librska, through the C ABI) against
+the FP64 oracle on identical seeded inputs.
+
+Bar (from the index contract and the FP32 arithmetic of the kernels):
+  * row norms, alias tables and every sampled index: bit-exact;
+  * iterates after K iterations: ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-4
+    and the same for z = x^*.
+"""
+import numpy as np
+import pytest
+
+from synth import gaussian_problem
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_10838_gb300 import build
+    build.build()
+    import oracle
+    oracle.build()
+    from paper_2203_10838_gb300.rska import Solver
+    return torch, oracle, Solver
+
+
+def alpha_star_mp(m, n, eta):
+    """alpha^* of Corollary 1 (uniform weights) with sigma_max^2 estimated by the
+    Marchenko-Pastur edge (sqrt(m) + sqrt(n))^2 and ||A||_F^2 ~ m n."""
+    s2 = (np.sqrt(m) + np.sqrt(n)) ** 2
+    return eta / (1.0 + (eta - 1) * s2 / (m * n))
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def run_case(env, m, n, s, eta, lam, t, seed, K, grid=None, noise=0.0, pseed=None):
+    torch, orc, Solver = env
+    prob = gaussian_problem(m, n, s, seed=pseed if pseed is not None else 1000 + seed,
+                            noise=noise)
+    A = torch.from_numpy(prob.A).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    sol = Solver(A, b, lam, eta, t, seed, n=n)
+    if grid is not None:
+        sol.set_option("grid", grid)
+    nu_g, thr_g, alias_g = [v.cpu().numpy() for v in sol.get_tables()]
+    sol.solve(K)
+    x, z = [v.cpu().numpy().astype(np.float64) for v in sol.get_x()]
+    idx = sol.get_indices(0, K).cpu().numpy()
+    info = {k: sol.query(k) for k in ("grid", "rows_resident", "w4max")}
+    sol.close()
+    An = prob.A[:, :n]
+    nu = orc.row_norms(An)
+    thr, alias = orc.alias_build(nu)
+    np.testing.assert_array_equal(nu_g, nu)
+    np.testing.assert_array_equal(thr_g.view(np.uint32), thr)
+    np.testing.assert_array_equal(alias_g, alias)
+    tau = orc.sample(thr, alias, seed=seed, eta=eta, k0=0, K=K)
+    np.testing.assert_array_equal(idx, tau)
+    zr = orc.rska_fixed(An, prob.b.astype(np.float64), lam, t, eta, tau, nu=nu)
+    xr = orc.soft_shrink(zr, lam)
+    return rel(x, xr), rel(z, zr), info
+
+
+CASES = {
+    # name: (m, n, s, eta, lam, t, seed, K, grid, noise)
+    "c1_full": (1000, 500, 25, 10, 1.0, 1.0, 0, 5000, None, 0.0),
+    "rsk_eta1_ragged": (37, 13, 3, 1, 0.5, 1.0, 1, 400, None, 0.0),
+    "odd_eta_grid": (300, 1001, 20, 7, 0.3, 3.0, 2, 300, None, 0.01),
+    "forced_grid5_half_warp": (500, 257, 10, 33, 1.0, 16.0, 3, 200, 5, 0.0),
+    "wide_n_many_ctas": (2000, 4099, 40, 64, 1.0, 32.0, 4, 100, None, 0.01),
+    "cpl8_partial_residency": (300, 9000, 50, 256, 2.0, 100.0, 5, 50, 16, 0.0),
+    "eta_above_m": (1500, 3000, 30, 2048, 1.0, 400.0, 6, 20, None, 0.0),
+    "single_cta_lambda0": (64, 96, 5, 4, 0.0, 2.0, 7, 500, None, 0.0),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_parity_against_oracle(env, name):
+    m, n, s, eta, lam, t, seed, K, grid, noise = CASES[name]
+    rx, rz, info = run_case(env, m, n, s, eta, lam, t, seed, K, grid=grid, noise=noise)
+    assert rx <= REL_TOL and rz <= REL_TOL, (name, rx, rz, info)
+
+
+def test_parity_full_size_bench_configuration(env):
+    """A 20000 x 10000 Gaussian system, 200 nonzeros, 1% noise, lambda = 2,
+    eta = 1024, t = alpha^*(eta): the launch configuration the benchmark times,
+    checked over the first 30 iterations, indices bit-exact."""
+    m, n, eta = 20000, 10000, 1024
+    t = float(alpha_star_mp(m, n, eta))
+    rx, rz, info = run_case(env, m, n, 200, eta, 2.0, t, 0, 30, noise=0.01, pseed=1001)
+    assert info["grid"] > 1
+    assert rx <= REL_TOL and rz <= REL_TOL, (rx, rz, info)
+
+
+def test_resume_continues_index_sequence(env):
+    torch, orc, Solver = env
+    prob = gaussian_problem(200, 120, 6, seed=31)
+    A = torch.from_numpy(prob.A).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    with Solver(A, b, 0.5, 6, 2.0, 9, n=120) as s1:
+        s1.solve(40)
+        _, z40 = s1.get_x()
+        s1.solve(60)
+        x100, _ = s1.get_x()
+        assert s1.iteration == 100
+    with Solver(A, b, 0.5, 6, 2.0, 9, n=120) as s2:
+        s2.set_state(z40, 40)
+        s2.solve(60)
+        x100b, _ = s2.get_x()
+    a, c = x100.cpu().numpy(), x100b.cpu().numpy()
+    assert rel(c.astype(np.float64), a.astype(np.float64)) <= 1e-5
+
+
+def test_metrics_match_oracle(env):
+    torch, orc, Solver = env
+    prob = gaussian_problem(700, 300, 12, seed=41)
+    A = torch.from_numpy(prob.A).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    xh = torch.from_numpy(prob.xhat.astype(np.float32)).cuda()
+    with Solver(A, b, 1.0, 16, 8.0, 4, n=300) as sol:
+        sol.solve(150)
+        rr, re = sol.metrics(xh)
+        _, z = sol.get_x()
+    zz = z.cpu().numpy().astype(np.float64)
+    rr_o, re_o = orc.metrics(prob.A[:, :300], prob.b.astype(np.float64), zz, 1.0,
+                             prob.xhat.astype(np.float32).astype(np.float64))
+    assert abs(rr - rr_o) <= 1e-6 * rr_o
+    assert abs(re - re_o) <= 1e-6 * re_o
+
+
+def test_solve_until_reaches_tolerance(env):
+    """Stopping rule of Algorithm 1: relative error <= 1e-6 checked every 100
+    iterations, on the 1000 x 500 configuration with t = alpha^*."""
+    torch, orc, Solver = env
+    m, n, eta = 1000, 500, 10
+    prob = gaussian_problem(m, n, 25, seed=1000)
+    A = torch.from_numpy(prob.A).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    xh = torch.from_numpy(prob.xhat.astype(np.float32)).cuda()
+    t = float(alpha_star_mp(m, n, eta))
+    with Solver(A, b, 1.0, eta, t, 0, n=n) as sol:
+        iters, err = sol.solve_until(200000, 100, 1e-6, xhat=xh)
+        _, z = sol.get_x()
+        assert sol.iteration == iters
+    assert iters % 100 == 0 and 0 < iters < 200000
+    assert err <= 1e-6
+    _, re_o = orc.metrics(prob.A[:, :n], prob.b.astype(np.float64),
+                          z.cpu().numpy().astype(np.float64), 1.0,
+                          prob.xhat.astype(np.float32).astype(np.float64))
+    assert re_o <= 1.01e-6
+
+
+def test_rejects_zero_row_and_nonfinite(env):
+    torch, orc, Solver = env
+    from paper_2203_10838_gb300._lib import RSKAError
+    prob = gaussian_problem(50, 20, 3, seed=5)
+    A0 = prob.A.copy()
+    A0[17] = 0.0
+    with pytest.raises(RSKAError) as e:
+        Solver(torch.from_numpy(A0).cuda(), torch.from_numpy(prob.b).cuda(), 1.0, 4, 1.0, 0,
+               n=20)
+    assert e.value.code == 2
+    A1 = prob.A.copy()
+    A1[3, 5] = np.nan
+    with pytest.raises(RSKAError) as e:
+        Solver(torch.from_numpy(A1).cuda(), torch.from_numpy(prob.b).cuda(), 1.0, 4, 1.0, 0,
+               n=20)
+    assert e.value.code == 3
+    b1 = prob.b.copy()
+    b1[0] = np.inf
+    with pytest.raises(RSKAError) as e:
+        Solver(torch.from_numpy(prob.A).cuda(), torch.from_numpy(b1).cuda(), 1.0, 4, 1.0, 0,
+               n=20)
+    assert e.value.code == 3
+    # padding columns beyond n may hold anything
+    p2 = gaussian_problem(50, 18, 3, seed=6)
+    A2 = p2.A.copy()
+    assert A2.shape[1] == 20
+    A2[:, 18:] = np.nan
+    with Solver(torch.from_numpy(A2).cuda(), torch.from_numpy(p2.b).cuda(), 1.0, 4, 1.0, 0,
+                n=18) as sol:
+        sol.solve(10)
+        x, _ = sol.get_x()
+        assert torch.isfinite(x).all()
