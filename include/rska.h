@@ -84,9 +84,11 @@ int rska_setup(rska_ctx **out, const float *A, int64_t m, int64_t n, int64_t lda
                void *stream);
 
 /*
- * rska_solve -- run K iterations of Algorithm 1 (k -> k + K) in one persistent
- * kernel launch on the context's stream.  Asynchronous; K = 0 is a no-op.
- * Errors: EINVAL (K < 0), a sticky code.
+ * rska_solve -- run K iterations of Algorithm 1 (k -> k + K) on the context's
+ * stream: per chunk of up to 2^21/eta iterations, one pre-sampling kernel
+ * (tau_k, b and 1/||a||^2 for the whole chunk) and one persistent kernel
+ * launch.  Asynchronous; K = 0 is a no-op.  Errors: EINVAL (K < 0), a sticky
+ * code.
  */
 int rska_solve(rska_ctx *ctx, int64_t K);
 
@@ -150,9 +152,12 @@ int rska_destroy(rska_ctx *ctx);
 /*
  * rska_query -- HOST: launch facts of the solver for this context:
  *   what = 0: CTAs in the persistent grid      1: threads per CTA
- *          2: rows of tau_k kept in shared memory per iteration
+ *          2: rows of tau_k kept on chip (shared memory + registers) per
+ *             iteration by the widest CTA; the rest are fetched twice
  *          3: float4 columns owned by the widest CTA
  *          4: dynamic shared memory bytes per CTA
+ *          5: row steps per thread held in registers (0 when the shared
+ *             memory tile holds all of tau_k)
  */
 int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
 

@@ -39,6 +39,11 @@ void free_all(Ctx* c) {
   cudaFree(c->stop);
   cudaFree(c->macc);
   cudaFree(c->scratch);
+  cudaFree(c->tidx);
+  cudaFree(c->tb);
+  cudaFree(c->tiv);
+  c->tidx = nullptr;
+  c->tb = c->tiv = nullptr;
   c->nu = nullptr;
   c->inv_nu = nullptr;
   c->thr = nullptr;
@@ -95,6 +100,9 @@ rska::SolveArgs solve_args(Ctx* c, int64_t K, const int* stop) {
   a.status = c->status;
   a.kdev = c->kdev;
   a.stop = stop;
+  a.tidx = c->tidx;
+  a.tb = c->tb;
+  a.tiv = c->tiv;
   a.K = K;
   a.limit_ns = c->limit_ns;
   return a;
@@ -153,13 +161,19 @@ int rska_setup(rska_ctx** out, const float* A, int64_t m, int64_t n, int64_t lda
     return rc;
   }
   const int64_t np = n_padded(n);
+  const int64_t eta4 = (eta + 3) / 4 * 4;
+  c->chunk = rska::kPresampleDraws / eta4;
+  if (c->chunk < 1) c->chunk = 1;
   if ((e = dalloc(&c->nu, m)) != cudaSuccess || (e = dalloc(&c->inv_nu, m)) != cudaSuccess ||
       (e = dalloc(&c->thr, m)) != cudaSuccess || (e = dalloc(&c->alias, m)) != cudaSuccess ||
       (e = dalloc(&c->z, np)) != cudaSuccess || (e = dalloc(&c->x, np)) != cudaSuccess ||
-      (e = dalloc(&c->racc, 3 * (size_t)eta)) != cudaSuccess ||
+      (e = dalloc(&c->racc, 3 * (size_t)eta * rska::kAccStride)) != cudaSuccess ||
       (e = dalloc(&c->bar, 1)) != cudaSuccess || (e = dalloc(&c->status, 1)) != cudaSuccess ||
       (e = dalloc(&c->kdev, 1)) != cudaSuccess || (e = dalloc(&c->stop, 1)) != cudaSuccess ||
       (e = dalloc(&c->macc, 8)) != cudaSuccess ||
+      (e = dalloc(&c->tidx, (size_t)c->chunk * eta4)) != cudaSuccess ||
+      (e = dalloc(&c->tb, (size_t)c->chunk * eta4)) != cudaSuccess ||
+      (e = dalloc(&c->tiv, (size_t)c->chunk * eta4)) != cudaSuccess ||
       (e = cudaMalloc(&c->scratch, (size_t)m * (sizeof(double) + sizeof(int32_t)))) !=
           cudaSuccess) {
     free_all(c);
@@ -200,11 +214,13 @@ int rska_solve(rska_ctx* h, int64_t K) {
   if (!h || K < 0) return RSKA_EINVAL;
   Ctx* c = &h->c;
   if (c->sticky) return c->sticky;
-  if (K == 0) return RSKA_OK;
-  rska::SolveArgs a = solve_args(c, K, nullptr);
-  cudaError_t e = rska::launch_solve(a, c->geom, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e);
-  c->k_host += K;
+  for (int64_t done = 0; done < K; done += c->chunk) {
+    const int64_t Kc = (K - done < c->chunk) ? (K - done) : c->chunk;
+    rska::SolveArgs a = solve_args(c, Kc, nullptr);
+    cudaError_t e = rska::launch_solve(a, c->geom, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->k_host += Kc;
+  }
   return RSKA_OK;
 }
 
@@ -218,8 +234,9 @@ int rska_solve_until(rska_ctx* h, int64_t max_iters, int64_t check_every, double
   cudaError_t e = cudaMemsetAsync(c->stop, 0, sizeof(int), s);
   int64_t* k_stop = reinterpret_cast<int64_t*>(c->macc + 6);
   if (e == cudaSuccess) e = cudaMemsetAsync(k_stop, 0xff, sizeof(int64_t), s);
-  for (int64_t done = 0; e == cudaSuccess && done < max_iters; done += check_every) {
-    const int64_t K = (max_iters - done < check_every) ? (max_iters - done) : check_every;
+  const int64_t step = (check_every < c->chunk) ? check_every : c->chunk;
+  for (int64_t done = 0; e == cudaSuccess && done < max_iters; done += step) {
+    const int64_t K = (max_iters - done < step) ? (max_iters - done) : step;
     rska::SolveArgs a = solve_args(c, K, c->stop);
     e = rska::launch_solve(a, c->geom, s);
     if (e == cudaSuccess)
@@ -352,6 +369,7 @@ int rska_query(rska_ctx* h, int what, int64_t* value_out) {
     case 2: *value_out = g.rows_res; return RSKA_OK;
     case 3: *value_out = g.w4max; return RSKA_OK;
     case 4: *value_out = (int64_t)g.smem; return RSKA_OK;
+    case 5: *value_out = g.rreg; return RSKA_OK;
     default: return RSKA_EINVAL;
   }
 }

@@ -10,14 +10,17 @@ namespace rska {
 
 constexpr int kSolveThreads = 512;      // threads per CTA of the persistent solver
 constexpr int kMaxEta = 4096;           // largest batch size eta
-constexpr int kMaxColsPerLane = 8;      // float4 columns per lane in the dot phase
+constexpr int kSolveRegRows = 12;       // row steps a thread may hold in registers
+constexpr int kAccStride = 32;          // floats between two rows' dot accumulators (128 B)
+constexpr int64_t kPresampleDraws = 1 << 21;  // draws pre-sampled per launch (at most)
 
 // Launch geometry of the persistent single-system solver.
 struct SolveGeometry {
   int grid = 0;          // CTAs (one per SM at most; all co-resident)
   int w4max = 0;         // float4 columns of the widest CTA
-  int cpl = 1;           // float4 columns per lane in the dot phase (1, 2, 4, 8)
-  int rows_res = 0;      // rows of tau_k kept in shared memory
+  int tile_cap = 0;      // float4 elements of the shared-memory row tile
+  int rreg = 0;          // row steps held in registers (0 or kSolveRegRows)
+  int rows_res = 0;      // rows of tau_k kept on chip by the widest CTA
   size_t smem = 0;       // dynamic shared memory per CTA
 };
 
@@ -41,6 +44,9 @@ struct SolveArgs {
   int* status;
   int64_t* kdev;               // iteration counter
   const int* stop;             // nullable: skip the launch when *stop != 0
+  const int32_t* tidx;         // pre-sampled tau (K rows of eta4)
+  const float* tb;             // b at tau
+  const float* tiv;            // 1/||a||^2 at tau
   int64_t K;
   uint64_t limit_ns;
 };
@@ -69,6 +75,10 @@ struct Ctx {
   int64_t* kdev = nullptr;
   int* stop = nullptr;
   double* macc = nullptr;      // metric accumulators and results
+  int32_t* tidx = nullptr;     // pre-sampled tau for one launch
+  float* tb = nullptr;
+  float* tiv = nullptr;
+  int64_t chunk = 1;           // iterations per persistent launch (pre-sample capacity)
   void* scratch = nullptr;     // alias-build scratch (freed after setup)
   // host mirrors
   int64_t k_host = 0;

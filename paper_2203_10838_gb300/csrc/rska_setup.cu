@@ -24,7 +24,7 @@ __global__ void row_norms_kernel(const float* __restrict__ A, int64_t m, int64_t
       const float a = __ldg(row + j);
       finite = finite && isfinite(a);
       const double ad = (double)a;
-      p = __dadd_rn(p, __dmul_rn(ad, ad));
+      p = __fma_rn(ad, ad, p);  // a*a is exact in FP64, so this equals p + a*a
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
@@ -43,29 +43,24 @@ __global__ void row_norms_kernel(const float* __restrict__ A, int64_t m, int64_t
 }
 
 // Sequential Vose construction in FP64 by one thread (the canonical order of
-// the index contract).  `stk` holds both LIFO stacks: "small" grows up from
-// index 0, "large" grows down from index m-1; together they never hold more
-// than m entries.
-__device__ void alias_build_one(const double* __restrict__ nu, int64_t m, uint32_t* thr,
-                                int32_t* alias, double* q, int32_t* stk) {
-  double W = 0.0;
-  for (int64_t i = 0; i < m; ++i) W = __dadd_rn(W, nu[i]);
+// the index contract), on q[i] = (nu_i m) / W already in place.  `stk` holds
+// both LIFO stacks: "small" grows up from index 0, "large" grows down from
+// index m-1; together they never hold more than m entries.
+template <typename IdxT>
+__device__ void vose_sequential(double* q, IdxT* stk, int64_t m, uint32_t* thr, int32_t* alias) {
   int64_t ns = 0, nl = 0;
-  const double md = (double)m;
   for (int64_t i = 0; i < m; ++i) {
-    const double qi = __ddiv_rn(__dmul_rn(nu[i], md), W);
-    q[i] = qi;
-    if (qi < 1.0) {
-      stk[ns++] = (int32_t)i;
+    if (q[i] < 1.0) {
+      stk[ns++] = (IdxT)i;
     } else {
-      stk[m - 1 - nl] = (int32_t)i;
+      stk[m - 1 - nl] = (IdxT)i;
       ++nl;
     }
   }
   while (ns > 0 && nl > 0) {
-    const int32_t l = stk[--ns];
+    const int64_t l = stk[--ns];
     --nl;
-    const int32_t g = stk[m - 1 - nl];
+    const int64_t g = stk[m - 1 - nl];
     const double ql = q[l];
     const double scaled = __dmul_rn(ql, 4294967296.0);
     uint32_t t;
@@ -77,33 +72,59 @@ __device__ void alias_build_one(const double* __restrict__ nu, int64_t m, uint32
       t = __double2uint_rz(scaled);
     }
     thr[l] = t;
-    alias[l] = g;
+    alias[l] = (int32_t)g;
     const double qg = __dsub_rn(__dadd_rn(q[g], ql), 1.0);
     q[g] = qg;
     if (qg < 1.0) {
-      stk[ns++] = g;
+      stk[ns++] = (IdxT)g;
     } else {
-      stk[m - 1 - nl] = g;
+      stk[m - 1 - nl] = (IdxT)g;
       ++nl;
     }
   }
   for (int64_t s = 0; s < ns; ++s) {
-    const int32_t l = stk[s];
+    const int64_t l = stk[s];
     thr[l] = 4294967295u;
-    alias[l] = l;
+    alias[l] = (int32_t)l;
   }
   for (int64_t s = 0; s < nl; ++s) {
-    const int32_t g = stk[m - 1 - s];
+    const int64_t g = stk[m - 1 - s];
     thr[g] = 4294967295u;
-    alias[g] = g;
+    alias[g] = (int32_t)g;
   }
 }
 
+// One block builds the table: all threads stage nu, thread 0 sums W in
+// ascending order, all threads form q_i = (nu_i m) / W, thread 0 runs Vose.
+// With use_smem the q and stack arrays live in shared memory (stack indices
+// as uint16, so m <= 65536); otherwise in the global scratch.
 __global__ void alias_build_kernel(const double* __restrict__ nu, int64_t m, uint32_t* thr,
-                                   int32_t* alias, double* q, int32_t* stk, const int* status) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  if (*status != kStatusOk) return;
-  alias_build_one(nu, m, thr, alias, q, stk);
+                                   int32_t* alias, double* gq, int32_t* gstk, const int* status,
+                                   int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sW;
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = (*status != kStatusOk);
+  __syncthreads();
+  if (sbad) return;
+  double* q = use_smem ? reinterpret_cast<double*>(smem) : gq;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) q[i] = nu[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double W = 0.0;
+    for (int64_t i = 0; i < m; ++i) W = __dadd_rn(W, q[i]);
+    sW = W;
+  }
+  __syncthreads();
+  const double W = sW;
+  const double md = (double)m;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) q[i] = __ddiv_rn(__dmul_rn(q[i], md), W);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (use_smem)
+    vose_sequential<uint16_t>(q, reinterpret_cast<uint16_t*>(q + m), m, thr, alias);
+  else
+    vose_sequential<int32_t>(q, gstk, m, thr, alias);
 }
 
 __global__ void indices_kernel(const uint32_t* __restrict__ thr, const int32_t* __restrict__ alias,
@@ -148,7 +169,21 @@ cudaError_t launch_row_norms(const float* A, int64_t m, int64_t n, int64_t lda, 
 cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,
                                double* q_scratch, int32_t* stack_scratch, int* status,
                                cudaStream_t s) {
-  alias_build_kernel<<<1, 32, 0, s>>>(nu, m, thr, alias, q_scratch, stack_scratch, status);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const size_t need = (size_t)m * (sizeof(double) + sizeof(uint16_t));
+  const int use_smem = (m <= 65536 && need + 64 <= (size_t)optin) ? 1 : 0;
+  const size_t smem = use_smem ? need : 0;
+  if (use_smem) {
+    e = cudaFuncSetAttribute(alias_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  alias_build_kernel<<<1, 256, smem, s>>>(nu, m, thr, alias, q_scratch, stack_scratch, status,
+                                          use_smem);
   return cudaGetLastError();
 }
 

@@ -1,20 +1,31 @@
 // rska_solve.cu -- the persistent single-system RSKA kernel (eq. rska,
-// Algorithm 1 with w_i = t).
+// Algorithm 1 with w_i = t) and its index pre-sampler.
 //
-// Work split: the n columns (as float4 groups) are split into P contiguous
-// slices, one per CTA, and every CTA keeps its slice of z = x^* and of
-// x = S_lambda(z) in shared memory for the whole launch.  One iteration:
-//   1. dot phase: each CTA reads its slice of the eta sampled rows (coalesced
-//      128-bit loads), forms the partial dots <a_i, x> over its columns with
-//      warp shuffles and adds them into a global accumulator (one float per
-//      row of tau_k); rows that fit stay in shared memory for step 3;
-//   2. the CTA draws tau_{k+1} (Philox + alias table) and fetches b_i and
-//      1/||a_i||^2 for it, hiding those latencies before the barrier;
-//   3. grid barrier; c_i = (t/eta)(<a_i, x> - b_i)/||a_i||^2 from the reduced
-//      dots; the CTA applies z_j -= sum_i c_i a_ij to its slice and
-//      re-thresholds x_j = S_lambda(z_j) (steps 5-6 of Algorithm 1).
-// The only cross-CTA exchange is eta floats per iteration.  A single-CTA grid
-// keeps the accumulator in shared memory and uses __syncthreads instead.
+// Work split.  The n columns, as float4 groups, are split into P contiguous
+// slices, one per CTA; a CTA keeps its slice of z = x^* and x = S_lambda(z)
+// in shared memory for the whole launch.  Inside a CTA, thread (rg, c) owns
+// float4 column c of the slice and the rows s = rg + RG*i of tau_k
+// (RG = threads / slice width), so consecutive threads touch consecutive
+// 16-byte words of a row (coalesced) and every thread's rows stay with it for
+// the whole iteration.
+//
+// One iteration k:
+//   1. the CTA's slice of the eta sampled rows is fetched once from HBM:
+//      the first rows with cp.async into shared memory (four commit groups, so
+//      the dots start while later groups are in flight), the next ones into
+//      registers, anything beyond on-chip capacity is streamed (and fetched
+//      again in step 4);
+//   2. each thread forms a_ij * x_j for its elements; a segmented warp scan
+//      sums the lanes of one row, shared atomics finish the CTA's partial dot,
+//      and one global atomic per row adds it to a padded accumulator;
+//   3. grid barrier (bounded wait);  c_s = (t/eta)(<a_s, x_k> - b_s)/||a_s||^2;
+//   4. z_j -= sum_s c_s a_sj from the on-chip rows, reduced over the row
+//      groups of each column, then x_j = S_lambda(z_j).
+// tau_{k}, b_{tau} and 1/||a_tau||^2 come from a pre-sampler kernel that draws
+// the whole launch's indices in parallel; the persistent kernel copies them
+// one iteration ahead, so no dependent gather sits on the critical path.  The
+// only cross-CTA exchange is eta floats per iteration.  A one-CTA grid keeps
+// the accumulator in shared memory and uses __syncthreads as the barrier.
 #include <algorithm>
 
 #include "rska_device.cuh"
@@ -25,17 +36,15 @@ namespace rska {
 namespace {
 
 constexpr int NT = kSolveThreads;
-constexpr int NW = NT / 32;
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
   return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
 }
 
-// Zero the components of v that lie at or beyond column n (only the last
-// float4 group of a row can hold such padding).
+// Zero the components of v at or beyond column n (only the last float4 group
+// of a row can hold padding).
 __device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
   const int64_t base = gc * 4;
-  if (base + 4 <= n) return v;
   float4 r = v;
   if (base + 0 >= n) r.x = 0.f;
   if (base + 1 >= n) r.y = 0.f;
@@ -44,28 +53,83 @@ __device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
   return r;
 }
 
-// Draw tau_k into idx[0..eta) and gather b_i, 1/||a_i||^2 for it.
-__device__ __forceinline__ void draw_iteration(const SolveArgs& a, int64_t k, int32_t* idx,
-                                               float* bsel, float* ivsel) {
-  const int npairs = (a.eta + 1) >> 1;
-  for (int q = threadIdx.x; q < npairs; q += NT) {
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src_gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst_smem)),
+               "l"(src_gmem)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ float4 ldg_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// Inclusive sum over the lanes of this thread's segment that precede it in
+// the warp; the segment's last lane in the warp ends with the segment total.
+__device__ __forceinline__ float seg_scan(float v, int lane, int segstart, int dmax) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    if (d < dmax) {
+      const float u = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane - d >= segstart) v += u;
+    }
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Pre-sampler: tau_k, b_{tau_k}, 1/||a_{tau_k}||^2 for k = k0 .. k0+K-1, with
+// k0 read from the device iteration counter.  Row j of each output (stride
+// eta4 = eta rounded up to 4) belongs to iteration k0 + j.
+// ---------------------------------------------------------------------------
+__global__ void presample_kernel(const uint32_t* __restrict__ thr, const int32_t* __restrict__ alias,
+                                 uint32_t m, uint64_t seed, uint32_t problem,
+                                 const int64_t* __restrict__ kdev, int64_t K, int32_t eta,
+                                 int32_t eta4, const float* __restrict__ b,
+                                 const float* __restrict__ inv_nu, int32_t* __restrict__ tidx,
+                                 float* __restrict__ tb, float* __restrict__ tiv,
+                                 const int* stop) {
+  if (stop != nullptr && ld_relaxed_s32(stop) != 0) return;
+  const int64_t k0 = *kdev;
+  const int64_t npairs = (eta + 1) / 2;
+  const int64_t total = K * npairs;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / npairs;
+    const uint32_t q = (uint32_t)(e - j * npairs);
     int32_t i0, i1;
-    draw_pair(a.seed, k, (uint32_t)q, a.problem, a.thr, a.alias, (uint32_t)a.m, &i0, &i1);
-    idx[2 * q] = i0;
-    bsel[2 * q] = __ldg(a.b + i0);
-    ivsel[2 * q] = __ldg(a.inv_nu + i0);
-    if (2 * q + 1 < a.eta) {
-      idx[2 * q + 1] = i1;
-      bsel[2 * q + 1] = __ldg(a.b + i1);
-      ivsel[2 * q + 1] = __ldg(a.inv_nu + i1);
+    draw_pair(seed, k0 + j, q, problem, thr, alias, m, &i0, &i1);
+    const int64_t o = j * eta4 + 2 * q;
+    tidx[o] = i0;
+    tb[o] = __ldg(b + i0);
+    tiv[o] = __ldg(inv_nu + i0);
+    if (2 * (int64_t)q + 1 < eta) {
+      tidx[o + 1] = i1;
+      tb[o + 1] = __ldg(b + i1);
+      tiv[o + 1] = __ldg(inv_nu + i1);
     }
   }
 }
 
-template <int CPL>
+template <int RREG>
 __global__ void __launch_bounds__(NT, 1)
-    rska_persistent_kernel(SolveArgs a, int w4max, int rows_res) {
-  constexpr int U = (CPL >= 8) ? 1 : 8 / CPL;  // rows in flight per lane
+    rska_persistent_kernel(SolveArgs a, int w4max, int tile_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
 
@@ -76,195 +140,238 @@ __global__ void __launch_bounds__(NT, 1)
   const int warp = tid >> 5;
   const int P = gridDim.x;
   const int eta = a.eta;
+  const int eta4 = (eta + 3) & ~3;
   const int64_t n4 = (a.n + 3) >> 2;
   const int64_t cb = (int64_t)blockIdx.x * n4 / P;
   const int64_t ce = (int64_t)(blockIdx.x + 1) * n4 / P;
   const int w4 = (int)(ce - cb);
   const bool single = (P == 1);
 
-  float4* tile = reinterpret_cast<float4*>(smem);               // rows_res x w4max
-  float4* zs = tile + (size_t)rows_res * w4max;                 // w4max
-  float4* xs = zs + w4max;                                      // w4max
-  float4* red = xs + w4max;                                     // NT
-  int32_t* idx = reinterpret_cast<int32_t*>(red + NT);          // 2 x eta
-  float* bsel = reinterpret_cast<float*>(idx + 2 * eta);        // 2 x eta
-  float* ivsel = bsel + 2 * eta;                                // 2 x eta
-  float* cs = ivsel + 2 * eta;                                  // eta
-  float* sacc = cs + eta;                                       // eta (single-CTA grid only)
+  // thread layout: RG row groups x w4 columns
+  const int RG = NT / w4;
+  const int NTa = RG * w4;
+  const int rg = tid / w4;
+  const int c = tid - rg * w4;
+  const bool active = rg < RG;
+  const int NI = (eta + RG - 1) / RG;        // row steps
+  const int IS = tile_cap / NTa;             // row steps held in shared memory
+  const int nIs = min(IS, NI);
+  const int segstart = max(rg * w4 - warp * 32, 0);
+  const int seglast = min((rg + 1) * w4 - 1 - warp * 32, 31);
+  const int dmax = min(w4, 32);
+  const bool tailc = active && ((cb + c) * 4 + 4 > a.n);
+
+  float4* tile = reinterpret_cast<float4*>(smem);                  // tile_cap
+  float4* zs = tile + tile_cap;                                    // w4max
+  float4* xs = zs + w4max;                                         // w4max
+  float4* red = xs + w4max;                                        // NT
+  int32_t* sidx = reinterpret_cast<int32_t*>(red + NT);            // 2 x eta4
+  float* sb = reinterpret_cast<float*>(sidx + 2 * eta4);           // eta4
+  float* siv = sb + eta4;                                          // eta4
+  float* cs = siv + eta4;                                          // eta4
+  float* sdot = cs + eta4;                                         // eta4
 
   const int64_t k0 = *a.kdev;
   const float lam = a.lambda;
-  const float4* zg = reinterpret_cast<const float4*>(a.z);
-  for (int c = tid; c < w4; c += NT) {
-    const float4 zv = zg[cb + c];
-    zs[c] = zv;
-    xs[c] = mask_tail(soft_shrink4(zv, lam), cb + c, a.n);
+  {
+    const float4* zg = reinterpret_cast<const float4*>(a.z);
+    for (int q = tid; q < w4; q += NT) {
+      const float4 zv = zg[cb + q];
+      zs[q] = zv;
+      xs[q] = mask_tail(soft_shrink4(zv, lam), cb + q, a.n);
+    }
+    for (int s = tid; s < eta4; s += NT) sdot[s] = 0.f;
+    for (int q = tid; q < eta4 / 4; q += NT) cp_async16(sidx + 4 * q, a.tidx + 4 * q);
+    cp_async_commit();
+    cp_async_wait<0>();
   }
-  if (single)
-    for (int s = tid; s < eta; s += NT) sacc[s] = 0.f;
-  draw_iteration(a, k0, idx, bsel, ivsel);
   __syncthreads();
 
-  // dot-phase lane layout: L lanes per row, RPW rows per warp
-  int L = 32;
-  if (w4 <= 16) {
-    L = 1;
-    while (L < w4) L <<= 1;
-  }
-  const int RPW = 32 / L;
-  const int sub = lane / L;
-  const int lc = lane % L;
-  const int rstride = NW * RPW;
-  // scatter-phase layout: RG row groups of w4 threads
-  const int RG = NT / w4;
-  const int rg = tid / w4;
-  const int sc = tid - rg * w4;
-
-  const float* Ab = a.A + cb * 4;
+  const float* Ab = a.A + cb * 4 + (active ? c : 0) * 4;
+  const int64_t lda = a.lda;
+  const int g1 = nIs / 4, g2 = nIs / 2, g3 = (3 * nIs) / 4;
 
   for (int64_t j = 0; j < a.K; ++j) {
     const int cur = (int)(j & 1);
+    const int32_t* I = sidx + cur * eta4;
+    const float4 xc = active ? xs[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // ---- 1. fetch this CTA's slice of the sampled rows ----
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i0 = (q == 0) ? 0 : (q == 1) ? g1 : (q == 2) ? g2 : g3;
+      const int i1 = (q == 0) ? g1 : (q == 1) ? g2 : (q == 2) ? g3 : nIs;
+      if (active) {
+        for (int i = i0; i < i1; ++i) {
+          const int s = rg + RG * i;
+          if (s < eta) cp_async16(tile + (size_t)i * NTa + tid, Ab + (int64_t)I[s] * lda);
+        }
+      }
+      cp_async_commit();
+    }
+    float4 rv[RREG > 0 ? RREG : 1];
+#pragma unroll
+    for (int r = 0; r < RREG; ++r) {
+      const int i = IS + r;
+      const int s = rg + RG * i;
+      rv[r] = (active && i < NI && s < eta)
+                  ? ldg_stream(reinterpret_cast<const float4*>(Ab + (int64_t)I[s] * lda))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    {  // b, 1/||a||^2 of this iteration; tau of the next one
+      const int nq = eta4 / 4;
+      const int32_t* gi = a.tidx + (j + 1) * eta4;
+      const float* gb = a.tb + j * eta4;
+      const float* gv = a.tiv + j * eta4;
+      int32_t* nidx = sidx + (cur ^ 1) * eta4;
+      const bool more = (j + 1 < a.K);
+      for (int q = tid; q < 3 * nq; q += NT) {
+        if (q < nq) {
+          cp_async16(sb + 4 * q, gb + 4 * q);
+        } else if (q < 2 * nq) {
+          cp_async16(siv + 4 * (q - nq), gv + 4 * (q - nq));
+        } else if (more) {
+          cp_async16(nidx + 4 * (q - 2 * nq), gi + 4 * (q - 2 * nq));
+        }
+      }
+      cp_async_commit();
+    }
+
+    // ---- 2. partial dots <a_s, x_k> over this CTA's columns ----
+    auto dot_step = [&](int i, float4 v) {
+      const int s = rg + RG * i;
+      const bool valid = active && s < eta;
+      if (tailc) v = mask_tail(v, cb + c, a.n);
+      float p = valid ? dot4(v, xc) : 0.f;
+      p = seg_scan(p, lane, segstart, dmax);
+      if (valid && lane == seglast) atomicAdd(sdot + s, p);
+    };
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q == 0) cp_async_wait<4>();
+      if (q == 1) cp_async_wait<3>();
+      if (q == 2) cp_async_wait<2>();
+      if (q == 3) cp_async_wait<1>();
+      const int i0 = (q == 0) ? 0 : (q == 1) ? g1 : (q == 2) ? g2 : g3;
+      const int i1 = (q == 0) ? g1 : (q == 1) ? g2 : (q == 2) ? g3 : nIs;
+      for (int i = i0; i < i1; ++i) dot_step(i, tile[(size_t)i * NTa + tid]);
+    }
+#pragma unroll
+    for (int r = 0; r < RREG; ++r)
+      if (IS + r < NI) dot_step(IS + r, rv[r]);
+    for (int i = IS + RREG; i < NI; i += 4) {  // beyond on-chip capacity
+      float4 sv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int s = rg + RG * (i + u);
+        sv[u] = (active && i + u < NI && s < eta)
+                    ? __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)I[s] * lda))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i + u < NI) dot_step(i + u, sv[u]);
+    }
+    __syncthreads();
+
     const int buf = (int)(j % 3);
-    const int32_t* I = idx + cur * eta;
-    float* acc_rows = single ? sacc : (a.racc + (size_t)buf * eta);
-
-    float4 xr[CPL];
-    bool tail[CPL];
-#pragma unroll
-    for (int jj = 0; jj < CPL; ++jj) {
-      const int c = lc + L * jj;
-      xr[jj] = (c < w4) ? xs[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-      tail[jj] = (c < w4) && ((cb + c) * 4 + 4 > a.n);
-    }
-
-    // ---- dot phase: r_i = <a_i, x_k> over this CTA's columns ----
-    for (int s0 = warp * RPW; s0 < eta; s0 += rstride * U) {
-      float4 av[U][CPL];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int s = s0 + sub + u * rstride;
-        const bool rv = s < eta;
-        const float* rowp = Ab + (int64_t)(rv ? I[s] : 0) * a.lda;
-#pragma unroll
-        for (int jj = 0; jj < CPL; ++jj) {
-          const int c = lc + L * jj;
-          av[u][jj] = (rv && c < w4) ? __ldg(reinterpret_cast<const float4*>(rowp) + c)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+    float* racc = a.racc + (size_t)buf * eta * kAccStride;
+    if (!single) {
+      for (int s = tid; s < eta; s += NT) {
+        atomicAdd(racc + (size_t)s * kAccStride, sdot[s]);
+        sdot[s] = 0.f;
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int s = s0 + sub + u * rstride;
-        float acc = 0.f;
-#pragma unroll
-        for (int jj = 0; jj < CPL; ++jj) {
-          float4 v = av[u][jj];
-          if (tail[jj]) v = mask_tail(v, cb + lc + L * jj, a.n);
-          acc += dot4(v, xr[jj]);
-          const int c = lc + L * jj;
-          if (s < rows_res && c < w4) tile[(size_t)s * w4max + c] = v;
-        }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1)
-          if (o < L) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lc == 0 && s < eta) {
-          if (single)
-            atomicAdd(acc_rows + s, acc);
-          else
-            atomicAdd(acc_rows + s, acc);
-        }
+      if (blockIdx.x == 0) {
+        float* nxt = a.racc + (size_t)((j + 1) % 3) * eta * kAccStride;
+        for (int s = tid; s < eta; s += NT) nxt[(size_t)s * kAccStride] = 0.f;
       }
     }
+    cp_async_wait<0>();
 
-    // ---- draw tau_{k+1}; recycle an accumulator buffer ----
-    if (j + 1 < a.K) draw_iteration(a, k0 + j + 1, idx + (cur ^ 1) * eta,
-                                    bsel + (cur ^ 1) * eta, ivsel + (cur ^ 1) * eta);
-    if (!single && blockIdx.x == 0) {
-      float* nxt = a.racc + (size_t)((j + 1) % 3) * eta;
-      for (int s = tid; s < eta; s += NT) nxt[s] = 0.f;
-    }
-
+    // ---- 3. exchange and coefficients ----
     if (single) {
       __syncthreads();
     } else if (!grid_barrier(a.bar, (unsigned long long)(j + 1), a.status, a.limit_ns,
                              &s_flag)) {
       return;
     }
-
-    // ---- coefficients c_i = (t/eta) (r_i - b_i) / ||a_i||^2 ----
-    const float* Bs = bsel + cur * eta;
-    const float* Vs = ivsel + cur * eta;
     for (int s = tid; s < eta; s += NT) {
       float r;
       if (single) {
-        r = sacc[s];
-        sacc[s] = 0.f;
+        r = sdot[s];
+        sdot[s] = 0.f;
       } else {
-        r = __ldcg(acc_rows + s);
+        r = __ldcg(racc + (size_t)s * kAccStride);
       }
-      cs[s] = a.coef * ((r - Bs[s]) * Vs[s]);
+      cs[s] = a.coef * ((r - sb[s]) * siv[s]);
     }
     __syncthreads();
 
-    // ---- scatter: z_j -= sum_i c_i a_ij over this CTA's columns ----
-    if (rg < RG) {
-      float4 acc4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      const bool tl = ((cb + sc) * 4 + 4 > a.n);
-      for (int s = rg; s < eta; s += RG) {
-        const float cval = cs[s];
-        float4 v;
-        if (s < rows_res) {
-          v = tile[(size_t)s * w4max + sc];
-        } else {
-          v = __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)I[s] * a.lda) + sc);
-          if (tl) v = mask_tail(v, cb + sc, a.n);
-        }
-        acc4.x = fmaf(cval, v.x, acc4.x);
-        acc4.y = fmaf(cval, v.y, acc4.y);
-        acc4.z = fmaf(cval, v.z, acc4.z);
-        acc4.w = fmaf(cval, v.w, acc4.w);
+    // ---- 4. z_j -= sum_s c_s a_sj ----
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto upd_step = [&](int i, float4 v) {
+      const int s = rg + RG * i;
+      if (active && s < eta) {
+        if (tailc) v = mask_tail(v, cb + c, a.n);
+        const float cv = cs[s];
+        acc.x = fmaf(cv, v.x, acc.x);
+        acc.y = fmaf(cv, v.y, acc.y);
+        acc.z = fmaf(cv, v.z, acc.z);
+        acc.w = fmaf(cv, v.w, acc.w);
       }
-      red[tid] = acc4;
+    };
+    for (int i = 0; i < nIs; ++i) upd_step(i, tile[(size_t)i * NTa + tid]);
+#pragma unroll
+    for (int r = 0; r < RREG; ++r)
+      if (IS + r < NI) upd_step(IS + r, rv[r]);
+    for (int i = IS + RREG; i < NI; i += 4) {
+      float4 sv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int s = rg + RG * (i + u);
+        sv[u] = (active && i + u < NI && s < eta)
+                    ? __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)I[s] * lda))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i + u < NI) upd_step(i + u, sv[u]);
     }
+    red[tid] = acc;
     __syncthreads();
-    for (int c = tid; c < w4; c += NT) {
-      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int g = 0; g < RG; ++g) {
-        const float4 v = red[g * w4 + c];
-        sum.x += v.x;
-        sum.y += v.y;
-        sum.z += v.z;
-        sum.w += v.w;
+    {
+      const float* redf = reinterpret_cast<const float*>(red);
+      float* zf = reinterpret_cast<float*>(zs);
+      float* xf = reinterpret_cast<float*>(xs);
+      for (int e = tid; e < w4 * 4; e += NT) {
+        float sum = 0.f;
+        for (int g = 0; g < RG; ++g) sum += redf[(size_t)g * w4 * 4 + e];
+        const int64_t col = cb * 4 + e;
+        const float zv = (col < a.n) ? zf[e] - sum : 0.f;
+        zf[e] = zv;
+        xf[e] = soft_shrink(zv, lam);
       }
-      float4 zv = zs[c];
-      zv.x -= sum.x;
-      zv.y -= sum.y;
-      zv.z -= sum.z;
-      zv.w -= sum.w;
-      zv = mask_tail(zv, cb + c, a.n);
-      zs[c] = zv;
-      xs[c] = soft_shrink4(zv, lam);
     }
     __syncthreads();
   }
 
   float4* zo = reinterpret_cast<float4*>(a.z);
   float4* xo = reinterpret_cast<float4*>(a.x);
-  for (int c = tid; c < w4; c += NT) {
-    zo[cb + c] = zs[c];
-    xo[cb + c] = xs[c];
+  for (int q = tid; q < w4; q += NT) {
+    zo[cb + q] = zs[q];
+    xo[cb + q] = xs[q];
   }
   if (blockIdx.x == 0 && tid == 0) *a.kdev = k0 + a.K;
 }
 
 size_t fixed_smem(int w4max, int eta) {
-  return (size_t)2 * w4max * 16 + (size_t)NT * 16 + (size_t)2 * eta * 12 + (size_t)eta * 4 +
-         (size_t)eta * 4;
+  const size_t eta4 = (size_t)((eta + 3) & ~3);
+  return (size_t)2 * w4max * 16 + (size_t)NT * 16 + 2 * eta4 * 4 + 4 * eta4 * 4;
 }
 
-template <int CPL>
+template <int RREG>
 cudaError_t set_smem_attr(size_t smem) {
-  return cudaFuncSetAttribute(rska_persistent_kernel<CPL>,
+  return cudaFuncSetAttribute(rska_persistent_kernel<RREG>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -283,41 +390,56 @@ bool plan_solve(int64_t n, int32_t eta, int num_sms, int grid_override, size_t s
   }
   P = std::max<int64_t>(1, std::min<int64_t>(P, std::min<int64_t>(num_sms, n4)));
   const int64_t w4max = (n4 + P - 1) / P;
-  int cpl = 1;
-  if (w4max > 32) cpl = 2;
-  if (w4max > 64) cpl = 4;
-  if (w4max > 128) cpl = 8;
-  if (w4max > 256) return false;
+  if (w4max > kSolveThreads / 2) return false;
   const size_t fixed = fixed_smem((int)w4max, eta) + 1024;
-  if (fixed > smem_optin) return false;
-  int64_t rows = (int64_t)((smem_optin - fixed) / ((size_t)w4max * 16));
-  rows = std::min<int64_t>(rows, eta);
+  if (fixed + 16 * (size_t)kSolveThreads > smem_optin) return false;
+  const int tile_cap = (int)((smem_optin - fixed) / 16);
+  // row steps of the widest CTA beyond shared memory decide the register part
+  const int64_t RGw = kSolveThreads / w4max;
+  const int64_t NI = (eta + RGw - 1) / RGw;
+  const int64_t IS = tile_cap / (RGw * w4max);
   g->grid = (int)P;
   g->w4max = (int)w4max;
-  g->cpl = cpl;
-  g->rows_res = (int)rows;
-  g->smem = fixed_smem((int)w4max, eta) + (size_t)rows * w4max * 16;
+  g->tile_cap = tile_cap;
+  g->rreg = (NI > IS) ? kSolveRegRows : 0;
+  g->rows_res = (int)std::min<int64_t>(eta, (IS + g->rreg) * RGw);
+  g->smem = fixed_smem((int)w4max, eta) + (size_t)tile_cap * 16;
   return true;
+}
+
+cudaError_t launch_presample(const SolveArgs& a, cudaStream_t s) {
+  const int64_t total = a.K * ((a.eta + 1) / 2);
+  if (total <= 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  presample_kernel<<<(unsigned)blocks, 256, 0, s>>>(
+      a.thr, a.alias, (uint32_t)a.m, a.seed, a.problem, a.kdev, a.K, a.eta, (a.eta + 3) & ~3,
+      a.b, a.inv_nu, const_cast<int32_t*>(a.tidx), const_cast<float*>(a.tb),
+      const_cast<float*>(a.tiv), a.stop);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_solve(const SolveArgs& a, const SolveGeometry& g, cudaStream_t s) {
   cudaError_t e;
   void* fn = nullptr;
-  switch (g.cpl) {
-    case 1: e = set_smem_attr<1>(g.smem); fn = (void*)rska_persistent_kernel<1>; break;
-    case 2: e = set_smem_attr<2>(g.smem); fn = (void*)rska_persistent_kernel<2>; break;
-    case 4: e = set_smem_attr<4>(g.smem); fn = (void*)rska_persistent_kernel<4>; break;
-    default: e = set_smem_attr<8>(g.smem); fn = (void*)rska_persistent_kernel<8>; break;
+  if (g.rreg > 0) {
+    e = set_smem_attr<kSolveRegRows>(g.smem);
+    fn = (void*)rska_persistent_kernel<kSolveRegRows>;
+  } else {
+    e = set_smem_attr<0>(g.smem);
+    fn = (void*)rska_persistent_kernel<0>;
   }
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(a.racc, 0, sizeof(float) * 3 * (size_t)a.eta, s);
+  e = launch_presample(a, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.racc, 0, sizeof(float) * 3 * (size_t)a.eta * kAccStride, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   SolveArgs args = a;
   int w4max = g.w4max;
-  int rows_res = g.rows_res;
-  void* params[] = {&args, &w4max, &rows_res};
+  int tile_cap = g.tile_cap;
+  void* params[] = {&args, &w4max, &tile_cap};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)g.grid);
   cfg.blockDim = dim3(NT);

@@ -12,7 +12,7 @@ import torch
 
 from ._lib import check, lib
 
-QUERY = {"grid": 0, "threads": 1, "rows_resident": 2, "w4max": 3, "smem": 4}
+QUERY = {"grid": 0, "threads": 1, "rows_resident": 2, "w4max": 3, "smem": 4, "rreg": 5}
 OPTION = {"grid": 0, "watchdog_us": 1}
 
 
