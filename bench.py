@@ -353,6 +353,28 @@ def run_gpu(args):
                "iterations": iters, "ms": tt_s * 1000.0, "rel_err": err,
                "check_every": 100}
 
+    # batch-size sweep of the same system (the eta axis of Sec. 5.2 at scale)
+    sweep = None
+    if not args.skip_sweep:
+        sweep = []
+        for eta_s in (1, 16, 64, 256, 1024):
+            K_s = {1: 4000, 16: 4000, 64: 2000, 256: 800, 1024: 300}[eta_s]
+            with Solver(A, b, LAM, eta_s, alpha_star_mp(M, N, eta_s), SEED, n=N,
+                        stream=stream) as ss:
+                ss.solve(min(200, K_s))
+                q0 = torch.cuda.Event(enable_timing=True)
+                q1 = torch.cuda.Event(enable_timing=True)
+                q0.record(stream)
+                ss.solve(K_s)
+                q1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = q0.elapsed_time(q1)
+                us_it = 1000.0 * ms / K_s
+                gbs = K_s * eta_s * (4.0 * N + 12.0) / (ms / 1000.0) / 1e9
+                sweep.append({"eta": eta_s, "us_per_iter": us_it,
+                              "row_updates_per_s": eta_s * K_s / (ms / 1000.0),
+                              "hbm_frac": gbs / hbm_peak})
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         rate, iters, el, _ = oracle_rate(prob, seconds=args.ref_seconds, max_iters=ITERS)
@@ -370,7 +392,7 @@ def run_gpu(args):
                 "clocks": clk, "gpu_launches": 2 * args.steps,
                 "accuracy": {"rel_residual": rel_res, "rel_error": rel_err,
                              "after_iterations": ITERS},
-                "plain_rska_gpu": plain, "time_to_accuracy": tta}
+                "plain_rska_gpu": plain, "time_to_accuracy": tta, "eta_sweep": sweep}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -387,6 +409,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-tta", action="store_true")
+    ap.add_argument("--skip-sweep", action="store_true")
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
                     help="kernel: only the timed persistent-kernel steps (for profiling)")
     ap.add_argument("--iters", type=int, default=None,
@@ -397,6 +420,7 @@ def main():
         ITERS = args.iters
     if args.mode == "kernel":
         args.skip_cpu = args.skip_plain = args.skip_tta = args.skip_e2e = True
+        args.skip_sweep = True
     else:
         args.skip_e2e = False
     if args.impl == "reference":

@@ -11,6 +11,7 @@ namespace rska {
 constexpr int kSolveThreads = 512;      // threads per CTA of the persistent solver
 constexpr int kMaxEta = 4096;           // largest batch size eta
 constexpr int kSolveRegRows = 12;       // row steps a thread may hold in registers
+constexpr int kDotBatch = 6;           // row steps whose partial dots are reduced together
 constexpr int kAccStride = 32;          // floats between two rows' dot accumulators (128 B)
 constexpr int64_t kPresampleDraws = 1 << 21;  // draws pre-sampled per launch (at most)
 

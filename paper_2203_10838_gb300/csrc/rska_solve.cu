@@ -10,17 +10,20 @@
 // the whole iteration.
 //
 // One iteration k:
-//   1. the CTA's slice of the eta sampled rows is fetched once from HBM:
-//      the first rows with cp.async into shared memory (four commit groups, so
-//      the dots start while later groups are in flight), the next ones into
-//      registers, anything beyond on-chip capacity is streamed (and fetched
-//      again in step 4);
-//   2. each thread forms a_ij * x_j for its elements; a segmented warp scan
-//      sums the lanes of one row, shared atomics finish the CTA's partial dot,
-//      and one global atomic per row adds it to a padded accumulator;
+//   1. the CTA's slice of the eta sampled rows is fetched once from HBM: the
+//      first row steps with cp.async into shared memory (one commit group per
+//      batch of kDotBatch row steps, so the dots start while later batches are
+//      in flight), the next ones into registers; anything beyond on-chip
+//      capacity is streamed and fetched again in step 4;
+//   2. each thread forms <a_s, x> over its float4 column for a batch of row
+//      steps into a shared buffer; the batch's rows are then summed across the
+//      slice by a few threads each (a shuffle finishes them) and one global
+//      atomic per row adds the CTA's partial dot to a padded accumulator;
 //   3. grid barrier (bounded wait);  c_s = (t/eta)(<a_s, x_k> - b_s)/||a_s||^2;
 //   4. z_j -= sum_s c_s a_sj from the on-chip rows, reduced over the row
-//      groups of each column, then x_j = S_lambda(z_j).
+//      groups of each column, then x_j = S_lambda(z_j).  As each on-chip slot
+//      is consumed it is refilled with the row of tau_{k+1}, so HBM streams
+//      the next iteration while this one finishes.
 // tau_{k}, b_{tau} and 1/||a_tau||^2 come from a pre-sampler kernel that draws
 // the whole launch's indices in parallel; the persistent kernel copies them
 // one iteration ahead, so no dependent gather sits on the critical path.  The
@@ -80,19 +83,6 @@ __device__ __forceinline__ float4 ldg_stream(const float4* p) {
   return v;
 }
 
-// Inclusive sum over the lanes of this thread's segment that precede it in
-// the warp; the segment's last lane in the warp ends with the segment total.
-__device__ __forceinline__ float seg_scan(float v, int lane, int segstart, int dmax) {
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    if (d < dmax) {
-      const float u = __shfl_up_sync(0xffffffffu, v, d);
-      if (lane - d >= segstart) v += u;
-    }
-  }
-  return v;
-}
-
 // ---------------------------------------------------------------------------
 // Pre-sampler: tau_k, b_{tau_k}, 1/||a_{tau_k}||^2 for k = k0 .. k0+K-1, with
 // k0 read from the device iteration counter.  Row j of each output (stride
@@ -127,17 +117,33 @@ __global__ void presample_kernel(const uint32_t* __restrict__ thr, const int32_t
   }
 }
 
+// cp.async.wait_group with a run-time count of groups allowed to stay pending.
+__device__ __forceinline__ void cp_async_wait_dyn(int pending) {
+  switch (pending) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;
+    case 7: cp_async_wait<7>(); break;
+    case 8: cp_async_wait<8>(); break;
+    case 9: cp_async_wait<9>(); break;
+    default: cp_async_wait<10>(); break;
+  }
+}
+
 template <int RREG>
 __global__ void __launch_bounds__(NT, 1)
     rska_persistent_kernel(SolveArgs a, int w4max, int tile_cap) {
+  constexpr int B = kDotBatch;  // row steps reduced together
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
 
   if (a.stop != nullptr && ld_relaxed_s32(a.stop) != 0) return;
 
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int warp = tid >> 5;
   const int P = gridDim.x;
   const int eta = a.eta;
   const int eta4 = (eta + 3) & ~3;
@@ -156,16 +162,18 @@ __global__ void __launch_bounds__(NT, 1)
   const int NI = (eta + RG - 1) / RG;        // row steps
   const int IS = tile_cap / NTa;             // row steps held in shared memory
   const int nIs = min(IS, NI);
-  const int segstart = max(rg * w4 - warp * 32, 0);
-  const int seglast = min((rg + 1) * w4 - 1 - warp * 32, 31);
-  const int dmax = min(w4, 32);
+  const int nbs = (nIs + B - 1) / B;         // shared-memory batches (one cp.async group each)
   const bool tailc = active && ((cb + c) * 4 + 4 > a.n);
+  // batch reduction layout: Q threads per row
+  int Q = 1;
+  while (Q < 32 && 2 * Q * B * RG <= NT) Q <<= 1;
 
   float4* tile = reinterpret_cast<float4*>(smem);                  // tile_cap
   float4* zs = tile + tile_cap;                                    // w4max
   float4* xs = zs + w4max;                                         // w4max
-  float4* red = xs + w4max;                                        // NT
-  int32_t* sidx = reinterpret_cast<int32_t*>(red + NT);            // 2 x eta4
+  float* ptile = reinterpret_cast<float*>(xs + w4max);             // B x NT (aliased by red)
+  float4* red = reinterpret_cast<float4*>(ptile);                  // NT (scatter phase)
+  int32_t* sidx = reinterpret_cast<int32_t*>(ptile + (size_t)B * NT);  // 2 x eta4
   float* sb = reinterpret_cast<float*>(sidx + 2 * eta4);           // eta4
   float* siv = sb + eta4;                                          // eta4
   float* cs = siv + eta4;                                          // eta4
@@ -180,7 +188,6 @@ __global__ void __launch_bounds__(NT, 1)
       zs[q] = zv;
       xs[q] = mask_tail(soft_shrink4(zv, lam), cb + q, a.n);
     }
-    for (int s = tid; s < eta4; s += NT) sdot[s] = 0.f;
     for (int q = tid; q < eta4 / 4; q += NT) cp_async16(sidx + 4 * q, a.tidx + 4 * q);
     cp_async_commit();
     cp_async_wait<0>();
@@ -189,42 +196,46 @@ __global__ void __launch_bounds__(NT, 1)
 
   const float* Ab = a.A + cb * 4 + (active ? c : 0) * 4;
   const int64_t lda = a.lda;
-  const int g1 = nIs / 4, g2 = nIs / 2, g3 = (3 * nIs) / 4;
+  auto row_ptr = [&](const int32_t* I, int s) {
+    return reinterpret_cast<const float4*>(Ab + (int64_t)I[s] * lda);
+  };
+
+  // fetch of the first iteration's rows (later iterations are fetched during
+  // the previous iteration's update phase)
+  float4 rv[RREG > 0 ? RREG : 1];
+  for (int b = 0; b < nbs; ++b) {
+    if (active) {
+      const int iend = min(nIs, (b + 1) * B);
+      for (int i = b * B; i < iend; ++i) {
+        const int s = rg + RG * i;
+        if (s < eta) cp_async16(tile + (size_t)i * NTa + tid, row_ptr(sidx, s));
+      }
+    }
+    cp_async_commit();
+  }
+#pragma unroll
+  for (int r = 0; r < RREG; ++r) {
+    const int i = IS + r;
+    const int s = rg + RG * i;
+    rv[r] = (active && i < NI && s < eta) ? ldg_stream(row_ptr(sidx, s))
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 
   for (int64_t j = 0; j < a.K; ++j) {
     const int cur = (int)(j & 1);
     const int32_t* I = sidx + cur * eta4;
+    const int32_t* In = sidx + (cur ^ 1) * eta4;
+    const bool more = (j + 1 < a.K);
     const float4 xc = active ? xs[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int buf = (int)(j % 3);
+    float* racc = a.racc + (size_t)buf * eta * kAccStride;
 
-    // ---- 1. fetch this CTA's slice of the sampled rows ----
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i0 = (q == 0) ? 0 : (q == 1) ? g1 : (q == 2) ? g2 : g3;
-      const int i1 = (q == 0) ? g1 : (q == 1) ? g2 : (q == 2) ? g3 : nIs;
-      if (active) {
-        for (int i = i0; i < i1; ++i) {
-          const int s = rg + RG * i;
-          if (s < eta) cp_async16(tile + (size_t)i * NTa + tid, Ab + (int64_t)I[s] * lda);
-        }
-      }
-      cp_async_commit();
-    }
-    float4 rv[RREG > 0 ? RREG : 1];
-#pragma unroll
-    for (int r = 0; r < RREG; ++r) {
-      const int i = IS + r;
-      const int s = rg + RG * i;
-      rv[r] = (active && i < NI && s < eta)
-                  ? ldg_stream(reinterpret_cast<const float4*>(Ab + (int64_t)I[s] * lda))
-                  : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     {  // b, 1/||a||^2 of this iteration; tau of the next one
       const int nq = eta4 / 4;
       const int32_t* gi = a.tidx + (j + 1) * eta4;
       const float* gb = a.tb + j * eta4;
       const float* gv = a.tiv + j * eta4;
       int32_t* nidx = sidx + (cur ^ 1) * eta4;
-      const bool more = (j + 1 < a.K);
       for (int q = tid; q < 3 * nq; q += NT) {
         if (q < nq) {
           cp_async16(sb + 4 * q, gb + 4 * q);
@@ -237,58 +248,78 @@ __global__ void __launch_bounds__(NT, 1)
       cp_async_commit();
     }
 
-    // ---- 2. partial dots <a_s, x_k> over this CTA's columns ----
-    auto dot_step = [&](int i, float4 v) {
+    // ---- partial dots: products to ptile, then a per-batch row reduction ----
+    auto product = [&](int i, float4 v) -> float {
       const int s = rg + RG * i;
-      const bool valid = active && s < eta;
+      if (!(active && i < NI && s < eta)) return 0.f;
       if (tailc) v = mask_tail(v, cb + c, a.n);
-      float p = valid ? dot4(v, xc) : 0.f;
-      p = seg_scan(p, lane, segstart, dmax);
-      if (valid && lane == seglast) atomicAdd(sdot + s, p);
+      return dot4(v, xc);
     };
+    auto reduce_batch = [&](int ib) {
+      __syncthreads();
+      const int rows = B * RG;
+      for (int t0 = 0; t0 < rows * Q; t0 += NT) {
+        const int t = t0 + tid;
+        const int rl = t / Q;
+        const int part = t - rl * Q;
+        float sum = 0.f;
+        int s = eta;
+        if (rl < rows) {
+          const int u = rl / RG;
+          const int g = rl - u * RG;
+          s = g + RG * (ib + u);
+          const float* pr = ptile + (size_t)u * NT + g * w4;
+          for (int cc = part; cc < w4; cc += Q) sum += pr[cc];
+        }
+        for (int o = Q >> 1; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (part == 0 && rl < rows && ib + rl / RG < NI && s < eta) {
+          if (single)
+            sdot[s] = sum;
+          else
+            atomicAdd(racc + (size_t)s * kAccStride, sum);
+        }
+      }
+      __syncthreads();
+    };
+    for (int b = 0; b < nbs; ++b) {
+      cp_async_wait_dyn(nbs - b);  // this batch's group done; later ones + meta may pend
+      const int iend = min(nIs, (b + 1) * B);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q == 0) cp_async_wait<4>();
-      if (q == 1) cp_async_wait<3>();
-      if (q == 2) cp_async_wait<2>();
-      if (q == 3) cp_async_wait<1>();
-      const int i0 = (q == 0) ? 0 : (q == 1) ? g1 : (q == 2) ? g2 : g3;
-      const int i1 = (q == 0) ? g1 : (q == 1) ? g2 : (q == 2) ? g3 : nIs;
-      for (int i = i0; i < i1; ++i) dot_step(i, tile[(size_t)i * NTa + tid]);
+      for (int u = 0; u < B; ++u) {
+        const int i = b * B + u;
+        ptile[(size_t)u * NT + tid] = (i < iend) ? product(i, tile[(size_t)i * NTa + tid]) : 0.f;
+      }
+      reduce_batch(b * B);
     }
+    if (nIs < NI) {
 #pragma unroll
-    for (int r = 0; r < RREG; ++r)
-      if (IS + r < NI) dot_step(IS + r, rv[r]);
-    for (int i = IS + RREG; i < NI; i += 4) {  // beyond on-chip capacity
-      float4 sv[4];
+      for (int rb = 0; rb < RREG; rb += B) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int s = rg + RG * (i + u);
-        sv[u] = (active && i + u < NI && s < eta)
-                    ? __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)I[s] * lda))
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < B; ++u)
+          ptile[(size_t)u * NT + tid] = (rb + u < RREG) ? product(IS + rb + u, rv[rb + u]) : 0.f;
+        if (IS + rb < NI) reduce_batch(IS + rb);
       }
+      for (int ib = IS + RREG; ib < NI; ib += B) {  // beyond on-chip capacity
+        float4 sv[B];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (i + u < NI) dot_step(i + u, sv[u]);
+        for (int u = 0; u < B; ++u) {
+          const int i = ib + u;
+          const int s = rg + RG * i;
+          sv[u] = (active && i < NI && s < eta) ? __ldg(row_ptr(I, s))
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) ptile[(size_t)u * NT + tid] = product(ib + u, sv[u]);
+        reduce_batch(ib);
+      }
     }
-    __syncthreads();
-
-    const int buf = (int)(j % 3);
-    float* racc = a.racc + (size_t)buf * eta * kAccStride;
-    if (!single) {
-      for (int s = tid; s < eta; s += NT) {
-        atomicAdd(racc + (size_t)s * kAccStride, sdot[s]);
-        sdot[s] = 0.f;
-      }
-      if (blockIdx.x == 0) {
-        float* nxt = a.racc + (size_t)((j + 1) % 3) * eta * kAccStride;
-        for (int s = tid; s < eta; s += NT) nxt[(size_t)s * kAccStride] = 0.f;
-      }
+    if (!single && blockIdx.x == 0) {
+      float* nxt = a.racc + (size_t)((j + 1) % 3) * eta * kAccStride;
+      for (int s = tid; s < eta; s += NT) nxt[(size_t)s * kAccStride] = 0.f;
     }
     cp_async_wait<0>();
 
-    // ---- 3. exchange and coefficients ----
+    // ---- exchange and coefficients ----
     if (single) {
       __syncthreads();
     } else if (!grid_barrier(a.bar, (unsigned long long)(j + 1), a.status, a.limit_ns,
@@ -296,22 +327,16 @@ __global__ void __launch_bounds__(NT, 1)
       return;
     }
     for (int s = tid; s < eta; s += NT) {
-      float r;
-      if (single) {
-        r = sdot[s];
-        sdot[s] = 0.f;
-      } else {
-        r = __ldcg(racc + (size_t)s * kAccStride);
-      }
+      const float r = single ? sdot[s] : __ldcg(racc + (size_t)s * kAccStride);
       cs[s] = a.coef * ((r - sb[s]) * siv[s]);
     }
     __syncthreads();
 
-    // ---- 4. z_j -= sum_s c_s a_sj ----
+    // ---- z_j -= sum_s c_s a_sj; refill each slot with the next iteration's row ----
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto upd_step = [&](int i, float4 v) {
+    auto upd = [&](int i, float4 v) {
       const int s = rg + RG * i;
-      if (active && s < eta) {
+      if (active && i < NI && s < eta) {
         if (tailc) v = mask_tail(v, cb + c, a.n);
         const float cv = cs[s];
         acc.x = fmaf(cv, v.x, acc.x);
@@ -320,40 +345,63 @@ __global__ void __launch_bounds__(NT, 1)
         acc.w = fmaf(cv, v.w, acc.w);
       }
     };
-    for (int i = 0; i < nIs; ++i) upd_step(i, tile[(size_t)i * NTa + tid]);
+    for (int b = 0; b < nbs; ++b) {
+      const int iend = min(nIs, (b + 1) * B);
+      for (int i = b * B; i < iend; ++i) {
+        float4* slot = tile + (size_t)i * NTa + tid;
+        upd(i, *slot);
+        const int s = rg + RG * i;
+        if (more && active && s < eta) cp_async16(slot, row_ptr(In, s));
+      }
+      cp_async_commit();
+    }
 #pragma unroll
-    for (int r = 0; r < RREG; ++r)
-      if (IS + r < NI) upd_step(IS + r, rv[r]);
-    for (int i = IS + RREG; i < NI; i += 4) {
-      float4 sv[4];
+    for (int r = 0; r < RREG; ++r) {
+      const int i = IS + r;
+      upd(i, rv[r]);
+      const int s = rg + RG * i;
+      if (more && active && i < NI && s < eta) rv[r] = ldg_stream(row_ptr(In, s));
+    }
+    for (int ib = IS + RREG; ib < NI; ib += B) {
+      float4 sv[B];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int s = rg + RG * (i + u);
-        sv[u] = (active && i + u < NI && s < eta)
-                    ? __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)I[s] * lda))
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < B; ++u) {
+        const int i = ib + u;
+        const int s = rg + RG * i;
+        sv[u] = (active && i < NI && s < eta) ? __ldg(row_ptr(I, s))
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (i + u < NI) upd_step(i + u, sv[u]);
+      for (int u = 0; u < B; ++u) upd(ib + u, sv[u]);
     }
     red[tid] = acc;
     __syncthreads();
     {
+      // column sums over the RG row groups: 4 threads per float4 component
       const float* redf = reinterpret_cast<const float*>(red);
       float* zf = reinterpret_cast<float*>(zs);
       float* xf = reinterpret_cast<float*>(xs);
-      for (int e = tid; e < w4 * 4; e += NT) {
+      const int ncomp = w4 * 4;
+      for (int t0 = 0; t0 < ncomp * 4; t0 += NT) {
+        const int t = t0 + tid;
+        const int e = t >> 2;
+        const int part = t & 3;
         float sum = 0.f;
-        for (int g = 0; g < RG; ++g) sum += redf[(size_t)g * w4 * 4 + e];
-        const int64_t col = cb * 4 + e;
-        const float zv = (col < a.n) ? zf[e] - sum : 0.f;
-        zf[e] = zv;
-        xf[e] = soft_shrink(zv, lam);
+        if (e < ncomp)
+          for (int g = part; g < RG; g += 4) sum += redf[(size_t)g * w4 * 4 + e];
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (part == 0 && e < ncomp) {
+          const int64_t col = cb * 4 + e;
+          const float zv = (col < a.n) ? zf[e] - sum : 0.f;
+          zf[e] = zv;
+          xf[e] = soft_shrink(zv, lam);
+        }
       }
     }
     __syncthreads();
   }
+  cp_async_wait<0>();
 
   float4* zo = reinterpret_cast<float4*>(a.z);
   float4* xo = reinterpret_cast<float4*>(a.x);
@@ -366,7 +414,8 @@ __global__ void __launch_bounds__(NT, 1)
 
 size_t fixed_smem(int w4max, int eta) {
   const size_t eta4 = (size_t)((eta + 3) & ~3);
-  return (size_t)2 * w4max * 16 + (size_t)NT * 16 + 2 * eta4 * 4 + 4 * eta4 * 4;
+  const size_t ptile = std::max<size_t>((size_t)kDotBatch * NT * 4, (size_t)NT * 16);
+  return (size_t)2 * w4max * 16 + ptile + 2 * eta4 * 4 + 4 * eta4 * 4;
 }
 
 template <int RREG>
