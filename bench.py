@@ -292,7 +292,8 @@ def run_gpu(args):
     achieved = alg_bytes / avg_launch_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": committed_traffic(),
-            "peak_kind": f"{peak_kind} (copy bandwidth)", "kernel": "rska_persistent_kernel",
+            "peak_kind": f"{peak_kind} (copy bandwidth)",
+            "kernel": "rska_rows_kernel" if sol.query("kernel") == 2 else "rska_persistent_kernel",
             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1000.0,
             "grid": sol.query("grid"), "rows_resident": sol.query("rows_resident")}
 
@@ -357,10 +358,12 @@ def run_gpu(args):
     sweep = None
     if not args.skip_sweep:
         sweep = []
-        for eta_s in (1, 16, 64, 256, 1024):
+        from paper_2203_10838_gb300.rska import KERNEL
+        for eta_s, kern in [(e, k) for e in (1, 16, 64, 256, 1024) for k in ("rows", "column")]:
             K_s = {1: 4000, 16: 4000, 64: 2000, 256: 800, 1024: 300}[eta_s]
             with Solver(A, b, LAM, eta_s, alpha_star_mp(M, N, eta_s), SEED, n=N,
                         stream=stream) as ss:
+                ss.set_option("kernel", KERNEL[kern])
                 ss.solve(min(200, K_s))
                 q0 = torch.cuda.Event(enable_timing=True)
                 q1 = torch.cuda.Event(enable_timing=True)
@@ -371,7 +374,8 @@ def run_gpu(args):
                 ms = q0.elapsed_time(q1)
                 us_it = 1000.0 * ms / K_s
                 gbs = K_s * eta_s * (4.0 * N + 12.0) / (ms / 1000.0) / 1e9
-                sweep.append({"eta": eta_s, "us_per_iter": us_it,
+                sweep.append({"eta": eta_s, "kernel": kern, "grid": ss.query("grid"),
+                              "us_per_iter": us_it,
                               "row_updates_per_s": eta_s * K_s / (ms / 1000.0),
                               "hbm_frac": gbs / hbm_peak})
 

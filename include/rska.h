@@ -158,6 +158,8 @@ int rska_destroy(rska_ctx *ctx);
  *          4: dynamic shared memory bytes per CTA
  *          5: row steps per thread held in registers (0 when the shared
  *             memory tile holds all of tau_k)
+ *          6: solver kernel in use: 1 column-split, 2 row-split
+ * Items 2, 3 and 5 describe the column-split kernel.
  */
 int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
 
@@ -166,6 +168,11 @@ int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
  *   what = 0: CTAs in the persistent grid (0 = automatic)
  *          1: watchdog limit of each device-side wait, in microseconds
  *             (default 2,000,000)
+ *          2: solver kernel: 0 automatic (row-split when n <= 10240, else
+ *             column-split), 1 column-split, 2 row-split
+ * The row-split kernel gives each CTA whole rows of tau_k (TMA bulk copies)
+ * and exchanges one n-vector per iteration; the column-split kernel gives
+ * each CTA a slice of every row and exchanges eta dots per iteration.
  */
 int rska_set_option(rska_ctx *ctx, int what, int64_t value);
 

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "rska_internal.h"
@@ -73,9 +74,26 @@ int plan(Ctx* c) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   if (e != cudaSuccess) return cuda_fail(c, e);
-  if (!rska::plan_solve(c->n, c->eta, c->num_sms, c->grid_override, (size_t)optin, &c->geom))
-    return RSKA_EUNSUPPORTED;
+  const bool col_ok =
+      rska::plan_solve(c->n, c->eta, c->num_sms, c->grid_override, (size_t)optin, &c->geom);
+  const bool rows_ok =
+      rska::plan_rows(c->n, c->eta, c->num_sms, c->grid_override, (size_t)optin, &c->rgeom);
+  if (c->kernel_choice == 1) {
+    if (!col_ok) return RSKA_EUNSUPPORTED;
+    c->use_rows = false;
+  } else if (c->kernel_choice == 2) {
+    if (!rows_ok) return RSKA_EUNSUPPORTED;
+    c->use_rows = true;
+  } else {
+    if (!col_ok && !rows_ok) return RSKA_EUNSUPPORTED;
+    c->use_rows = rows_ok;
+  }
   return RSKA_OK;
+}
+
+cudaError_t launch_any(Ctx* c, const rska::SolveArgs& a) {
+  return c->use_rows ? rska::launch_rows(a, c->rgeom, c->stream)
+                     : rska::launch_solve(a, c->geom, c->stream);
 }
 
 rska::SolveArgs solve_args(Ctx* c, int64_t K, const int* stop) {
@@ -167,7 +185,8 @@ int rska_setup(rska_ctx** out, const float* A, int64_t m, int64_t n, int64_t lda
   if ((e = dalloc(&c->nu, m)) != cudaSuccess || (e = dalloc(&c->inv_nu, m)) != cudaSuccess ||
       (e = dalloc(&c->thr, m)) != cudaSuccess || (e = dalloc(&c->alias, m)) != cudaSuccess ||
       (e = dalloc(&c->z, np)) != cudaSuccess || (e = dalloc(&c->x, np)) != cudaSuccess ||
-      (e = dalloc(&c->racc, 3 * (size_t)eta * rska::kAccStride)) != cudaSuccess ||
+      (e = dalloc(&c->racc, 3 * std::max<size_t>((size_t)eta * rska::kAccStride, (size_t)np))) !=
+          cudaSuccess ||
       (e = dalloc(&c->bar, 1)) != cudaSuccess || (e = dalloc(&c->status, 1)) != cudaSuccess ||
       (e = dalloc(&c->kdev, 1)) != cudaSuccess || (e = dalloc(&c->stop, 1)) != cudaSuccess ||
       (e = dalloc(&c->macc, 8)) != cudaSuccess ||
@@ -217,7 +236,7 @@ int rska_solve(rska_ctx* h, int64_t K) {
   for (int64_t done = 0; done < K; done += c->chunk) {
     const int64_t Kc = (K - done < c->chunk) ? (K - done) : c->chunk;
     rska::SolveArgs a = solve_args(c, Kc, nullptr);
-    cudaError_t e = rska::launch_solve(a, c->geom, c->stream);
+    cudaError_t e = launch_any(c, a);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->k_host += Kc;
   }
@@ -235,15 +254,27 @@ int rska_solve_until(rska_ctx* h, int64_t max_iters, int64_t check_every, double
   int64_t* k_stop = reinterpret_cast<int64_t*>(c->macc + 6);
   if (e == cudaSuccess) e = cudaMemsetAsync(k_stop, 0xff, sizeof(int64_t), s);
   const int64_t step = (check_every < c->chunk) ? check_every : c->chunk;
-  for (int64_t done = 0; e == cudaSuccess && done < max_iters; done += step) {
-    const int64_t K = (max_iters - done < step) ? (max_iters - done) : step;
-    rska::SolveArgs a = solve_args(c, K, c->stop);
-    e = rska::launch_solve(a, c->geom, s);
-    if (e == cudaSuccess)
-      e = rska::launch_metrics(c->A, c->m, c->n, c->lda, c->b, c->z, c->lambda, xhat, c->macc,
-                               c->stop, s);
-    if (e == cudaSuccess)
-      e = rska::launch_metrics_finish(c->macc, xhat != nullptr, tol, c->stop, k_stop, c->kdev, s);
+  // Enqueue chunk + check pairs in waves; between waves read the stop flag,
+  // so a run that stops early does not pay for enqueueing the whole budget.
+  int64_t done = 0;
+  int64_t wave = 4;
+  int stopped = 0;
+  while (e == cudaSuccess && done < max_iters && !stopped) {
+    for (int64_t w = 0; w < wave && done < max_iters && e == cudaSuccess; ++w) {
+      const int64_t K = (max_iters - done < step) ? (max_iters - done) : step;
+      rska::SolveArgs a = solve_args(c, K, c->stop);
+      e = launch_any(c, a);
+      if (e == cudaSuccess)
+        e = rska::launch_metrics(c->A, c->m, c->n, c->lda, c->b, c->z, c->lambda, xhat, c->macc,
+                                 c->stop, s);
+      if (e == cudaSuccess)
+        e = rska::launch_metrics_finish(c->macc, xhat != nullptr, tol, c->stop, k_stop, c->kdev,
+                                        s);
+      done += K;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&stopped, c->stop, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (wave < 64) wave *= 2;
   }
   if (e != cudaSuccess) return cuda_fail(c, e);
   double res[2];
@@ -370,6 +401,7 @@ int rska_query(rska_ctx* h, int what, int64_t* value_out) {
     case 3: *value_out = g.w4max; return RSKA_OK;
     case 4: *value_out = (int64_t)g.smem; return RSKA_OK;
     case 5: *value_out = g.rreg; return RSKA_OK;
+    case 6: *value_out = h->c.use_rows ? 2 : 1; return RSKA_OK;
     default: return RSKA_EINVAL;
   }
 }
@@ -393,6 +425,17 @@ int rska_set_option(rska_ctx* h, int what, int64_t value) {
       if (value < 1) return RSKA_EINVAL;
       c->limit_ns = (uint64_t)value * 1000ull;
       return RSKA_OK;
+    case 2: {
+      if (value < 0 || value > 2) return RSKA_EINVAL;
+      const int old = c->kernel_choice;
+      c->kernel_choice = (int)value;
+      int rc = plan(c);
+      if (rc != RSKA_OK) {
+        c->kernel_choice = old;
+        plan(c);
+      }
+      return rc;
+    }
     default:
       return RSKA_EINVAL;
   }

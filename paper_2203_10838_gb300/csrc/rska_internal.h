@@ -14,6 +14,7 @@ constexpr int kSolveRegRows = 12;       // row steps a thread may hold in regist
 constexpr int kDotBatch = 6;           // row steps whose partial dots are reduced together
 constexpr int kAccStride = 32;          // floats between two rows' dot accumulators (128 B)
 constexpr int64_t kPresampleDraws = 1 << 21;  // draws pre-sampled per launch (at most)
+constexpr int kRowsMaxZ = 5;            // row-split kernel: float4 columns per thread (n <= 10240)
 
 // Launch geometry of the persistent single-system solver.
 struct SolveGeometry {
@@ -23,6 +24,15 @@ struct SolveGeometry {
   int rreg = 0;          // row steps held in registers (0 or kSolveRegRows)
   int rows_res = 0;      // rows of tau_k kept on chip by the widest CTA
   size_t smem = 0;       // dynamic shared memory per CTA
+};
+
+// Launch geometry of the row-split single-system solver.
+struct RowsGeometry {
+  int grid = 0;          // CTAs
+  int zreg = 0;          // float4 columns per thread
+  int slots = 0;         // shared-memory row slots of the TMA ring
+  int rowbytes_pad = 0;  // bytes per slot
+  size_t smem = 0;
 };
 
 struct SolveArgs {
@@ -87,6 +97,9 @@ struct Ctx {
   int grid_override = 0;
   uint64_t limit_ns = 2000000000ull;
   SolveGeometry geom;
+  RowsGeometry rgeom;
+  int kernel_choice = 0;       // 0 automatic, 1 column-split, 2 row-split
+  bool use_rows = false;
 };
 
 // launchers (return cudaError_t of the launch)
@@ -101,6 +114,10 @@ cudaError_t launch_indices(const uint32_t* thr, const int32_t* alias, int64_t m,
 bool plan_solve(int64_t n, int32_t eta, int num_sms, int grid_override, size_t smem_optin,
                 SolveGeometry* g);
 cudaError_t launch_solve(const SolveArgs& a, const SolveGeometry& g, cudaStream_t s);
+cudaError_t launch_presample(const SolveArgs& a, cudaStream_t s);
+bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t smem_optin,
+               RowsGeometry* g);
+cudaError_t launch_rows(const SolveArgs& a, const RowsGeometry& g, cudaStream_t s);
 cudaError_t launch_metrics(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
                            const float* z, float lambda, const float* xhat, double* acc,
                            const int* stop, cudaStream_t s);

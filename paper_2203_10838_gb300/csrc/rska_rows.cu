@@ -1,0 +1,424 @@
+// rska_rows.cu -- row-split persistent RSKA kernel (eq. rska, Algorithm 1 with
+// w_i = t) for n <= 4 * kSolveThreads * kRowsMaxZ.
+//
+// Work split.  Slot s of tau_k belongs to CTA s mod P, which reads the whole
+// row a_{tau_k(s)} (n floats, one TMA bulk copy into a ring of shared-memory
+// slots), forms <a_s, x_k> with a block reduction, the coefficient
+// c_s = (t/eta)(<a_s, x_k> - b_s)/||a_s||^2, and adds c_s a_s into its partial
+// update Delta_p (registers).  The only exchange per iteration is the sum of
+// the P partial updates: each CTA adds Delta_p into a global accumulator with
+// 16-byte vector reductions, passes one grid barrier, and reads the total
+// back; every CTA keeps a full copy of z = x^* (shared memory) and of
+// x = S_lambda(z) (registers) and applies z -= Delta, x = S_lambda(z) itself.
+//
+// Rows never wait across the barrier: a row is consumed as soon as it lands,
+// so the TMA producer (thread 0) refills freed slots with the rows of
+// iteration k+1 while iteration k is still in its exchange, and HBM keeps
+// streaming through the barrier.  tau_k, b_tau and 1/||a_tau||^2 come from the
+// pre-sampler.  Every device-side wait (mbarrier, grid barrier) is bounded.
+#include <algorithm>
+
+#include "rska_device.cuh"
+#include "rska_internal.h"
+
+namespace rska {
+
+namespace {
+
+constexpr int NT = kSolveThreads;
+constexpr int NWARPS = NT / 32;
+constexpr int G = 2;                 // rows reduced together
+constexpr int SLOTS_MAX = 8;
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float* p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+
+__device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
+  const int64_t base = gc * 4;
+  float4 r = v;
+  if (base + 0 >= n) r.x = 0.f;
+  if (base + 1 >= n) r.y = 0.f;
+  if (base + 2 >= n) r.z = 0.f;
+  if (base + 3 >= n) r.w = 0.f;
+  return r;
+}
+
+// Bounded wait on an mbarrier phase; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity,
+                                                  uint64_t limit_ns) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (!mbar_try_wait(b, parity)) {
+    if (global_timer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src_gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(su32(dst_smem)), "l"(src_gmem)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int ZREG>
+__global__ void __launch_bounds__(NT, 1)
+    rska_rows_kernel(SolveArgs a, int slots, int rowbytes_pad) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[SLOTS_MAX];
+  __shared__ float wpart[2][NWARPS][G];
+  __shared__ int s_flag;
+
+  if (a.stop != nullptr && ld_relaxed_s32(a.stop) != 0) return;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int P = gridDim.x;
+  const int p = blockIdx.x;
+  const int eta = a.eta;
+  const int eta4 = (eta + 3) & ~3;
+  const int64_t n4 = (a.n + 3) >> 2;
+  const bool single = (P == 1);
+  const int rpi = (p < eta) ? (eta - p + P - 1) / P : 0;  // rows of tau_k owned per iteration
+  const uint32_t rowbytes = (uint32_t)(n4 * 16);
+
+  unsigned char* ring = smem;                                            // slots x rowbytes_pad
+  float4* zsh = reinterpret_cast<float4*>(smem + (size_t)slots * rowbytes_pad);  // ZREG x NT
+  int32_t* midx = reinterpret_cast<int32_t*>(zsh + (size_t)ZREG * NT);   // 3 x rpi
+  float* mb = reinterpret_cast<float*>(midx + 3 * rpi);
+  float* miv = mb + 3 * rpi;
+
+  const int64_t k0 = *a.kdev;
+  const float lam = a.lambda;
+  const float coef = a.coef;
+
+  // column ownership: float4 columns t + NT*r
+  float4 xr[ZREG];
+  float4 dl[ZREG];
+#pragma unroll
+  for (int r = 0; r < ZREG; ++r) {
+    const int64_t col = tid + (int64_t)NT * r;
+    float4 zv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (col < n4) zv = reinterpret_cast<const float4*>(a.z)[col];
+    zsh[(size_t)r * NT + tid] = zv;
+    xr[r] = (col < n4) ? mask_tail(soft_shrink4(zv, lam), col, a.n)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (tid == 0)
+    for (int i = 0; i < slots; ++i) mbar_init(&full[i], 1);
+  // metadata of iterations 0 and 1
+  for (int e = tid; e < 2 * rpi; e += NT) {
+    const int jj = e / rpi, q = e - jj * rpi;
+    if (jj < a.K) {
+      const int64_t o = (int64_t)jj * eta4 + p + (int64_t)P * q;
+      midx[jj * rpi + q] = a.tidx[o];
+      mb[jj * rpi + q] = a.tb[o];
+      miv[jj * rpi + q] = a.tiv[o];
+    }
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+
+  // producer state (thread 0) and consumer state (all threads)
+  const int64_t total_rows = (int64_t)rpi * a.K;
+  int64_t prod = 0;        // rows issued
+  int64_t cons = 0;        // rows consumed
+  uint32_t parity_bits = 0;  // per-slot phase parity
+  int gcount = 0;            // groups consumed (selects the wpart buffer)
+  const float* Abase = a.A;
+  const int64_t lda = a.lda;
+  // issue rows while slots are free and the row's iteration is <= jmax
+  auto produce = [&](int64_t jmax) {
+    if (tid != 0) return;
+    while (prod < total_rows && prod - cons < slots) {
+      const int64_t jj = prod / rpi;
+      if (jj > jmax) break;
+      const int q = (int)(prod - jj * rpi);
+      const int sl = (int)(prod % slots);
+      const int32_t row = midx[(jj % 3) * rpi + q];
+      mbar_expect_tx(&full[sl], rowbytes);
+      tma_load_1d(ring + (size_t)sl * rowbytes_pad, Abase + (int64_t)row * lda, rowbytes,
+                  &full[sl]);
+      ++prod;
+    }
+  };
+  // on an error exit: let every issued copy land before shared memory goes away
+  auto drain = [&]() {
+    if (tid == 0) {
+      for (int64_t g = cons; g < prod; ++g) {
+        const int sl = (int)(g % slots);
+        mbar_wait_bounded(&full[sl], (parity_bits >> sl) & 1u, a.limit_ns);
+        parity_bits ^= (1u << sl);
+      }
+    }
+    __syncthreads();
+  };
+  produce(1);
+
+  for (int64_t j = 0; j < a.K; ++j) {
+    const int mcur = (int)(j % 3);
+    // metadata of iteration j+2 (used from the next iteration on)
+    if (j + 2 < a.K) {
+      const int ms = (int)((j + 2) % 3);
+      for (int q = tid; q < rpi; q += NT) {
+        const int64_t o = (j + 2) * eta4 + p + (int64_t)P * q;
+        cp_async4(midx + ms * rpi + q, a.tidx + o);
+        cp_async4(mb + ms * rpi + q, a.tb + o);
+        cp_async4(miv + ms * rpi + q, a.tiv + o);
+      }
+    }
+    cp_async_commit();
+    produce(j + 1);
+
+    // ---- this CTA's rows of tau_k: dots, coefficients, partial update ----
+    for (int q0 = 0; q0 < rpi; q0 += G) {
+      const int ng = min(G, rpi - q0);
+      float4 av[G][ZREG];
+      float pd[G];
+      bool tmo = false;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        pd[g] = 0.f;
+        if (g < ng) {
+          const int sl = (int)((cons + g) % slots);
+          const uint32_t par = (parity_bits >> sl) & 1u;
+          if (!mbar_wait_bounded(&full[sl], par, a.limit_ns)) tmo = true;
+          const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
+#pragma unroll
+          for (int r = 0; r < ZREG; ++r) {
+            const int64_t col = tid + (int64_t)NT * r;
+            float4 v = (col < n4) ? rowp[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col == n4 - 1) v = mask_tail(v, col, a.n);
+            av[g][r] = v;
+            pd[g] += dot4(v, xr[r]);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < ZREG; ++r) av[g][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) pd[g] += __shfl_xor_sync(0xffffffffu, pd[g], o);
+      }
+      const int wp = gcount & 1;
+      ++gcount;
+      if (lane == 0) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) wpart[wp][warp][g] = pd[g];
+      }
+      if (__syncthreads_or(tmo)) {
+        if (tid == 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        drain();
+        return;
+      }
+      // the group's slots are free: advance the consumer, refill
+      for (int g = 0; g < ng; ++g) parity_bits ^= (1u << (int)((cons + g) % slots));
+      cons += ng;
+      produce(j + 1);
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        if (g < ng) {
+          float d = 0.f;
+#pragma unroll
+          for (int w = 0; w < NWARPS; ++w) d += wpart[wp][w][g];
+          const int q = q0 + g;
+          const float cval = coef * ((d - mb[mcur * rpi + q]) * miv[mcur * rpi + q]);
+#pragma unroll
+          for (int r = 0; r < ZREG; ++r) {
+            dl[r].x = fmaf(cval, av[g][r].x, dl[r].x);
+            dl[r].y = fmaf(cval, av[g][r].y, dl[r].y);
+            dl[r].z = fmaf(cval, av[g][r].z, dl[r].z);
+            dl[r].w = fmaf(cval, av[g][r].w, dl[r].w);
+          }
+        }
+      }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+
+    // ---- exchange: Delta = sum_p Delta_p ----
+    if (single) {
+#pragma unroll
+      for (int r = 0; r < ZREG; ++r) {
+        const int64_t col = tid + (int64_t)NT * r;
+        if (col < n4) {
+          float4 zv = zsh[(size_t)r * NT + tid];
+          zv.x -= dl[r].x;
+          zv.y -= dl[r].y;
+          zv.z -= dl[r].z;
+          zv.w -= dl[r].w;
+          zv = mask_tail(zv, col, a.n);
+          zsh[(size_t)r * NT + tid] = zv;
+          xr[r] = soft_shrink4(zv, lam);
+        }
+        dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncthreads();
+      continue;
+    }
+    const int buf = (int)(j % 3);
+    float* dacc = a.racc + (size_t)buf * n4 * 4;
+#pragma unroll
+    for (int r = 0; r < ZREG; ++r) {
+      const int64_t col = tid + (int64_t)NT * r;
+      if (rpi > 0 && col < n4) red_add_v4(dacc + col * 4, dl[r]);
+      dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (p == 0) {
+      float4* nxt = reinterpret_cast<float4*>(a.racc + (size_t)((j + 1) % 3) * n4 * 4);
+      for (int64_t col = tid; col < n4; col += NT) nxt[col] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (!grid_barrier(a.bar, (unsigned long long)(j + 1), a.status, a.limit_ns, &s_flag)) {
+      drain();
+      return;
+    }
+    produce(j + 1);
+    const float4* dtot = reinterpret_cast<const float4*>(dacc);
+#pragma unroll
+    for (int r = 0; r < ZREG; ++r) {
+      const int64_t col = tid + (int64_t)NT * r;
+      if (col < n4) {
+        const float4 d = __ldcg(dtot + col);
+        float4 zv = zsh[(size_t)r * NT + tid];
+        zv.x -= d.x;
+        zv.y -= d.y;
+        zv.z -= d.z;
+        zv.w -= d.w;
+        zv = mask_tail(zv, col, a.n);
+        zsh[(size_t)r * NT + tid] = zv;
+        xr[r] = soft_shrink4(zv, lam);
+      }
+    }
+  }
+
+  if (p == 0) {
+    float4* zo = reinterpret_cast<float4*>(a.z);
+    float4* xo = reinterpret_cast<float4*>(a.x);
+#pragma unroll
+    for (int r = 0; r < ZREG; ++r) {
+      const int64_t col = tid + (int64_t)NT * r;
+      if (col < n4) {
+        zo[col] = zsh[(size_t)r * NT + tid];
+        xo[col] = xr[r];
+      }
+    }
+    if (tid == 0) *a.kdev = k0 + a.K;
+  }
+}
+
+template <int ZREG>
+cudaError_t launch_rows_t(const SolveArgs& a, const RowsGeometry& g, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(rska_rows_kernel<ZREG>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+  if (e != cudaSuccess) return e;
+  SolveArgs args = a;
+  int slots = g.slots;
+  int rbp = g.rowbytes_pad;
+  void* params[] = {&args, &slots, &rbp};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = g.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, (void*)rska_rows_kernel<ZREG>, params);
+}
+
+}  // namespace
+
+bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t smem_optin,
+               RowsGeometry* g) {
+  const int64_t n4 = (n + 3) / 4;
+  const int64_t zreg = (n4 + NT - 1) / NT;
+  if (zreg > kRowsMaxZ) return false;
+  const int z = (int)std::max<int64_t>(1, zreg);
+  // Small iterations (all of tau_k within ~128 KB) run on one CTA: no grid
+  // barrier at all; otherwise one CTA per SM up to one row per CTA.
+  const int64_t iter_bytes = (int64_t)eta * n4 * 16;
+  int64_t P = grid_override > 0 ? grid_override
+                                : (iter_bytes <= (128 << 10) ? 1 : std::min<int64_t>(num_sms, eta));
+  P = std::max<int64_t>(1, std::min<int64_t>(P, num_sms));
+  const int64_t rpi = (eta + P - 1) / P;
+  const int64_t rowbytes = n4 * 16;
+  const int64_t rowbytes_pad = (rowbytes + 127) / 128 * 128;
+  const size_t fixed = (size_t)z * NT * 16 + (size_t)3 * rpi * 12 + 2048;
+  if (fixed + 2 * rowbytes_pad > smem_optin) return false;
+  int64_t slots = (int64_t)((smem_optin - fixed) / rowbytes_pad);
+  slots = std::min<int64_t>(slots, SLOTS_MAX);
+  if (slots < 2) return false;
+  g->grid = (int)P;
+  g->zreg = z;
+  g->slots = (int)slots;
+  g->rowbytes_pad = (int)rowbytes_pad;
+  g->smem = (size_t)slots * rowbytes_pad + (size_t)z * NT * 16 + (size_t)3 * rpi * 12;
+  return true;
+}
+
+cudaError_t launch_rows(const SolveArgs& a, const RowsGeometry& g, cudaStream_t s) {
+  cudaError_t e = launch_presample(a, s);
+  if (e != cudaSuccess) return e;
+  const int64_t n4 = (a.n + 3) / 4;
+  e = cudaMemsetAsync(a.racc, 0, sizeof(float) * 3 * (size_t)n4 * 4, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  switch (g.zreg) {
+    case 1: return launch_rows_t<1>(a, g, s);
+    case 2: return launch_rows_t<2>(a, g, s);
+    case 3: return launch_rows_t<3>(a, g, s);
+    case 4: return launch_rows_t<4>(a, g, s);
+    default: return launch_rows_t<5>(a, g, s);
+  }
+}
+
+}  // namespace rska

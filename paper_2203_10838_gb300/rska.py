@@ -12,8 +12,10 @@ import torch
 
 from ._lib import check, lib
 
-QUERY = {"grid": 0, "threads": 1, "rows_resident": 2, "w4max": 3, "smem": 4, "rreg": 5}
-OPTION = {"grid": 0, "watchdog_us": 1}
+QUERY = {"grid": 0, "threads": 1, "rows_resident": 2, "w4max": 3, "smem": 4, "rreg": 5,
+         "kernel": 6}
+OPTION = {"grid": 0, "watchdog_us": 1, "kernel": 2}
+KERNEL = {"auto": 0, "column": 1, "rows": 2}
 
 
 def _stream_ptr(stream) -> ctypes.c_void_p:

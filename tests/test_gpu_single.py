@@ -40,20 +40,23 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def run_case(env, m, n, s, eta, lam, t, seed, K, grid=None, noise=0.0, pseed=None):
+def run_case(env, m, n, s, eta, lam, t, seed, K, grid=None, noise=0.0, pseed=None,
+             kernel="auto"):
     torch, orc, Solver = env
+    from paper_2203_10838_gb300.rska import KERNEL
     prob = gaussian_problem(m, n, s, seed=pseed if pseed is not None else 1000 + seed,
                             noise=noise)
     A = torch.from_numpy(prob.A).cuda()
     b = torch.from_numpy(prob.b).cuda()
     sol = Solver(A, b, lam, eta, t, seed, n=n)
+    sol.set_option("kernel", KERNEL[kernel])
     if grid is not None:
         sol.set_option("grid", grid)
     nu_g, thr_g, alias_g = [v.cpu().numpy() for v in sol.get_tables()]
     sol.solve(K)
     x, z = [v.cpu().numpy().astype(np.float64) for v in sol.get_x()]
     idx = sol.get_indices(0, K).cpu().numpy()
-    info = {k: sol.query(k) for k in ("grid", "rows_resident", "w4max")}
+    info = {k: sol.query(k) for k in ("grid", "rows_resident", "w4max", "kernel")}
     sol.close()
     An = prob.A[:, :n]
     nu = orc.row_norms(An)
@@ -81,21 +84,34 @@ CASES = {
 }
 
 
+ROWS_OK = {k for k, v in CASES.items() if v[1] <= 10240}
+
+
+@pytest.mark.parametrize("kernel", ["column", "rows"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_parity_against_oracle(env, name):
+def test_parity_against_oracle(env, name, kernel):
+    if kernel == "rows" and name not in ROWS_OK:
+        pytest.skip("row-split kernel covers n <= 10240")
     m, n, s, eta, lam, t, seed, K, grid, noise = CASES[name]
-    rx, rz, info = run_case(env, m, n, s, eta, lam, t, seed, K, grid=grid, noise=noise)
+    rx, rz, info = run_case(env, m, n, s, eta, lam, t, seed, K, grid=grid, noise=noise,
+                            kernel=kernel)
+    assert info["kernel"] == (2 if kernel == "rows" else 1)
     assert rx <= REL_TOL and rz <= REL_TOL, (name, rx, rz, info)
 
 
-def test_parity_full_size_bench_configuration(env):
+@pytest.mark.parametrize("kernel", ["auto", "column"])
+def test_parity_full_size_bench_configuration(env, kernel):
     """A 20000 x 10000 Gaussian system, 200 nonzeros, 1% noise, lambda = 2,
-    eta = 1024, t = alpha^*(eta): the launch configuration the benchmark times,
-    checked over the first 30 iterations, indices bit-exact."""
+    eta = 1024, t = alpha^*(eta): the launch configuration the benchmark times
+    (automatic choice: the row-split kernel), checked over the first 30
+    iterations, indices bit-exact."""
     m, n, eta = 20000, 10000, 1024
     t = float(alpha_star_mp(m, n, eta))
-    rx, rz, info = run_case(env, m, n, 200, eta, 2.0, t, 0, 30, noise=0.01, pseed=1001)
+    rx, rz, info = run_case(env, m, n, 200, eta, 2.0, t, 0, 30, noise=0.01, pseed=1001,
+                            kernel=kernel)
     assert info["grid"] > 1
+    if kernel == "auto":
+        assert info["kernel"] == 2
     assert rx <= REL_TOL and rz <= REL_TOL, (rx, rz, info)
 
 
