@@ -176,6 +176,32 @@ int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
  */
 int rska_set_option(rska_ctx *ctx, int what, int64_t value);
 
+/*
+ * rska_solve_noalloc -- one-shot solve that allocates no device memory.  The
+ * paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc while they run (an external memory budget or custom allocator
+ * that forbids it, or code that must not synchronize the device the way
+ * cudaMalloc/cudaFree may).
+ *   A, b, lambda, eta, t, seed  as for rska_setup (A, b device, read only).
+ *   K       iterations of Algorithm 1 from z_0 = 0 (K >= 0).
+ *   x_out   device, n floats: x_K = S_lambda(z_K) (may be NULL if z_out is set)
+ *   z_out   device, n floats: z_K (may be NULL if x_out is set)
+ * Results equal those of rska_setup + rska_solve(K) + rska_get_x within FP32
+ * reduction-order rounding (same index sequence).  All working memory lives
+ * in one 4 MiB file-scope device array that every GPU loading this library
+ * reserves until the process exits.  Limits: m <= 65536, n <= 16384 and
+ * eta <= 1024; larger problems return RSKA_EUNSUPPORTED.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress, once per device, under a lock), so make that first
+ * call before any stream capture.  Every call shares the one array and
+ * re-initializes it: calls whose work overlaps on the GPU (different streams
+ * or threads without ordering) race and corrupt each other's results.
+ * Synchronizes `stream`.  Errors: EINVAL, EUNSUPPORTED, EZEROROW, ENONFINITE,
+ * ECUDA, ETIMEOUT.
+ */
+int rska_solve_noalloc(const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
+                       float lambda, int32_t eta, float t, uint64_t seed, int64_t K,
+                       float *x_out, float *z_out, void *stream);
+
 /* rska_strerror -- static English text for a return code. */
 const char *rska_strerror(int code);
 

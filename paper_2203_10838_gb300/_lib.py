@@ -37,6 +37,7 @@ def _declare(lib):
         "rska_destroy": ([P], c_int),
         "rska_query": ([P, c_int, ctypes.POINTER(i64)], c_int),
         "rska_set_option": ([P, c_int, i64], c_int),
+        "rska_solve_noalloc": ([P, i64, i64, i64, P, f32, i32, f32, u64, i64, P, P, P], c_int),
         "rska_strerror": ([c_int], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():

@@ -152,3 +152,20 @@ def rska_get_x(solver: Solver):
 
 def rska_destroy(solver: Solver):
     solver.close()
+
+
+def rska_solve_noalloc(A: torch.Tensor, b: torch.Tensor, lam: float, eta: int, t: float,
+                       seed: int, K: int, n: int | None = None, stream=None):
+    """One-shot solve that allocates no device memory inside the library (its
+    working memory is a fixed device array); returns (x, z).  The output
+    tensors are allocated here by torch, before the call."""
+    if A.dtype != torch.float32 or b.dtype != torch.float32:
+        raise ValueError("A and b must be float32")
+    m, lda = A.shape
+    n = lda if n is None else int(n)
+    x = torch.empty(n, dtype=torch.float32, device=A.device)
+    z = torch.empty(n, dtype=torch.float32, device=A.device)
+    check(lib().rska_solve_noalloc(_dptr(A), m, n, lda, _dptr(b), float(lam), int(eta), float(t),
+                                   int(seed), int(K), _dptr(x), _dptr(z), _stream_ptr(stream)),
+          "rska_solve_noalloc")
+    return x, z
