@@ -11,11 +11,13 @@
 // back; every CTA keeps a full copy of z = x^* (shared memory) and of
 // x = S_lambda(z) (registers) and applies z -= Delta, x = S_lambda(z) itself.
 //
-// Rows never wait across the barrier: a row is consumed as soon as it lands,
-// so the TMA producer (thread 0) refills freed slots with the rows of
-// iteration k+1 while iteration k is still in its exchange, and HBM keeps
-// streaming through the barrier.  tau_k, b_tau and 1/||a_tau||^2 come from the
-// pre-sampler.  Every device-side wait (mbarrier, grid barrier) is bounded.
+// Ring discipline.  A warp releases a slot (empty mbarrier) the moment the
+// row is in its registers; thread 0 refills free slots without blocking at
+// every group boundary and inside the grid-barrier spin, so the ring stays
+// full also while the CTA is in the exchange: HBM streams the next
+// iteration's rows through the barrier.  tau, b and 1/||a||^2 of the next
+// iterations are copied from the pre-sampled arrays two iterations ahead.
+// Every device-side wait (full/empty mbarriers, grid barrier) is bounded.
 #include <algorithm>
 
 #include "rska_device.cuh"
@@ -25,10 +27,10 @@ namespace rska {
 
 namespace {
 
-constexpr int NT = kSolveThreads;
-constexpr int NWARPS = NT / 32;
+constexpr int NC = kSolveThreads;   // threads per CTA
+constexpr int NCW = NC / 32;         // warps per CTA
 constexpr int G = 2;                 // rows reduced together
-constexpr int SLOTS_MAX = 8;
+constexpr int SLOTS_MAX = 16;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -43,10 +45,26 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Non-blocking test of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(su32(b)), "r"(parity)
@@ -66,6 +84,11 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 __device__ __forceinline__ void red_add_v4(float* p, float4 v) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
                "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src_gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(su32(dst_smem)), "l"(src_gmem)
                : "memory");
 }
 
@@ -94,21 +117,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity,
   return true;
 }
 
-__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src_gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(su32(dst_smem)), "l"(src_gmem)
-               : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
 template <int ZREG>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NC, 1)
     rska_rows_kernel(SolveArgs a, int slots, int rowbytes_pad) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[SLOTS_MAX];
-  __shared__ float wpart[2][NWARPS][G];
+  __shared__ __align__(8) uint64_t empty[SLOTS_MAX];
+  __shared__ float wpart[2][NCW][G];
+  __shared__ float sb[SLOTS_MAX];
+  __shared__ float siv[SLOTS_MAX];
   __shared__ int s_flag;
 
   if (a.stop != nullptr && ld_relaxed_s32(a.stop) != 0) return;
@@ -124,10 +141,11 @@ __global__ void __launch_bounds__(NT, 1)
   const bool single = (P == 1);
   const int rpi = (p < eta) ? (eta - p + P - 1) / P : 0;  // rows of tau_k owned per iteration
   const uint32_t rowbytes = (uint32_t)(n4 * 16);
+  const int64_t total_rows = (int64_t)rpi * a.K;
 
-  unsigned char* ring = smem;                                            // slots x rowbytes_pad
-  float4* zsh = reinterpret_cast<float4*>(smem + (size_t)slots * rowbytes_pad);  // ZREG x NT
-  int32_t* midx = reinterpret_cast<int32_t*>(zsh + (size_t)ZREG * NT);   // 3 x rpi
+  unsigned char* ring = smem;                                                     // slots x rowbytes_pad
+  float4* zsh = reinterpret_cast<float4*>(smem + (size_t)slots * rowbytes_pad);  // ZREG x NC
+  int32_t* midx = reinterpret_cast<int32_t*>(zsh + (size_t)ZREG * NC);           // 3 x rpi
   float* mb = reinterpret_cast<float*>(midx + 3 * rpi);
   float* miv = mb + 3 * rpi;
 
@@ -135,23 +153,27 @@ __global__ void __launch_bounds__(NT, 1)
   const float lam = a.lambda;
   const float coef = a.coef;
 
-  // column ownership: float4 columns t + NT*r
+  // column ownership: float4 columns t + NC*r
   float4 xr[ZREG];
   float4 dl[ZREG];
 #pragma unroll
   for (int r = 0; r < ZREG; ++r) {
-    const int64_t col = tid + (int64_t)NT * r;
+    const int64_t col = tid + (int64_t)NC * r;
     float4 zv = make_float4(0.f, 0.f, 0.f, 0.f);
     if (col < n4) zv = reinterpret_cast<const float4*>(a.z)[col];
-    zsh[(size_t)r * NT + tid] = zv;
+    zsh[(size_t)r * NC + tid] = zv;
     xr[r] = (col < n4) ? mask_tail(soft_shrink4(zv, lam), col, a.n)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
     dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (tid == 0)
-    for (int i = 0; i < slots; ++i) mbar_init(&full[i], 1);
+  if (tid == 0) {
+    for (int i = 0; i < slots; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NCW);
+    }
+  }
   // metadata of iterations 0 and 1
-  for (int e = tid; e < 2 * rpi; e += NT) {
+  for (int e = tid; e < 2 * rpi; e += NC) {
     const int jj = e / rpi, q = e - jj * rpi;
     if (jj < a.K) {
       const int64_t o = (int64_t)jj * eta4 + p + (int64_t)P * q;
@@ -163,79 +185,83 @@ __global__ void __launch_bounds__(NT, 1)
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
 
-  // producer state (thread 0) and consumer state (all threads)
-  const int64_t total_rows = (int64_t)rpi * a.K;
-  int64_t prod = 0;        // rows issued
-  int64_t cons = 0;        // rows consumed
-  uint32_t parity_bits = 0;  // per-slot phase parity
-  int gcount = 0;            // groups consumed (selects the wpart buffer)
-  const float* Abase = a.A;
-  const int64_t lda = a.lda;
-  // issue rows while slots are free and the row's iteration is <= jmax
+  int64_t prod = 0;  // rows issued (thread 0)
+  int64_t cons = 0;  // rows consumed
+  int gcount = 0;    // groups consumed (selects the wpart buffer)
+  // Thread 0: issue rows into free slots, never blocking; rows of iterations
+  // up to jmax (their metadata is in shared memory).
   auto produce = [&](int64_t jmax) {
-    if (tid != 0) return;
-    while (prod < total_rows && prod - cons < slots) {
+    while (prod < total_rows) {
       const int64_t jj = prod / rpi;
       if (jj > jmax) break;
-      const int q = (int)(prod - jj * rpi);
       const int sl = (int)(prod % slots);
-      const int32_t row = midx[(jj % 3) * rpi + q];
+      const int64_t use = prod / slots;
+      if (use > 0 && !mbar_test(&empty[sl], (uint32_t)((use - 1) & 1))) break;
+      const int q = (int)(prod - jj * rpi);
+      const int ms = (int)(jj % 3) * rpi + q;
+      sb[sl] = mb[ms];
+      siv[sl] = miv[ms];
       mbar_expect_tx(&full[sl], rowbytes);
-      tma_load_1d(ring + (size_t)sl * rowbytes_pad, Abase + (int64_t)row * lda, rowbytes,
+      tma_load_1d(ring + (size_t)sl * rowbytes_pad, a.A + (int64_t)midx[ms] * a.lda, rowbytes,
                   &full[sl]);
       ++prod;
     }
   };
-  // on an error exit: let every issued copy land before shared memory goes away
-  auto drain = [&]() {
+  // error exit: let every issued copy land before shared memory goes away
+  auto bail = [&]() {
     if (tid == 0) {
       for (int64_t g = cons; g < prod; ++g) {
         const int sl = (int)(g % slots);
-        mbar_wait_bounded(&full[sl], (parity_bits >> sl) & 1u, a.limit_ns);
-        parity_bits ^= (1u << sl);
+        mbar_wait_bounded(&full[sl], (uint32_t)((g / slots) & 1), a.limit_ns);
       }
     }
     __syncthreads();
   };
-  produce(1);
+  if (tid == 0) produce(1);
 
   for (int64_t j = 0; j < a.K; ++j) {
-    const int mcur = (int)(j % 3);
     // metadata of iteration j+2 (used from the next iteration on)
     if (j + 2 < a.K) {
       const int ms = (int)((j + 2) % 3);
-      for (int q = tid; q < rpi; q += NT) {
+      for (int q = tid; q < rpi; q += NC) {
         const int64_t o = (j + 2) * eta4 + p + (int64_t)P * q;
         cp_async4(midx + ms * rpi + q, a.tidx + o);
         cp_async4(mb + ms * rpi + q, a.tb + o);
         cp_async4(miv + ms * rpi + q, a.tiv + o);
       }
     }
-    cp_async_commit();
-    produce(j + 1);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
 
     // ---- this CTA's rows of tau_k: dots, coefficients, partial update ----
     for (int q0 = 0; q0 < rpi; q0 += G) {
       const int ng = min(G, rpi - q0);
+      if (tid == 0) produce(j + 1);
       float4 av[G][ZREG];
-      float pd[G];
-      bool tmo = false;
+      float pd[G], bg[G], ivg[G];
+      int tmo = 0;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         pd[g] = 0.f;
+        bg[g] = 0.f;
+        ivg[g] = 0.f;
         if (g < ng) {
-          const int sl = (int)((cons + g) % slots);
-          const uint32_t par = (parity_bits >> sl) & 1u;
-          if (!mbar_wait_bounded(&full[sl], par, a.limit_ns)) tmo = true;
+          const int64_t gi = cons + g;
+          const int sl = (int)(gi % slots);
+          if (!mbar_wait_bounded(&full[sl], (uint32_t)((gi / slots) & 1), a.limit_ns)) tmo = 1;
           const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
 #pragma unroll
           for (int r = 0; r < ZREG; ++r) {
-            const int64_t col = tid + (int64_t)NT * r;
+            const int64_t col = tid + (int64_t)NC * r;
             float4 v = (col < n4) ? rowp[col] : make_float4(0.f, 0.f, 0.f, 0.f);
             if (col == n4 - 1) v = mask_tail(v, col, a.n);
             av[g][r] = v;
-            pd[g] += dot4(v, xr[r]);
           }
+          bg[g] = sb[sl];
+          ivg[g] = siv[sl];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[sl]);  // the row is in registers: free the slot
+#pragma unroll
+          for (int r = 0; r < ZREG; ++r) pd[g] += dot4(av[g][r], xr[r]);
         } else {
 #pragma unroll
           for (int r = 0; r < ZREG; ++r) av[g][r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -255,21 +281,17 @@ __global__ void __launch_bounds__(NT, 1)
       if (__syncthreads_or(tmo)) {
         if (tid == 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        drain();
+        bail();
         return;
       }
-      // the group's slots are free: advance the consumer, refill
-      for (int g = 0; g < ng; ++g) parity_bits ^= (1u << (int)((cons + g) % slots));
       cons += ng;
-      produce(j + 1);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        if (g < ng) {
-          float d = 0.f;
+        float d = (lane < NCW) ? wpart[wp][lane][g] : 0.f;
 #pragma unroll
-          for (int w = 0; w < NWARPS; ++w) d += wpart[wp][w][g];
-          const int q = q0 + g;
-          const float cval = coef * ((d - mb[mcur * rpi + q]) * miv[mcur * rpi + q]);
+        for (int o = NCW / 2; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (g < ng) {
+          const float cval = coef * ((d - bg[g]) * ivg[g]);
 #pragma unroll
           for (int r = 0; r < ZREG; ++r) {
             dl[r].x = fmaf(cval, av[g][r].x, dl[r].x);
@@ -281,20 +303,21 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (tid == 0) produce(j + 1);
 
     // ---- exchange: Delta = sum_p Delta_p ----
     if (single) {
 #pragma unroll
       for (int r = 0; r < ZREG; ++r) {
-        const int64_t col = tid + (int64_t)NT * r;
+        const int64_t col = tid + (int64_t)NC * r;
         if (col < n4) {
-          float4 zv = zsh[(size_t)r * NT + tid];
+          float4 zv = zsh[(size_t)r * NC + tid];
           zv.x -= dl[r].x;
           zv.y -= dl[r].y;
           zv.z -= dl[r].z;
           zv.w -= dl[r].w;
           zv = mask_tail(zv, col, a.n);
-          zsh[(size_t)r * NT + tid] = zv;
+          zsh[(size_t)r * NC + tid] = zv;
           xr[r] = soft_shrink4(zv, lam);
         }
         dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -306,32 +329,58 @@ __global__ void __launch_bounds__(NT, 1)
     float* dacc = a.racc + (size_t)buf * n4 * 4;
 #pragma unroll
     for (int r = 0; r < ZREG; ++r) {
-      const int64_t col = tid + (int64_t)NT * r;
+      const int64_t col = tid + (int64_t)NC * r;
       if (rpi > 0 && col < n4) red_add_v4(dacc + col * 4, dl[r]);
       dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (p == 0) {
       float4* nxt = reinterpret_cast<float4*>(a.racc + (size_t)((j + 1) % 3) * n4 * 4);
-      for (int64_t col = tid; col < n4; col += NT) nxt[col] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t col = tid; col < n4; col += NC) nxt[col] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (!grid_barrier(a.bar, (unsigned long long)(j + 1), a.status, a.limit_ns, &s_flag)) {
-      drain();
+    // grid barrier (bounded); thread 0 keeps the ring fed while it waits
+    __syncthreads();
+    if (tid == 0) {
+      int ok = 1;
+      __threadfence();
+      atomicAdd(a.bar, 1ull);
+      const unsigned long long target = (unsigned long long)(j + 1) * (unsigned long long)P;
+      const uint64_t t0 = global_timer_ns();
+      uint32_t spins = 0;
+      while (ld_acquire_u64(a.bar) < target) {
+        produce(j + 1);
+        if ((++spins & 15u) == 0) {
+          if (ld_relaxed_s32(a.status) != kStatusOk) {
+            ok = 0;
+            break;
+          }
+          if (global_timer_ns() - t0 > a.limit_ns) {
+            atomicCAS(a.status, kStatusOk, kStatusTimeout);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      s_flag = ok;
+    }
+    __syncthreads();
+    if (!s_flag) {
+      bail();
       return;
     }
-    produce(j + 1);
     const float4* dtot = reinterpret_cast<const float4*>(dacc);
 #pragma unroll
     for (int r = 0; r < ZREG; ++r) {
-      const int64_t col = tid + (int64_t)NT * r;
+      const int64_t col = tid + (int64_t)NC * r;
       if (col < n4) {
         const float4 d = __ldcg(dtot + col);
-        float4 zv = zsh[(size_t)r * NT + tid];
+        float4 zv = zsh[(size_t)r * NC + tid];
         zv.x -= d.x;
         zv.y -= d.y;
         zv.z -= d.z;
         zv.w -= d.w;
         zv = mask_tail(zv, col, a.n);
-        zsh[(size_t)r * NT + tid] = zv;
+        zsh[(size_t)r * NC + tid] = zv;
         xr[r] = soft_shrink4(zv, lam);
       }
     }
@@ -342,9 +391,9 @@ __global__ void __launch_bounds__(NT, 1)
     float4* xo = reinterpret_cast<float4*>(a.x);
 #pragma unroll
     for (int r = 0; r < ZREG; ++r) {
-      const int64_t col = tid + (int64_t)NT * r;
+      const int64_t col = tid + (int64_t)NC * r;
       if (col < n4) {
-        zo[col] = zsh[(size_t)r * NT + tid];
+        zo[col] = zsh[(size_t)r * NC + tid];
         xo[col] = xr[r];
       }
     }
@@ -363,7 +412,7 @@ cudaError_t launch_rows_t(const SolveArgs& a, const RowsGeometry& g, cudaStream_
   void* params[] = {&args, &slots, &rbp};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)g.grid);
-  cfg.blockDim = dim3(NT);
+  cfg.blockDim = dim3(NC);
   cfg.dynamicSmemBytes = g.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -379,7 +428,7 @@ cudaError_t launch_rows_t(const SolveArgs& a, const RowsGeometry& g, cudaStream_
 bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t smem_optin,
                RowsGeometry* g) {
   const int64_t n4 = (n + 3) / 4;
-  const int64_t zreg = (n4 + NT - 1) / NT;
+  const int64_t zreg = (n4 + NC - 1) / NC;
   if (zreg > kRowsMaxZ) return false;
   const int z = (int)std::max<int64_t>(1, zreg);
   // Small iterations (all of tau_k within ~128 KB) run on one CTA: no grid
@@ -388,10 +437,10 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   int64_t P = grid_override > 0 ? grid_override
                                 : (iter_bytes <= (128 << 10) ? 1 : std::min<int64_t>(num_sms, eta));
   P = std::max<int64_t>(1, std::min<int64_t>(P, num_sms));
-  const int64_t rpi = (eta + P - 1) / P;
   const int64_t rowbytes = n4 * 16;
   const int64_t rowbytes_pad = (rowbytes + 127) / 128 * 128;
-  const size_t fixed = (size_t)z * NT * 16 + (size_t)3 * rpi * 12 + 2048;
+  const int64_t rpi = (eta + P - 1) / P;
+  const size_t fixed = (size_t)z * NC * 16 + (size_t)3 * rpi * 12 + 2048;
   if (fixed + 2 * rowbytes_pad > smem_optin) return false;
   int64_t slots = (int64_t)((smem_optin - fixed) / rowbytes_pad);
   slots = std::min<int64_t>(slots, SLOTS_MAX);
@@ -400,7 +449,7 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   g->zreg = z;
   g->slots = (int)slots;
   g->rowbytes_pad = (int)rowbytes_pad;
-  g->smem = (size_t)slots * rowbytes_pad + (size_t)z * NT * 16 + (size_t)3 * rpi * 12;
+  g->smem = (size_t)slots * rowbytes_pad + (size_t)z * NC * 16 + (size_t)3 * rpi * 12;
   return true;
 }
 
