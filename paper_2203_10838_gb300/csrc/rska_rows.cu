@@ -287,9 +287,11 @@ __global__ void __launch_bounds__(NC, 1)
       cons += ng;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
+        // lanes 0..NCW-1 hold the warp partials, the rest zero; a full xor
+        // butterfly leaves the total in every lane
         float d = (lane < NCW) ? wpart[wp][lane][g] : 0.f;
 #pragma unroll
-        for (int o = NCW / 2; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         if (g < ng) {
           const float cval = coef * ((d - bg[g]) * ivg[g]);
 #pragma unroll
