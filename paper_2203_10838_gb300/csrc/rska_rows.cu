@@ -219,6 +219,43 @@ __global__ void __launch_bounds__(NC, 1)
   };
   if (tid == 0) produce(1);
 
+  // rows of the current group, in registers (they may be loaded during the
+  // previous iteration's exchange: have_pre)
+  float4 av[G][ZREG];
+  float bg[G], ivg[G];
+  bool have_pre = false;
+  // wait for rows cons .. cons+ng-1, copy this thread's columns to registers,
+  // release their slots; returns 1 on a timeout
+  auto load_group = [&](int ng) -> int {
+    int tmo = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      bg[g] = 0.f;
+      ivg[g] = 0.f;
+      if (g < ng) {
+        const int64_t gi = cons + g;
+        const int sl = (int)(gi % slots);
+        if (!mbar_wait_bounded(&full[sl], (uint32_t)((gi / slots) & 1), a.limit_ns)) tmo = 1;
+        const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
+#pragma unroll
+        for (int r = 0; r < ZREG; ++r) {
+          const int64_t col = tid + (int64_t)NC * r;
+          float4 v = (col < n4) ? rowp[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (col == n4 - 1) v = mask_tail(v, col, a.n);
+          av[g][r] = v;
+        }
+        bg[g] = sb[sl];
+        ivg[g] = siv[sl];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sl]);  // the row is in registers: free the slot
+      } else {
+#pragma unroll
+        for (int r = 0; r < ZREG; ++r) av[g][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    return tmo;
+  };
+
   for (int64_t j = 0; j < a.K; ++j) {
     // metadata of iteration j+2 (used from the next iteration on)
     if (j + 2 < a.K) {
@@ -236,36 +273,14 @@ __global__ void __launch_bounds__(NC, 1)
     for (int q0 = 0; q0 < rpi; q0 += G) {
       const int ng = min(G, rpi - q0);
       if (tid == 0) produce(j + 1);
-      float4 av[G][ZREG];
-      float pd[G], bg[G], ivg[G];
+      float pd[G];
       int tmo = 0;
+      if (!(q0 == 0 && have_pre)) tmo = load_group(ng);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         pd[g] = 0.f;
-        bg[g] = 0.f;
-        ivg[g] = 0.f;
-        if (g < ng) {
-          const int64_t gi = cons + g;
-          const int sl = (int)(gi % slots);
-          if (!mbar_wait_bounded(&full[sl], (uint32_t)((gi / slots) & 1), a.limit_ns)) tmo = 1;
-          const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
 #pragma unroll
-          for (int r = 0; r < ZREG; ++r) {
-            const int64_t col = tid + (int64_t)NC * r;
-            float4 v = (col < n4) ? rowp[col] : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (col == n4 - 1) v = mask_tail(v, col, a.n);
-            av[g][r] = v;
-          }
-          bg[g] = sb[sl];
-          ivg[g] = siv[sl];
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&empty[sl]);  // the row is in registers: free the slot
-#pragma unroll
-          for (int r = 0; r < ZREG; ++r) pd[g] += dot4(av[g][r], xr[r]);
-        } else {
-#pragma unroll
-          for (int r = 0; r < ZREG; ++r) av[g][r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        for (int r = 0; r < ZREG; ++r) pd[g] += dot4(av[g][r], xr[r]);
       }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
@@ -304,6 +319,7 @@ __global__ void __launch_bounds__(NC, 1)
         }
       }
     }
+    have_pre = false;
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (tid == 0) produce(j + 1);
 
@@ -339,16 +355,25 @@ __global__ void __launch_bounds__(NC, 1)
       float4* nxt = reinterpret_cast<float4*>(a.racc + (size_t)((j + 1) % 3) * n4 * 4);
       for (int64_t col = tid; col < n4; col += NC) nxt[col] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    // grid barrier (bounded); thread 0 keeps the ring fed while it waits
+    // grid barrier (bounded): arrive, pull the next iteration's first rows
+    // into registers (freeing their slots), then wait; thread 0 keeps the
+    // ring fed while it waits
     __syncthreads();
     if (tid == 0) {
-      int ok = 1;
       __threadfence();
       atomicAdd(a.bar, 1ull);
+    }
+    int pre_tmo = 0;
+    if (j + 1 < a.K && rpi > 0) {
+      pre_tmo = load_group(min(G, rpi));
+      have_pre = true;
+    }
+    if (tid == 0) {
+      int ok = pre_tmo ? 0 : 1;
       const unsigned long long target = (unsigned long long)(j + 1) * (unsigned long long)P;
       const uint64_t t0 = global_timer_ns();
       uint32_t spins = 0;
-      while (ld_acquire_u64(a.bar) < target) {
+      while (ok && ld_acquire_u64(a.bar) < target) {
         produce(j + 1);
         if ((++spins & 15u) == 0) {
           if (ld_relaxed_s32(a.status) != kStatusOk) {
@@ -365,8 +390,8 @@ __global__ void __launch_bounds__(NC, 1)
       __threadfence();
       s_flag = ok;
     }
-    __syncthreads();
-    if (!s_flag) {
+    if (__syncthreads_or(pre_tmo) || !s_flag) {
+      if (tid == 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
       bail();
       return;
     }
