@@ -11,6 +11,9 @@
 // back; every CTA keeps a full copy of z = x^* (shared memory) and of
 // x = S_lambda(z) (registers) and applies z -= Delta, x = S_lambda(z) itself.
 //
+// A row is fetched as several 4 KB bulk copies on one mbarrier: the copy
+// engine overlaps independent copies but streams each one slowly.
+//
 // Ring discipline.  A warp releases a slot (empty mbarrier) the moment the
 // row is in its registers; thread 0 refills free slots without blocking at
 // every group boundary and inside the grid-barrier spin, so the ring stays
@@ -31,6 +34,7 @@ constexpr int NC = kSolveThreads;   // threads per CTA
 constexpr int NCW = NC / 32;         // warps per CTA
 constexpr int G = 2;                 // rows reduced together
 constexpr int SLOTS_MAX = 16;
+constexpr uint32_t kTmaChunk = 4096;  // bytes per bulk copy (a multiple of 16)
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -202,8 +206,15 @@ __global__ void __launch_bounds__(NC, 1)
       sb[sl] = mb[ms];
       siv[sl] = miv[ms];
       mbar_expect_tx(&full[sl], rowbytes);
-      tma_load_1d(ring + (size_t)sl * rowbytes_pad, a.A + (int64_t)midx[ms] * a.lda, rowbytes,
-                  &full[sl]);
+      // one bulk copy streams slowly on its own; chunks of kTmaChunk bytes run
+      // concurrently, so a row lands in about one memory latency
+      const unsigned char* src =
+          reinterpret_cast<const unsigned char*>(a.A + (int64_t)midx[ms] * a.lda);
+      unsigned char* dst = ring + (size_t)sl * rowbytes_pad;
+      for (uint32_t off = 0; off < rowbytes; off += kTmaChunk) {
+        const uint32_t bytes = (rowbytes - off < kTmaChunk) ? (rowbytes - off) : kTmaChunk;
+        tma_load_1d(dst + off, src + off, bytes, &full[sl]);
+      }
       ++prod;
     }
   };
