@@ -11,9 +11,6 @@
 // back; every CTA keeps a full copy of z = x^* (shared memory) and of
 // x = S_lambda(z) (registers) and applies z -= Delta, x = S_lambda(z) itself.
 //
-// A row is fetched as several 4 KB bulk copies on one mbarrier: the copy
-// engine overlaps independent copies but streams each one slowly.
-//
 // Ring discipline.  A warp releases a slot (empty mbarrier) the moment the
 // row is in its registers; thread 0 refills free slots without blocking at
 // every group boundary and inside the grid-barrier spin, so the ring stays
@@ -34,7 +31,6 @@ constexpr int NC = kSolveThreads;   // threads per CTA
 constexpr int NCW = NC / 32;         // warps per CTA
 constexpr int G = 2;                 // rows reduced together
 constexpr int SLOTS_MAX = 16;
-constexpr uint32_t kTmaChunk = 4096;  // bytes per bulk copy (a multiple of 16)
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -110,13 +106,15 @@ __device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
   return r;
 }
 
-// Bounded wait on an mbarrier phase; false after limit_ns.
+// Bounded wait on an mbarrier phase; false after limit_ns.  The timer is read
+// only every 64 polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity,
                                                   uint64_t limit_ns) {
   if (mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = global_timer_ns();
+  uint32_t spins = 0;
   while (!mbar_try_wait(b, parity)) {
-    if (global_timer_ns() - t0 > limit_ns) return false;
+    if ((++spins & 63u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -206,15 +204,8 @@ __global__ void __launch_bounds__(NC, 1)
       sb[sl] = mb[ms];
       siv[sl] = miv[ms];
       mbar_expect_tx(&full[sl], rowbytes);
-      // one bulk copy streams slowly on its own; chunks of kTmaChunk bytes run
-      // concurrently, so a row lands in about one memory latency
-      const unsigned char* src =
-          reinterpret_cast<const unsigned char*>(a.A + (int64_t)midx[ms] * a.lda);
-      unsigned char* dst = ring + (size_t)sl * rowbytes_pad;
-      for (uint32_t off = 0; off < rowbytes; off += kTmaChunk) {
-        const uint32_t bytes = (rowbytes - off < kTmaChunk) ? (rowbytes - off) : kTmaChunk;
-        tma_load_1d(dst + off, src + off, bytes, &full[sl]);
-      }
+      tma_load_1d(ring + (size_t)sl * rowbytes_pad, a.A + (int64_t)midx[ms] * a.lda, rowbytes,
+                  &full[sl]);
       ++prod;
     }
   };
@@ -246,7 +237,10 @@ __global__ void __launch_bounds__(NC, 1)
       if (g < ng) {
         const int64_t gi = cons + g;
         const int sl = (int)(gi % slots);
-        if (!mbar_wait_bounded(&full[sl], (uint32_t)((gi / slots) & 1), a.limit_ns)) tmo = 1;
+        // one lane per warp polls; __syncwarp orders the landed row for the others
+        if (lane == 0 && !mbar_wait_bounded(&full[sl], (uint32_t)((gi / slots) & 1), a.limit_ns))
+          tmo = 1;
+        __syncwarp();
         const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
 #pragma unroll
         for (int r = 0; r < ZREG; ++r) {
