@@ -373,7 +373,11 @@ __global__ void __launch_bounds__(NC, 1)
       pre_tmo = load_group(min(G, rpi));
       have_pre = true;
     }
+    // every warp has released the preloaded rows' slots: refill them now, so
+    // the next iteration streams while this one waits at the barrier
+    pre_tmo = __syncthreads_or(pre_tmo);
     if (tid == 0) {
+      produce(j + 1);
       int ok = pre_tmo ? 0 : 1;
       const unsigned long long target = (unsigned long long)(j + 1) * (unsigned long long)P;
       const uint64_t t0 = global_timer_ns();
