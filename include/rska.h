@@ -168,7 +168,7 @@ int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
  *   what = 0: CTAs in the persistent grid (0 = automatic)
  *          1: watchdog limit of each device-side wait, in microseconds
  *             (default 2,000,000)
- *          2: solver kernel: 0 automatic (row-split when n <= 10240, else
+ *          2: solver kernel: 0 automatic (row-split when n <= 11520, else
  *             column-split), 1 column-split, 2 row-split
  * The row-split kernel gives each CTA whole rows of tau_k (TMA bulk copies)
  * and exchanges one n-vector per iteration; the column-split kernel gives

@@ -11,13 +11,14 @@
 // back; every CTA keeps a full copy of z = x^* (shared memory) and of
 // x = S_lambda(z) (registers) and applies z -= Delta, x = S_lambda(z) itself.
 //
-// Ring discipline.  A warp releases a slot (empty mbarrier) the moment the
-// row is in its registers; thread 0 refills free slots without blocking at
-// every group boundary and inside the grid-barrier spin, so the ring stays
-// full also while the CTA is in the exchange: HBM streams the next
-// iteration's rows through the barrier.  tau, b and 1/||a||^2 of the next
-// iterations are copied from the pre-sampled arrays two iterations ahead.
-// Every device-side wait (full/empty mbarriers, grid barrier) is bounded.
+// Warp roles.  Warps 0..14 consume rows (each thread owns float4 columns
+// t + 480 r); warp 15 is the producer: it reads tau, b and 1/||a||^2 of the
+// upcoming rows from the pre-sampled arrays and, for each row, waits for its
+// ring slot to be released and issues the TMA copy at once.  A consumer warp
+// releases a slot (empty mbarrier) the moment the row is in its registers, so
+// the ring stays full, also while the consumers are in the exchange: HBM
+// streams the next iteration's rows through the barrier.  Every device-side
+// wait (full/empty mbarriers, grid barrier) is bounded.
 #include <algorithm>
 
 #include "rska_device.cuh"
@@ -27,8 +28,9 @@ namespace rska {
 
 namespace {
 
-constexpr int NC = kSolveThreads;   // threads per CTA
-constexpr int NCW = NC / 32;         // warps per CTA
+constexpr int NT = kSolveThreads;   // threads per CTA
+constexpr int NC = NT - 32;          // consumer threads (warps 0..14)
+constexpr int NCW = NC / 32;         // consumer warps
 constexpr int G = 2;                 // rows reduced together
 constexpr int SLOTS_MAX = 16;
 
@@ -60,18 +62,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 
-// Non-blocking test of an mbarrier phase.
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
                                             uint64_t* bar) {
   asm volatile(
@@ -87,9 +77,20 @@ __device__ __forceinline__ void red_add_v4(float* p, float4 v) {
                : "memory");
 }
 
-__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src_gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(su32(dst_smem)), "l"(src_gmem)
-               : "memory");
+// Barrier among the consumer warps only (named barrier 1).
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
+}
+
+__device__ __forceinline__ int consumer_sync_or(int pred) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
+      " selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(pred), "n"(NC)
+      : "memory");
+  return r;
 }
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
@@ -106,21 +107,24 @@ __device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
   return r;
 }
 
-// Bounded wait on an mbarrier phase; false after limit_ns.  The timer is read
-// only every 64 polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity,
-                                                  uint64_t limit_ns) {
+// Bounded wait on an mbarrier phase: false after limit_ns, or once *abort is
+// set (when abort is given).  The timer is read every 64 polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity, uint64_t limit_ns,
+                                                  const volatile int* abort) {
   if (mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   uint32_t spins = 0;
   while (!mbar_try_wait(b, parity)) {
-    if ((++spins & 63u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
+    if ((++spins & 63u) == 0) {
+      if (global_timer_ns() - t0 > limit_ns) return false;
+      if (abort != nullptr && *abort) return false;
+    }
   }
   return true;
 }
 
 template <int ZREG>
-__global__ void __launch_bounds__(NC, 1)
+__global__ void __launch_bounds__(NT, 1)
     rska_rows_kernel(SolveArgs a, int slots, int rowbytes_pad) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[SLOTS_MAX];
@@ -129,6 +133,9 @@ __global__ void __launch_bounds__(NC, 1)
   __shared__ float sb[SLOTS_MAX];
   __shared__ float siv[SLOTS_MAX];
   __shared__ int s_flag;
+  __shared__ volatile int s_abort;        // consumers -> producer: stop issuing
+  __shared__ volatile int s_pdone;        // producer -> consumers: no more copies
+  __shared__ volatile long long s_prod;   // rows issued so far
 
   if (a.stop != nullptr && ld_relaxed_s32(a.stop) != 0) return;
 
@@ -147,10 +154,78 @@ __global__ void __launch_bounds__(NC, 1)
 
   unsigned char* ring = smem;                                                     // slots x rowbytes_pad
   float4* zsh = reinterpret_cast<float4*>(smem + (size_t)slots * rowbytes_pad);  // ZREG x NC
-  int32_t* midx = reinterpret_cast<int32_t*>(zsh + (size_t)ZREG * NC);           // 3 x rpi
-  float* mb = reinterpret_cast<float*>(midx + 3 * rpi);
-  float* miv = mb + 3 * rpi;
 
+  if (tid == 0) {
+    for (int i = 0; i < slots; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NCW);
+    }
+    s_abort = 0;
+    s_pdone = 0;
+    s_prod = 0;
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+
+  // ------------------------------------------------------------ producer --
+  if (warp == NCW) {
+    bool stop_now = false;
+    int32_t row = 0;
+    float bv = 0.f, ivv = 0.f;
+    auto fetch_meta = [&](int64_t g0) {  // lane l: metadata of row g0 + l
+      const int64_t gl = g0 + lane;
+      row = 0;
+      bv = 0.f;
+      ivv = 0.f;
+      if (gl < total_rows) {
+        const int64_t jj = gl / rpi;
+        const int q = (int)(gl - jj * rpi);
+        const int64_t o = jj * eta4 + p + (int64_t)P * q;
+        row = a.tidx[o];
+        bv = a.tb[o];
+        ivv = a.tiv[o];
+      }
+    };
+    fetch_meta(0);
+    for (int64_t g0 = 0; g0 < total_rows && !stop_now; g0 += 32) {
+      const int32_t crow = row;
+      const float cb = bv, civ = ivv;
+      if (g0 + 32 < total_rows) fetch_meta(g0 + 32);  // next batch in flight meanwhile
+      const int cnt = (int)((total_rows - g0 < 32) ? (total_rows - g0) : 32);
+      for (int i = 0; i < cnt; ++i) {
+        const int32_t r_i = __shfl_sync(0xffffffffu, crow, i);
+        const float b_i = __shfl_sync(0xffffffffu, cb, i);
+        const float iv_i = __shfl_sync(0xffffffffu, civ, i);
+        int bad = 0;
+        if (lane == 0) {
+          const int64_t gi = g0 + i;
+          const int sl = (int)(gi % slots);
+          const int64_t use = gi / slots;
+          if (use > 0 && !mbar_wait_bounded(&empty[sl], (uint32_t)((use - 1) & 1), a.limit_ns,
+                                            &s_abort))
+            bad = 1;
+          if (!bad && s_abort) bad = 1;
+          if (!bad) {
+            sb[sl] = b_i;
+            siv[sl] = iv_i;
+            mbar_expect_tx(&full[sl], rowbytes);
+            tma_load_1d(ring + (size_t)sl * rowbytes_pad, a.A + (int64_t)r_i * a.lda, rowbytes,
+                        &full[sl]);
+            s_prod = gi + 1;
+          }
+        }
+        if (__shfl_sync(0xffffffffu, bad, 0)) {
+          stop_now = true;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) s_pdone = 1;
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers --
   const int64_t k0 = *a.kdev;
   const float lam = a.lambda;
   const float coef = a.coef;
@@ -168,61 +243,25 @@ __global__ void __launch_bounds__(NC, 1)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
     dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (tid == 0) {
-    for (int i = 0; i < slots; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], NCW);
-    }
-  }
-  // metadata of iterations 0 and 1
-  for (int e = tid; e < 2 * rpi; e += NC) {
-    const int jj = e / rpi, q = e - jj * rpi;
-    if (jj < a.K) {
-      const int64_t o = (int64_t)jj * eta4 + p + (int64_t)P * q;
-      midx[jj * rpi + q] = a.tidx[o];
-      mb[jj * rpi + q] = a.tb[o];
-      miv[jj * rpi + q] = a.tiv[o];
-    }
-  }
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  __syncthreads();
 
-  int64_t prod = 0;  // rows issued (thread 0)
   int64_t cons = 0;  // rows consumed
   int gcount = 0;    // groups consumed (selects the wpart buffer)
-  // Thread 0: issue rows into free slots, never blocking; rows of iterations
-  // up to jmax (their metadata is in shared memory).
-  auto produce = [&](int64_t jmax) {
-    while (prod < total_rows) {
-      const int64_t jj = prod / rpi;
-      if (jj > jmax) break;
-      const int sl = (int)(prod % slots);
-      const int64_t use = prod / slots;
-      if (use > 0 && !mbar_test(&empty[sl], (uint32_t)((use - 1) & 1))) break;
-      const int q = (int)(prod - jj * rpi);
-      const int ms = (int)(jj % 3) * rpi + q;
-      sb[sl] = mb[ms];
-      siv[sl] = miv[ms];
-      mbar_expect_tx(&full[sl], rowbytes);
-      tma_load_1d(ring + (size_t)sl * rowbytes_pad, a.A + (int64_t)midx[ms] * a.lda, rowbytes,
-                  &full[sl]);
-      ++prod;
-    }
-  };
-  // error exit: let every issued copy land before shared memory goes away
+  // error exit: stop the producer, let every issued copy land, leave
   auto bail = [&]() {
     if (tid == 0) {
-      for (int64_t g = cons; g < prod; ++g) {
+      s_abort = 1;
+      const uint64_t t0 = global_timer_ns();
+      while (!s_pdone && global_timer_ns() - t0 < a.limit_ns) {
+      }
+      const int64_t issued = s_prod;
+      for (int64_t g = cons; g < issued; ++g) {
         const int sl = (int)(g % slots);
-        mbar_wait_bounded(&full[sl], (uint32_t)((g / slots) & 1), a.limit_ns);
+        mbar_wait_bounded(&full[sl], (uint32_t)((g / slots) & 1), a.limit_ns, nullptr);
       }
     }
-    __syncthreads();
+    consumer_sync();
   };
-  if (tid == 0) produce(1);
 
-  // rows of the current group, in registers (they may be loaded during the
-  // previous iteration's exchange: have_pre)
   float4 av[G][ZREG];
   float bg[G], ivg[G];
   bool have_pre = false;
@@ -238,7 +277,8 @@ __global__ void __launch_bounds__(NC, 1)
         const int64_t gi = cons + g;
         const int sl = (int)(gi % slots);
         // one lane per warp polls; __syncwarp orders the landed row for the others
-        if (lane == 0 && !mbar_wait_bounded(&full[sl], (uint32_t)((gi / slots) & 1), a.limit_ns))
+        if (lane == 0 &&
+            !mbar_wait_bounded(&full[sl], (uint32_t)((gi / slots) & 1), a.limit_ns, nullptr))
           tmo = 1;
         __syncwarp();
         const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
@@ -262,22 +302,9 @@ __global__ void __launch_bounds__(NC, 1)
   };
 
   for (int64_t j = 0; j < a.K; ++j) {
-    // metadata of iteration j+2 (used from the next iteration on)
-    if (j + 2 < a.K) {
-      const int ms = (int)((j + 2) % 3);
-      for (int q = tid; q < rpi; q += NC) {
-        const int64_t o = (j + 2) * eta4 + p + (int64_t)P * q;
-        cp_async4(midx + ms * rpi + q, a.tidx + o);
-        cp_async4(mb + ms * rpi + q, a.tb + o);
-        cp_async4(miv + ms * rpi + q, a.tiv + o);
-      }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-
     // ---- this CTA's rows of tau_k: dots, coefficients, partial update ----
     for (int q0 = 0; q0 < rpi; q0 += G) {
       const int ng = min(G, rpi - q0);
-      if (tid == 0) produce(j + 1);
       float pd[G];
       int tmo = 0;
       if (!(q0 == 0 && have_pre)) tmo = load_group(ng);
@@ -298,9 +325,8 @@ __global__ void __launch_bounds__(NC, 1)
 #pragma unroll
         for (int g = 0; g < G; ++g) wpart[wp][warp][g] = pd[g];
       }
-      if (__syncthreads_or(tmo)) {
+      if (consumer_sync_or(tmo)) {
         if (tid == 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         bail();
         return;
       }
@@ -325,8 +351,6 @@ __global__ void __launch_bounds__(NC, 1)
       }
     }
     have_pre = false;
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (tid == 0) produce(j + 1);
 
     // ---- exchange: Delta = sum_p Delta_p ----
     if (single) {
@@ -345,7 +369,6 @@ __global__ void __launch_bounds__(NC, 1)
         }
         dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      __syncthreads();
       continue;
     }
     const int buf = (int)(j % 3);
@@ -361,9 +384,8 @@ __global__ void __launch_bounds__(NC, 1)
       for (int64_t col = tid; col < n4; col += NC) nxt[col] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // grid barrier (bounded): arrive, pull the next iteration's first rows
-    // into registers (freeing their slots), then wait; thread 0 keeps the
-    // ring fed while it waits
-    __syncthreads();
+    // into registers (freeing their slots for the producer), then wait
+    consumer_sync();
     if (tid == 0) {
       __threadfence();
       atomicAdd(a.bar, 1ull);
@@ -373,17 +395,12 @@ __global__ void __launch_bounds__(NC, 1)
       pre_tmo = load_group(min(G, rpi));
       have_pre = true;
     }
-    // every warp has released the preloaded rows' slots: refill them now, so
-    // the next iteration streams while this one waits at the barrier
-    pre_tmo = __syncthreads_or(pre_tmo);
     if (tid == 0) {
-      produce(j + 1);
-      int ok = pre_tmo ? 0 : 1;
+      int ok = 1;
       const unsigned long long target = (unsigned long long)(j + 1) * (unsigned long long)P;
       const uint64_t t0 = global_timer_ns();
       uint32_t spins = 0;
-      while (ok && ld_acquire_u64(a.bar) < target) {
-        produce(j + 1);
+      while (ld_acquire_u64(a.bar) < target) {
         if ((++spins & 15u) == 0) {
           if (ld_relaxed_s32(a.status) != kStatusOk) {
             ok = 0;
@@ -399,7 +416,7 @@ __global__ void __launch_bounds__(NC, 1)
       __threadfence();
       s_flag = ok;
     }
-    if (__syncthreads_or(pre_tmo) || !s_flag) {
+    if (consumer_sync_or(pre_tmo) || !s_flag) {
       if (tid == 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
       bail();
       return;
@@ -448,7 +465,7 @@ cudaError_t launch_rows_t(const SolveArgs& a, const RowsGeometry& g, cudaStream_
   void* params[] = {&args, &slots, &rbp};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)g.grid);
-  cfg.blockDim = dim3(NC);
+  cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = g.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -475,8 +492,7 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   P = std::max<int64_t>(1, std::min<int64_t>(P, num_sms));
   const int64_t rowbytes = n4 * 16;
   const int64_t rowbytes_pad = (rowbytes + 127) / 128 * 128;
-  const int64_t rpi = (eta + P - 1) / P;
-  const size_t fixed = (size_t)z * NC * 16 + (size_t)3 * rpi * 12 + 2048;
+  const size_t fixed = (size_t)z * NC * 16 + 2048;
   if (fixed + 2 * rowbytes_pad > smem_optin) return false;
   int64_t slots = (int64_t)((smem_optin - fixed) / rowbytes_pad);
   slots = std::min<int64_t>(slots, SLOTS_MAX);
@@ -485,7 +501,7 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   g->zreg = z;
   g->slots = (int)slots;
   g->rowbytes_pad = (int)rowbytes_pad;
-  g->smem = (size_t)slots * rowbytes_pad + (size_t)z * NC * 16 + (size_t)3 * rpi * 12;
+  g->smem = (size_t)slots * rowbytes_pad + (size_t)z * NC * 16;
   return true;
 }
 
@@ -502,7 +518,8 @@ cudaError_t launch_rows(const SolveArgs& a, const RowsGeometry& g, cudaStream_t 
     case 2: return launch_rows_t<2>(a, g, s);
     case 3: return launch_rows_t<3>(a, g, s);
     case 4: return launch_rows_t<4>(a, g, s);
-    default: return launch_rows_t<5>(a, g, s);
+    case 5: return launch_rows_t<5>(a, g, s);
+    default: return launch_rows_t<6>(a, g, s);
   }
 }
 
