@@ -8,8 +8,8 @@
 // update Delta_p (registers).  The only exchange per iteration is the sum of
 // the P partial updates: each CTA adds Delta_p into a global accumulator with
 // 16-byte vector reductions, passes one grid barrier, and reads the total
-// back; every CTA keeps a full copy of z = x^* and of x = S_lambda(z) in
-// registers and applies z -= Delta, x = S_lambda(z) itself.
+// back; every CTA keeps a full copy of z = x^* (shared memory) and of
+// x = S_lambda(z) (registers) and applies z -= Delta, x = S_lambda(z) itself.
 //
 // Warp roles.  Warps 0..14 consume rows (each thread owns float4 columns
 // t + 480 r); warp 15 is the producer: it reads tau, b and 1/||a||^2 of the
@@ -31,7 +31,7 @@ namespace {
 constexpr int NT = kSolveThreads;   // threads per CTA
 constexpr int NC = NT - 32;          // consumer threads (warps 0..14)
 constexpr int NCW = NC / 32;         // consumer warps
-constexpr int G = 1;                 // rows reduced together
+constexpr int G = 2;                 // rows reduced together
 constexpr int SLOTS_MAX = 16;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(NT, 1)
   const uint32_t rowbytes = (uint32_t)(n4 * 16);
   const int64_t total_rows = (int64_t)rpi * a.K;
 
-  unsigned char* ring = smem;  // slots x rowbytes_pad
+  unsigned char* ring = smem;                                                     // slots x rowbytes_pad
+  float4* zsh = reinterpret_cast<float4*>(smem + (size_t)slots * rowbytes_pad);  // ZREG x NC
 
   if (tid == 0) {
     for (int i = 0; i < slots; ++i) {
@@ -229,9 +230,7 @@ __global__ void __launch_bounds__(NT, 1)
   const float lam = a.lambda;
   const float coef = a.coef;
 
-  // column ownership: float4 columns t + NC*r; z, x and the partial update
-  // of those columns live in registers
-  float4 zr[ZREG];
+  // column ownership: float4 columns t + NC*r
   float4 xr[ZREG];
   float4 dl[ZREG];
 #pragma unroll
@@ -239,7 +238,7 @@ __global__ void __launch_bounds__(NT, 1)
     const int64_t col = tid + (int64_t)NC * r;
     float4 zv = make_float4(0.f, 0.f, 0.f, 0.f);
     if (col < n4) zv = reinterpret_cast<const float4*>(a.z)[col];
-    zr[r] = zv;
+    zsh[(size_t)r * NC + tid] = zv;
     xr[r] = (col < n4) ? mask_tail(soft_shrink4(zv, lam), col, a.n)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
     dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -359,13 +358,13 @@ __global__ void __launch_bounds__(NT, 1)
       for (int r = 0; r < ZREG; ++r) {
         const int64_t col = tid + (int64_t)NC * r;
         if (col < n4) {
-          float4 zv = zr[r];
+          float4 zv = zsh[(size_t)r * NC + tid];
           zv.x -= dl[r].x;
           zv.y -= dl[r].y;
           zv.z -= dl[r].z;
           zv.w -= dl[r].w;
           zv = mask_tail(zv, col, a.n);
-          zr[r] = zv;
+          zsh[(size_t)r * NC + tid] = zv;
           xr[r] = soft_shrink4(zv, lam);
         }
         dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -428,13 +427,13 @@ __global__ void __launch_bounds__(NT, 1)
       const int64_t col = tid + (int64_t)NC * r;
       if (col < n4) {
         const float4 d = __ldcg(dtot + col);
-        float4 zv = zr[r];
+        float4 zv = zsh[(size_t)r * NC + tid];
         zv.x -= d.x;
         zv.y -= d.y;
         zv.z -= d.z;
         zv.w -= d.w;
         zv = mask_tail(zv, col, a.n);
-        zr[r] = zv;
+        zsh[(size_t)r * NC + tid] = zv;
         xr[r] = soft_shrink4(zv, lam);
       }
     }
@@ -447,7 +446,7 @@ __global__ void __launch_bounds__(NT, 1)
     for (int r = 0; r < ZREG; ++r) {
       const int64_t col = tid + (int64_t)NC * r;
       if (col < n4) {
-        zo[col] = zr[r];
+        zo[col] = zsh[(size_t)r * NC + tid];
         xo[col] = xr[r];
       }
     }
@@ -493,7 +492,7 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   P = std::max<int64_t>(1, std::min<int64_t>(P, num_sms));
   const int64_t rowbytes = n4 * 16;
   const int64_t rowbytes_pad = (rowbytes + 127) / 128 * 128;
-  const size_t fixed = 2048;
+  const size_t fixed = (size_t)z * NC * 16 + 2048;
   if (fixed + 2 * rowbytes_pad > smem_optin) return false;
   int64_t slots = (int64_t)((smem_optin - fixed) / rowbytes_pad);
   slots = std::min<int64_t>(slots, SLOTS_MAX);
@@ -502,7 +501,7 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   g->zreg = z;
   g->slots = (int)slots;
   g->rowbytes_pad = (int)rowbytes_pad;
-  g->smem = (size_t)slots * rowbytes_pad;
+  g->smem = (size_t)slots * rowbytes_pad + (size_t)z * NC * 16;
   return true;
 }
 
