@@ -70,23 +70,26 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {"rska_rows_kernel": ["rska_rows.cu", "rska_device.cuh"],
+                  "rska_persistent_kernel": ["rska_solve.cu", "rska_device.cuh"]}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2203_10838_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    for fn in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
-def committed_traffic():
-    """DRAM bytes per launch of the persistent kernel from the committed ncu
-    summary, or None when the kernel source changed since it was taken."""
-    p = os.path.join(ROOT, "profiles", "rska_persistent_traffic.json")
+def committed_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel's source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash(kernel) or d.get("iters_per_launch") != ITERS:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -290,10 +293,10 @@ def run_gpu(args):
     alg_bytes = ITERS * ETA * (4.0 * N + 12.0) + 8.0 * N
     avg_launch_s = statistics.mean(launch_ms) / 1000.0
     achieved = alg_bytes / avg_launch_s / 1e9
+    kname = "rska_rows_kernel" if sol.query("kernel") == 2 else "rska_persistent_kernel"
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": committed_traffic(),
-            "peak_kind": f"{peak_kind} (copy bandwidth)",
-            "kernel": "rska_rows_kernel" if sol.query("kernel") == 2 else "rska_persistent_kernel",
+            "frac": achieved / hbm_peak, "traffic": committed_traffic(kname),
+            "peak_kind": f"{peak_kind} (copy bandwidth)", "kernel": kname,
             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1000.0,
             "grid": sol.query("grid"), "rows_resident": sol.query("rows_resident")}
 
