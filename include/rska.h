@@ -176,6 +176,60 @@ int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
  */
 int rska_set_option(rska_ctx *ctx, int what, int64_t value);
 
+/* ------------------------------------------------------------------------ */
+/* Batched independent systems: eq. (rska) / Algorithm 1 run on P problems   */
+/* (A_p, b_p) in one persistent launch, each with its own index stream       */
+/* (counter word 3 of the index contract = p) and its own stopping test.     */
+/* ------------------------------------------------------------------------ */
+typedef struct rska_batch rska_batch;
+
+/*
+ * rska_batch_setup -- FP64 row norms and alias tables for every problem
+ * (Definition 1; Sec. 5, v1/v2), W_p = sum ||a_i||^2 and ||b_p||^2.
+ *   A       device, borrowed: all matrices, A_p at element offset a_off[p],
+ *           row-major m[p] x n[p] with leading dimension lda[p] (a multiple
+ *           of 4; a_off[p] a multiple of 4; A 16-byte aligned).
+ *   b       device, borrowed: b_p at element offset b_off[p] (m[p] floats).
+ *   a_off, m, n, lda, b_off   HOST arrays of P entries (copied).
+ *   lambda, eta, t, seed      shared by all problems, as for rska_setup.
+ * Limits: n[p] <= 2688.  Synchronizes.  Errors: EINVAL, EUNSUPPORTED, ENOMEM,
+ * ECUDA, and EZEROROW / ENONFINITE of the first failing problem.
+ */
+int rska_batch_setup(rska_batch **out, int32_t P, const float *A, const int64_t *a_off,
+                     const int64_t *m, const int64_t *n, const int64_t *lda, const float *b,
+                     const int64_t *b_off, float lambda, int32_t eta, float t, uint64_t seed,
+                     void *stream);
+
+/*
+ * rska_batch_solve -- from z_p = 0, iterate every problem until its relative
+ * residual ||A_p x - b_p|| / ||b_p|| <= tol (checked every check_every
+ * iterations, 0 = ceil(m_p/eta); the exact FP64-accumulated check runs only
+ * when a running estimate from the sampled residuals is within 4 tol) or
+ * until max_iters.  tol = 0 runs exactly max_iters iterations on every problem.
+ * One CTA per problem, problems taken largest first.  Asynchronous.
+ */
+int rska_batch_solve(rska_batch *bt, int64_t max_iters, double tol, int64_t check_every);
+
+/* rska_batch_results -- HOST outputs (P entries each, nullable): iterations
+ * run and the last exact relative residual per problem.  Synchronizes. */
+int rska_batch_results(rska_batch *bt, int64_t *iters, double *rel_res);
+
+/* rska_batch_offsets -- HOST: P+1 offsets of each problem's x / z in the
+ * packed outputs (n rounded up to 4 per problem). */
+int rska_batch_offsets(rska_batch *bt, int64_t *x_off);
+
+/* rska_batch_get_x -- copy the packed x = S_lambda(z) and z (device, length
+ * x_off[P] each, either may be NULL).  Synchronizes. */
+int rska_batch_get_x(rska_batch *bt, float *x_out, float *z_out);
+
+/* rska_batch_get_tables -- copy the packed FP64 row norms, thresholds and
+ * aliases (device, sum of m[p] entries each, problem p's rows after those of
+ * problems 0..p-1; either may be NULL).  Synchronizes. */
+int rska_batch_get_tables(rska_batch *bt, double *nu_out, uint32_t *thr_out, int32_t *alias_out);
+
+/* rska_batch_destroy -- free the batch's device memory. */
+int rska_batch_destroy(rska_batch *bt);
+
 /*
  * rska_solve_noalloc -- one-shot solve that allocates no device memory.  The
  * paper has no counterpart: this exists for callers that cannot call

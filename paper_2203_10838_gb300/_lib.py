@@ -37,6 +37,13 @@ def _declare(lib):
         "rska_destroy": ([P], c_int),
         "rska_query": ([P, c_int, ctypes.POINTER(i64)], c_int),
         "rska_set_option": ([P, c_int, i64], c_int),
+        "rska_batch_setup": ([PP, i32, P, P, P, P, P, P, P, f32, i32, f32, u64, P], c_int),
+        "rska_batch_solve": ([P, i64, f64, i64], c_int),
+        "rska_batch_results": ([P, P, P], c_int),
+        "rska_batch_offsets": ([P, P], c_int),
+        "rska_batch_get_x": ([P, P, P], c_int),
+        "rska_batch_get_tables": ([P, P, P, P], c_int),
+        "rska_batch_destroy": ([P], c_int),
         "rska_solve_noalloc": ([P, i64, i64, i64, P, f32, i32, f32, u64, i64, P, P, P], c_int),
         "rska_strerror": ([c_int], ctypes.c_char_p),
     }

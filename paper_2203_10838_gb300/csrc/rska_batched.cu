@@ -1,0 +1,844 @@
+// rska_batched.cu -- many independent RSKA systems in one persistent launch
+// (eq. rska, Algorithm 1 with w_i = t, run on every (A_p, b_p) with its own
+// index stream), each stopping by itself at a relative residual
+// ||A_p x - b_p|| / ||b_p|| <= tol (Algorithm 1, "until a stopping criterion
+// is satisfied").
+//
+// One CTA owns one problem at a time and takes problems from a queue sorted
+// by estimated work (largest first).  Inside a CTA, warps 0..6 consume rows:
+// each thread owns float4 columns t + 224 r of z, x (and the partial update),
+// so a row's dot is a block reduction and its update c_s a_s is local.  Warp
+// 7 produces: it draws tau_k on the fly (Philox4x32-10 + alias table, 32 slots
+// per warp step, counter word 3 = problem id) and copies each drawn row with
+// one TMA bulk copy into a ring of shared-memory slots as soon as the slot is
+// released.
+//
+// Stopping: every C_p iterations the CTA first looks at an unbiased estimate
+// of ||A_p x - b_p||^2 built for free from the sampled residuals
+// (sum of r_s^2 / (eta p_s) over the window, p_s = ||a_s||^2 / W_p); only when
+// it is within (4 tol)^2 ||b_p||^2 does it run the exact check (FP32
+// products, FP64 accumulation, one pass over A_p).  Every device-side wait is
+// bounded.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "rska_alias.cuh"
+#include "rska_device.cuh"
+#include "rska_internal.h"
+
+namespace rska {
+
+namespace {
+
+constexpr int BT = 256;          // threads per CTA
+constexpr int BC = BT - 32;      // consumer threads (warps 0..6)
+constexpr int BCW = BC / 32;     // consumer warps
+constexpr int BG = 2;            // rows reduced together
+constexpr int BZ = kBatchMaxZ;   // float4 columns per consumer thread
+constexpr int BSLOTS = 6;        // ring slots
+constexpr int BCTAS_PER_SM = 3;
+
+struct BatchArgs {
+  int32_t P;
+  const int32_t* order;      // problems, largest first
+  const float* A;
+  const int64_t* a_off;      // element offset of A_p
+  const int32_t* m;
+  const int32_t* n;
+  const int64_t* lda;
+  const float* b;
+  const int64_t* b_off;
+  const int64_t* row_off;    // offset of problem p's rows in the per-row tables
+  const float* inv_nu;
+  const uint32_t* thr;
+  const int32_t* alias;
+  const double* W;           // sum of ||a_i||^2 per problem
+  const double* bnorm2;      // ||b_p||^2
+  const int64_t* x_off;      // offset of problem p in z / x (n rounded up to 4)
+  float* z;
+  float* x;
+  int64_t* iters;
+  double* relres;
+  float lambda;
+  float coef;                // t / eta
+  int32_t eta;
+  uint64_t seed;
+  int64_t max_iters;
+  double tol;                // 0: run max_iters on every problem
+  int64_t check_every;       // 0: ceil(m_p / eta)
+  int* queue;
+  int* status;
+  uint64_t limit_ns;
+  int rowbytes_pad;          // bytes per ring slot
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity, uint64_t limit_ns,
+                                                  const volatile int* abort) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  uint32_t spins = 0;
+  while (!mbar_try_wait(b, parity)) {
+    if ((++spins & 63u) == 0) {
+      if (global_timer_ns() - t0 > limit_ns) return false;
+      if (abort != nullptr && *abort) return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(BC) : "memory");
+}
+
+__device__ __forceinline__ int consumer_sync_or(int pred) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
+      " selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(pred), "n"(BC)
+      : "memory");
+  return r;
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+
+__device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
+  const int64_t base = gc * 4;
+  float4 r = v;
+  if (base + 0 >= n) r.x = 0.f;
+  if (base + 1 >= n) r.y = 0.f;
+  if (base + 2 >= n) r.z = 0.f;
+  if (base + 3 >= n) r.w = 0.f;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Setup: FP64 row norms in the canonical order (one CTA per problem, one warp
+// per row), then one thread per problem builds its alias table and sums W_p
+// and ||b_p||^2.
+// ---------------------------------------------------------------------------
+__global__ void batch_norms_kernel(BatchArgs a, double* nu, float* inv_nu, int* pstat) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
+    const int m = a.m[p], n = a.n[p];
+    const float* Ap = a.A + a.a_off[p];
+    const float* bp = a.b + a.b_off[p];
+    const int64_t lda = a.lda[p];
+    const int64_t ro = a.row_off[p];
+    for (int i = warp; i < m; i += nw) {
+      const float* row = Ap + (int64_t)i * lda;
+      double acc = 0.0;
+      bool finite = true;
+      for (int j = lane; j < n; j += 32) {
+        const float v = __ldg(row + j);
+        finite = finite && isfinite(v);
+        const double vd = (double)v;
+        acc = __fma_rn(vd, vd, acc);
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+      finite = __all_sync(0xffffffffu, finite);
+      if (lane == 0) {
+        const float bi = __ldg(bp + i);
+        if (!finite || !isfinite(bi) || !isfinite(acc))
+          atomicCAS(pstat + p, kStatusOk, kStatusNonFinite);
+        else if (acc == 0.0)
+          atomicCAS(pstat + p, kStatusOk, kStatusZeroRow);
+        nu[ro + i] = acc;
+        inv_nu[ro + i] = (acc > 0.0) ? (float)__ddiv_rn(1.0, acc) : 0.0f;
+      }
+    }
+  }
+}
+
+__global__ void batch_alias_kernel(BatchArgs a, const double* nu, double* q, int32_t* stk,
+                                   uint32_t* thr, int32_t* alias, double* W, double* bnorm2,
+                                   const int* pstat) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  const int m = a.m[p];
+  const int64_t ro = a.row_off[p];
+  const float* bp = a.b + a.b_off[p];
+  double bb = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double bi = (double)bp[i];
+    bb = __fma_rn(bi, bi, bb);
+  }
+  bnorm2[p] = bb;
+  if (pstat[p] != kStatusOk) {
+    W[p] = 0.0;
+    return;
+  }
+  double w = 0.0;
+  for (int i = 0; i < m; ++i) w = __dadd_rn(w, nu[ro + i]);
+  W[p] = w;
+  const double md = (double)m;
+  for (int i = 0; i < m; ++i) q[ro + i] = __ddiv_rn(__dmul_rn(nu[ro + i], md), w);
+  vose_sequential<int32_t>(q + ro, stk + ro, m, thr + ro, alias + ro);
+}
+
+// ---------------------------------------------------------------------------
+// The persistent batched solver.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[BSLOTS];
+  __shared__ __align__(8) uint64_t empty[BSLOTS];
+  __shared__ float wpart[2][BCW][BG];
+  __shared__ float sb[BSLOTS];
+  __shared__ float siv[BSLOTS];
+  __shared__ double dpart[BCW];
+  __shared__ int s_prob;
+  __shared__ volatile int s_allow;   // producer may issue iterations < s_allow
+  __shared__ volatile int s_stop;    // the current problem is finished
+  __shared__ volatile int s_abort;
+  __shared__ int s_gate;
+  __shared__ double s_relres;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int eta = a.eta;
+  unsigned char* ring = smem;
+  float4* zsh = reinterpret_cast<float4*>(smem + (size_t)BSLOTS * a.rowbytes_pad);  // BZ x BC
+
+  if (tid == 0) {
+    for (int i = 0; i < BSLOTS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], BCW);
+    }
+    s_abort = 0;
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+
+  int64_t prod = 0;  // rows issued by this CTA (producer lane 0)
+  int64_t cons = 0;  // rows consumed by this CTA
+  int gcount = 0;
+
+  for (;;) {
+    if (tid == 0) {
+      const int qi = atomicAdd(a.queue, 1);
+      s_prob = (qi < a.P && ld_relaxed_s32(a.status) == kStatusOk) ? a.order[qi] : -1;
+      s_stop = 0;
+    }
+    __syncthreads();
+    const int p = s_prob;
+    if (p < 0) break;
+    const int m = a.m[p];
+    const int n = a.n[p];
+    const int64_t n4 = (n + 3) >> 2;
+    const int64_t lda = a.lda[p];
+    const float* Ap = a.A + a.a_off[p];
+    const float* bp = a.b + a.b_off[p];
+    const int64_t ro = a.row_off[p];
+    const uint32_t rowbytes = (uint32_t)(n4 * 16);
+    const int64_t C = a.check_every > 0 ? a.check_every : (m + eta - 1) / eta;
+    const int64_t kmax = a.max_iters;
+    if (tid == 0) {
+      s_allow = (int)(C < kmax ? C : kmax);
+      s_relres = -1.0;
+    }
+    __syncthreads();
+
+    if (warp == BCW) {
+      // ------------------------------------------------------- producer --
+      bool bad = false;
+      for (int64_t jj = 0; jj < kmax && !bad; ++jj) {
+        // wait until the consumers allow iteration jj (or stop the problem)
+        if (lane == 0) {
+          const uint64_t t0 = global_timer_ns();
+          uint32_t spins = 0;
+          while (jj >= s_allow && !s_stop && !s_abort) {
+            if ((++spins & 63u) == 0 && global_timer_ns() - t0 > a.limit_ns) {
+              atomicCAS(a.status, kStatusOk, kStatusTimeout);
+              s_abort = 1;
+            }
+          }
+        }
+        __syncwarp();
+        if (s_stop || s_abort) break;
+        for (int s0 = 0; s0 < eta && !bad; s0 += 32) {
+          const int s = s0 + lane;
+          int32_t row = 0;
+          float bv = 0.f, ivv = 0.f;
+          {
+            int32_t i0, i1;
+            draw_pair(a.seed, jj, (uint32_t)(s >> 1), (uint32_t)p, a.thr + ro, a.alias + ro,
+                      (uint32_t)m, &i0, &i1);
+            row = (s & 1) ? i1 : i0;
+            if (s < eta) {
+              bv = __ldg(bp + row);
+              ivv = __ldg(a.inv_nu + ro + row);
+            }
+          }
+          const int cnt = min(32, eta - s0);
+          for (int i = 0; i < cnt; ++i) {
+            const int32_t r_i = __shfl_sync(0xffffffffu, row, i);
+            const float b_i = __shfl_sync(0xffffffffu, bv, i);
+            const float iv_i = __shfl_sync(0xffffffffu, ivv, i);
+            int fail = 0;
+            if (lane == 0) {
+              const int sl = (int)(prod % BSLOTS);
+              const int64_t use = prod / BSLOTS;
+              if (use > 0 && !mbar_wait_bounded(&empty[sl], (uint32_t)((use - 1) & 1), a.limit_ns,
+                                                &s_abort))
+                fail = 1;
+              if (!fail) {
+                sb[sl] = b_i;
+                siv[sl] = iv_i;
+                mbar_expect_tx(&full[sl], rowbytes);
+                tma_load_1d(ring + (size_t)sl * a.rowbytes_pad, Ap + (int64_t)r_i * lda, rowbytes,
+                            &full[sl]);
+                ++prod;
+              }
+            }
+            if (__shfl_sync(0xffffffffu, fail, 0)) {
+              if (lane == 0) {
+                atomicCAS(a.status, kStatusOk, kStatusTimeout);
+                s_abort = 1;
+              }
+              bad = true;
+              break;
+            }
+          }
+        }
+      }
+    } else {
+      // ------------------------------------------------------ consumers --
+      const float lam = a.lambda;
+      const float coef = a.coef;
+      const double w_over_eta = a.W[p] / (double)eta;
+      float4 xr[BZ], dl[BZ];
+#pragma unroll
+      for (int r = 0; r < BZ; ++r) {
+        xr[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        zsh[(size_t)r * BC + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      double est = 0.0;  // thread 0: windowed estimate of ||A x - b||^2 (times C)
+      float4 av[BG][BZ];
+      float bg[BG], ivg[BG];
+      int64_t k = 0;
+      bool fail = false;
+      for (; k < kmax; ++k) {
+        for (int q0 = 0; q0 < eta; q0 += BG) {
+          const int ng = min(BG, eta - q0);
+          int tmo = 0;
+#pragma unroll
+          for (int g = 0; g < BG; ++g) {
+            bg[g] = 0.f;
+            ivg[g] = 0.f;
+            if (g < ng) {
+              const int64_t gi = cons + g;
+              const int sl = (int)(gi % BSLOTS);
+              if (lane == 0 && !mbar_wait_bounded(&full[sl], (uint32_t)((gi / BSLOTS) & 1),
+                                                  a.limit_ns, &s_abort))
+                tmo = 1;
+              __syncwarp();
+              const float4* rowp =
+                  reinterpret_cast<const float4*>(ring + (size_t)sl * a.rowbytes_pad);
+#pragma unroll
+              for (int r = 0; r < BZ; ++r) {
+                const int64_t col = tid + (int64_t)BC * r;
+                float4 v = (col < n4) ? rowp[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (col == n4 - 1) v = mask_tail(v, col, n);
+                av[g][r] = v;
+              }
+              bg[g] = sb[sl];
+              ivg[g] = siv[sl];
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&empty[sl]);
+            } else {
+#pragma unroll
+              for (int r = 0; r < BZ; ++r) av[g][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+          float pd[BG];
+#pragma unroll
+          for (int g = 0; g < BG; ++g) {
+            pd[g] = 0.f;
+#pragma unroll
+            for (int r = 0; r < BZ; ++r) pd[g] += dot4(av[g][r], xr[r]);
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) pd[g] += __shfl_xor_sync(0xffffffffu, pd[g], o);
+          }
+          const int wp = gcount & 1;
+          ++gcount;
+          if (lane == 0) {
+#pragma unroll
+            for (int g = 0; g < BG; ++g) wpart[wp][warp][g] = pd[g];
+          }
+          if (consumer_sync_or(tmo)) {
+            fail = true;
+            break;
+          }
+          cons += ng;
+#pragma unroll
+          for (int g = 0; g < BG; ++g) {
+            float d = (lane < BCW) ? wpart[wp][lane][g] : 0.f;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (g < ng) {
+              const float r = d - bg[g];
+              if (tid == 0) est += w_over_eta * (double)r * (double)r * (double)ivg[g];
+              const float cval = coef * (r * ivg[g]);
+#pragma unroll
+              for (int rr = 0; rr < BZ; ++rr) {
+                dl[rr].x = fmaf(cval, av[g][rr].x, dl[rr].x);
+                dl[rr].y = fmaf(cval, av[g][rr].y, dl[rr].y);
+                dl[rr].z = fmaf(cval, av[g][rr].z, dl[rr].z);
+                dl[rr].w = fmaf(cval, av[g][rr].w, dl[rr].w);
+              }
+            }
+          }
+        }
+        if (fail) break;
+        // z -= Delta, x = S_lambda(z) on this thread's columns
+#pragma unroll
+        for (int r = 0; r < BZ; ++r) {
+          const int64_t col = tid + (int64_t)BC * r;
+          if (col < n4) {
+            float4 zv = zsh[(size_t)r * BC + tid];
+            zv.x -= dl[r].x;
+            zv.y -= dl[r].y;
+            zv.z -= dl[r].z;
+            zv.w -= dl[r].w;
+            zv = mask_tail(zv, col, n);
+            zsh[(size_t)r * BC + tid] = zv;
+            xr[r] = soft_shrink4(zv, lam);
+          }
+          dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const bool last = (k + 1 == kmax);
+        if ((k + 1) % C != 0 && !last) continue;
+
+        // ---- check point: gate on the estimate, then the exact residual ----
+        if (tid == 0) {
+          const double window = (double)((k + 1) % C == 0 ? C : (k + 1) % C);
+          const double est_mean = est / window;
+          est = 0.0;
+          const double lim = 4.0 * a.tol;
+          s_gate = last || (a.tol > 0.0 && est_mean <= lim * lim * a.bnorm2[p]);
+        }
+        consumer_sync();
+        if (s_gate) {
+          // exact check: one warp per row, FP32 products within a lane, FP64 across
+          double acc = 0.0;
+          for (int i = warp; i < m; i += BCW) {
+            const float4* row = reinterpret_cast<const float4*>(Ap + (int64_t)i * lda);
+            float part = 0.f;
+            for (int64_t c4 = lane; c4 < n4; c4 += 32) {
+              float4 v = __ldg(row + c4);
+              if (c4 == n4 - 1) v = mask_tail(v, c4, n);
+              const float4 zv = zsh[c4];  // column c4 lives at [c4 / BC][c4 % BC]
+              part += dot4(v, soft_shrink4(zv, lam));
+            }
+            double d = (double)part;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (lane == 0) {
+              const double ri = d - (double)__ldg(bp + i);
+              acc += ri * ri;
+            }
+          }
+          if (lane == 0) dpart[warp] = acc;
+          consumer_sync();
+          if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < BCW; ++w) tot += dpart[w];
+            const double bb = a.bnorm2[p];
+            s_relres = sqrt(tot) / (bb > 0.0 ? sqrt(bb) : 1e-30);
+          }
+          consumer_sync();
+          if ((a.tol > 0.0 && s_relres <= a.tol) || last) {
+            k += 1;
+            break;
+          }
+        }
+        if (tid == 0) {
+          const int64_t nxt = k + 1 + C;
+          s_allow = (int)(nxt < kmax ? nxt : kmax);
+        }
+        consumer_sync();
+      }
+      // problem finished (or failed): publish results, release the producer
+      if (tid == 0) {
+        s_stop = 1;
+        if (fail) {
+          atomicCAS(a.status, kStatusOk, kStatusTimeout);
+          s_abort = 1;
+        }
+        a.iters[p] = k;
+        a.relres[p] = s_relres;
+      }
+      float* zo = a.z + a.x_off[p];
+      float* xo = a.x + a.x_off[p];
+#pragma unroll
+      for (int r = 0; r < BZ; ++r) {
+        const int64_t col = tid + (int64_t)BC * r;
+        if (col < n4) {
+          reinterpret_cast<float4*>(zo)[col] = zsh[(size_t)r * BC + tid];
+          reinterpret_cast<float4*>(xo)[col] = xr[r];
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+  }
+  // let every copy this CTA issued land before the CTA's shared memory goes away
+  if (tid == BC) {
+    for (int64_t g = 0; g < BSLOTS && prod - g - 1 >= 0; ++g) {
+      const int64_t gi = prod - 1 - g;
+      mbar_wait_bounded(&full[gi % BSLOTS], (uint32_t)((gi / BSLOTS) & 1), a.limit_ns, nullptr);
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace
+}  // namespace rska
+
+using rska::BatchArgs;
+
+struct rska_batch {
+  int32_t P = 0;
+  int32_t eta = 1;
+  float lambda = 0.f, t = 1.f;
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int64_t total_rows = 0, total_x = 0;
+  int max_n4 = 0;
+  std::vector<int64_t> h_x_off;
+  // device
+  const float* A = nullptr;
+  const float* b = nullptr;
+  int32_t* d_order = nullptr;
+  int64_t* d_a_off = nullptr;
+  int32_t* d_m = nullptr;
+  int32_t* d_n = nullptr;
+  int64_t* d_lda = nullptr;
+  int64_t* d_b_off = nullptr;
+  int64_t* d_row_off = nullptr;
+  int64_t* d_x_off = nullptr;
+  double* nu = nullptr;
+  float* inv_nu = nullptr;
+  uint32_t* thr = nullptr;
+  int32_t* alias = nullptr;
+  double* W = nullptr;
+  double* bnorm2 = nullptr;
+  float* z = nullptr;
+  float* x = nullptr;
+  int64_t* iters = nullptr;
+  double* relres = nullptr;
+  int* pstat = nullptr;
+  int* queue = nullptr;
+  int* status = nullptr;
+  int sticky = RSKA_OK;
+  uint64_t limit_ns = 2000000000ull;
+};
+
+namespace {
+
+void batch_free(rska_batch* bt) {
+  void* ptrs[] = {bt->d_order, bt->d_a_off, bt->d_m,   bt->d_n,     bt->d_lda,  bt->d_b_off,
+                  bt->d_row_off, bt->d_x_off, bt->nu,  bt->inv_nu,  bt->thr,    bt->alias,
+                  bt->W,       bt->bnorm2,  bt->z,     bt->x,       bt->iters,  bt->relres,
+                  bt->pstat,   bt->queue,   bt->status};
+  for (void* p : ptrs) cudaFree(p);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+BatchArgs make_args(rska_batch* bt) {
+  BatchArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.P = bt->P;
+  a.order = bt->d_order;
+  a.A = bt->A;
+  a.a_off = bt->d_a_off;
+  a.m = bt->d_m;
+  a.n = bt->d_n;
+  a.lda = bt->d_lda;
+  a.b = bt->b;
+  a.b_off = bt->d_b_off;
+  a.row_off = bt->d_row_off;
+  a.inv_nu = bt->inv_nu;
+  a.thr = bt->thr;
+  a.alias = bt->alias;
+  a.W = bt->W;
+  a.bnorm2 = bt->bnorm2;
+  a.x_off = bt->d_x_off;
+  a.z = bt->z;
+  a.x = bt->x;
+  a.iters = bt->iters;
+  a.relres = bt->relres;
+  a.lambda = bt->lambda;
+  a.coef = bt->t / (float)bt->eta;
+  a.eta = bt->eta;
+  a.seed = bt->seed;
+  a.queue = bt->queue;
+  a.status = bt->status;
+  a.limit_ns = bt->limit_ns;
+  a.rowbytes_pad = (int)(((int64_t)bt->max_n4 * 16 + 127) / 128 * 128);
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rska_batch_setup(rska_batch** out, int32_t P, const float* A, const int64_t* a_off,
+                     const int64_t* m, const int64_t* n, const int64_t* lda, const float* b,
+                     const int64_t* b_off, float lambda, int32_t eta, float t, uint64_t seed,
+                     void* stream) {
+  if (!out) return RSKA_EINVAL;
+  *out = nullptr;
+  if (P < 1 || !A || !b || !a_off || !m || !n || !lda || !b_off || eta < 1 ||
+      eta > rska::kMaxEta || !(lambda >= 0.f) || !std::isfinite(lambda) || !(t > 0.f) ||
+      !std::isfinite(t))
+    return RSKA_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(A) % 16) != 0) return RSKA_EINVAL;
+  std::vector<int32_t> hm(P), hn(P);
+  std::vector<int64_t> row_off(P), x_off(P + 1);
+  int64_t rows = 0, xs = 0;
+  int max_n4 = 1;
+  for (int32_t p = 0; p < P; ++p) {
+    if (m[p] < 1 || n[p] < 1 || lda[p] < n[p] || (lda[p] % 4) != 0 || (a_off[p] % 4) != 0 ||
+        a_off[p] < 0 || b_off[p] < 0 || m[p] > 0x7fffffff)
+      return RSKA_EINVAL;
+    const int64_t n4 = (n[p] + 3) / 4;
+    if (n4 > (int64_t)rska::BC * rska::BZ) return RSKA_EUNSUPPORTED;
+    hm[p] = (int32_t)m[p];
+    hn[p] = (int32_t)n[p];
+    row_off[p] = rows;
+    rows += m[p];
+    x_off[p] = xs;
+    xs += n4 * 4;
+    max_n4 = std::max<int>(max_n4, (int)n4);
+  }
+  x_off[P] = xs;
+  // largest estimated work first (iterations and bytes per iteration both grow with n)
+  std::vector<int32_t> order(P);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t u, int32_t v) {
+    const double wu = (double)hn[u] * hn[u] + (double)hm[u] * hn[u] / eta;
+    const double wv = (double)hn[v] * hn[v] + (double)hm[v] * hn[v] / eta;
+    return wu > wv;
+  });
+
+  rska_batch* bt = new (std::nothrow) rska_batch;
+  if (!bt) return RSKA_ENOMEM;
+  bt->P = P;
+  bt->eta = eta;
+  bt->lambda = lambda;
+  bt->t = t;
+  bt->seed = seed;
+  bt->stream = static_cast<cudaStream_t>(stream);
+  bt->A = A;
+  bt->b = b;
+  bt->total_rows = rows;
+  bt->total_x = xs;
+  bt->max_n4 = max_n4;
+  bt->h_x_off = x_off;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&bt->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  double* q = nullptr;
+  int32_t* stk = nullptr;
+  if (e == cudaSuccess &&
+      ((e = dalloc(&bt->d_order, P)) != cudaSuccess || (e = dalloc(&bt->d_a_off, P)) != cudaSuccess ||
+       (e = dalloc(&bt->d_m, P)) != cudaSuccess || (e = dalloc(&bt->d_n, P)) != cudaSuccess ||
+       (e = dalloc(&bt->d_lda, P)) != cudaSuccess || (e = dalloc(&bt->d_b_off, P)) != cudaSuccess ||
+       (e = dalloc(&bt->d_row_off, P)) != cudaSuccess ||
+       (e = dalloc(&bt->d_x_off, P + 1)) != cudaSuccess || (e = dalloc(&bt->nu, rows)) != cudaSuccess ||
+       (e = dalloc(&bt->inv_nu, rows)) != cudaSuccess || (e = dalloc(&bt->thr, rows)) != cudaSuccess ||
+       (e = dalloc(&bt->alias, rows)) != cudaSuccess || (e = dalloc(&bt->W, P)) != cudaSuccess ||
+       (e = dalloc(&bt->bnorm2, P)) != cudaSuccess || (e = dalloc(&bt->z, xs)) != cudaSuccess ||
+       (e = dalloc(&bt->x, xs)) != cudaSuccess || (e = dalloc(&bt->iters, P)) != cudaSuccess ||
+       (e = dalloc(&bt->relres, P)) != cudaSuccess || (e = dalloc(&bt->pstat, P)) != cudaSuccess ||
+       (e = dalloc(&bt->queue, 1)) != cudaSuccess || (e = dalloc(&bt->status, 1)) != cudaSuccess ||
+       (e = dalloc(&q, rows)) != cudaSuccess || (e = dalloc(&stk, rows)) != cudaSuccess)) {
+  }
+  cudaStream_t s = bt->stream;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_order, order.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_a_off, a_off, sizeof(int64_t) * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_m, hm.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_n, hn.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_lda, lda, sizeof(int64_t) * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_b_off, b_off, sizeof(int64_t) * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_row_off, row_off.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_x_off, x_off.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->pstat, 0, sizeof(int) * P, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->z, 0, sizeof(float) * xs, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->x, 0, sizeof(float) * xs, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->iters, 0, sizeof(int64_t) * P, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->relres, 0, sizeof(double) * P, s);
+  if (e == cudaSuccess) {
+    BatchArgs a = make_args(bt);
+    const int nblk = std::min<int>(P, bt->num_sms * 8);
+    rska::batch_norms_kernel<<<nblk, 256, 0, s>>>(a, bt->nu, bt->inv_nu, bt->pstat);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      rska::batch_alias_kernel<<<(P + 63) / 64, 64, 0, s>>>(a, bt->nu, q, stk, bt->thr, bt->alias,
+                                                            bt->W, bt->bnorm2, bt->pstat);
+      e = cudaGetLastError();
+    }
+  }
+  std::vector<int> hst(P, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), bt->pstat, sizeof(int) * P, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(q);
+  cudaFree(stk);
+  if (e != cudaSuccess) {
+    batch_free(bt);
+    delete bt;
+    return (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+  }
+  for (int32_t p = 0; p < P; ++p) {
+    if (hst[p] != 0) {
+      batch_free(bt);
+      delete bt;
+      return hst[p];
+    }
+  }
+  *out = bt;
+  return RSKA_OK;
+}
+
+int rska_batch_solve(rska_batch* bt, int64_t max_iters, double tol, int64_t check_every) {
+  if (!bt || max_iters < 1 || !(tol >= 0.0) || check_every < 0) return RSKA_EINVAL;
+  if (bt->sticky) return bt->sticky;
+  cudaStream_t s = bt->stream;
+  BatchArgs a = make_args(bt);
+  a.max_iters = max_iters;
+  a.tol = tol;
+  a.check_every = check_every;
+  const size_t smem = (size_t)rska::BSLOTS * a.rowbytes_pad + (size_t)rska::BZ * rska::BC * 16;
+  cudaError_t e = cudaFuncSetAttribute(rska::rska_batched_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->queue, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->z, 0, sizeof(float) * bt->total_x, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bt->x, 0, sizeof(float) * bt->total_x, s);
+  int blocks_per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, rska::rska_batched_kernel,
+                                                      rska::BT, smem);
+  if (e == cudaSuccess) {
+    const int grid = std::max(1, std::min<int>(bt->P, bt->num_sms * std::max(1, blocks_per_sm)));
+    rska::rska_batched_kernel<<<grid, rska::BT, smem, s>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    bt->sticky = RSKA_ECUDA;
+    return RSKA_ECUDA;
+  }
+  return RSKA_OK;
+}
+
+int rska_batch_results(rska_batch* bt, int64_t* iters, double* rel_res) {
+  if (!bt) return RSKA_EINVAL;
+  cudaStream_t s = bt->stream;
+  int st = 0;
+  cudaError_t e = cudaSuccess;
+  if (iters) e = cudaMemcpyAsync(iters, bt->iters, sizeof(int64_t) * bt->P, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && rel_res)
+    e = cudaMemcpyAsync(rel_res, bt->relres, sizeof(double) * bt->P, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, bt->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return RSKA_ECUDA;
+  if (st != 0) bt->sticky = st;
+  return st;
+}
+
+int rska_batch_get_x(rska_batch* bt, float* x_out, float* z_out) {
+  if (!bt) return RSKA_EINVAL;
+  cudaStream_t s = bt->stream;
+  cudaError_t e = cudaSuccess;
+  if (x_out) e = cudaMemcpyAsync(x_out, bt->x, sizeof(float) * bt->total_x, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && z_out)
+    e = cudaMemcpyAsync(z_out, bt->z, sizeof(float) * bt->total_x, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? RSKA_OK : RSKA_ECUDA;
+}
+
+int rska_batch_offsets(rska_batch* bt, int64_t* x_off) {
+  if (!bt || !x_off) return RSKA_EINVAL;
+  std::memcpy(x_off, bt->h_x_off.data(), sizeof(int64_t) * (bt->P + 1));
+  return RSKA_OK;
+}
+
+int rska_batch_get_tables(rska_batch* bt, double* nu_out, uint32_t* thr_out, int32_t* alias_out) {
+  if (!bt) return RSKA_EINVAL;
+  cudaStream_t s = bt->stream;
+  const size_t R = (size_t)bt->total_rows;
+  cudaError_t e = cudaSuccess;
+  if (nu_out) e = cudaMemcpyAsync(nu_out, bt->nu, sizeof(double) * R, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && thr_out)
+    e = cudaMemcpyAsync(thr_out, bt->thr, sizeof(uint32_t) * R, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && alias_out)
+    e = cudaMemcpyAsync(alias_out, bt->alias, sizeof(int32_t) * R, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? RSKA_OK : RSKA_ECUDA;
+}
+
+int rska_batch_destroy(rska_batch* bt) {
+  if (!bt) return RSKA_EINVAL;
+  cudaStreamSynchronize(bt->stream);
+  batch_free(bt);
+  delete bt;
+  return RSKA_OK;
+}
+
+}  // extern "C"

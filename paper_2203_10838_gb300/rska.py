@@ -169,3 +169,75 @@ def rska_solve_noalloc(A: torch.Tensor, b: torch.Tensor, lam: float, eta: int, t
                                    int(seed), int(K), _dptr(x), _dptr(z), _stream_ptr(stream)),
           "rska_solve_noalloc")
     return x, z
+
+
+class BatchSolver:
+    """Many independent problems in one persistent launch (rska_batch_*).
+
+    A: packed float32 CUDA tensor holding every A_p at element offset a_off[p]
+    (row-major, leading dimension lda[p]); b: packed float32 CUDA tensor with
+    b_p at b_off[p].  a_off, m, n, lda, b_off: integer sequences (host).
+    """
+
+    def __init__(self, A: torch.Tensor, b: torch.Tensor, a_off, m, n, lda, b_off, lam: float,
+                 eta: int, t: float, seed: int, stream=None):
+        import numpy as np
+        self.A, self.b = A, b
+        self.P = len(m)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = A.device
+        self._host = [np.ascontiguousarray(v, dtype=np.int64) for v in (a_off, m, n, lda, b_off)]
+        ptrs = [ctypes.c_void_p(v.ctypes.data) for v in self._host]
+        h = ctypes.c_void_p()
+        check(lib().rska_batch_setup(ctypes.byref(h), self.P, _dptr(A), *ptrs[:4], _dptr(b),
+                                     ptrs[4], float(lam), int(eta), float(t), int(seed),
+                                     _stream_ptr(self.stream)), "rska_batch_setup")
+        self._h = h
+        self.x_off = np.zeros(self.P + 1, dtype=np.int64)
+        check(lib().rska_batch_offsets(self._h, ctypes.c_void_p(self.x_off.ctypes.data)),
+              "rska_batch_offsets")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rska_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, max_iters: int, tol: float = 0.0, check_every: int = 0):
+        check(lib().rska_batch_solve(self._h, int(max_iters), float(tol), int(check_every)),
+              "rska_batch_solve")
+
+    def results(self):
+        import numpy as np
+        it = np.zeros(self.P, dtype=np.int64)
+        rr = np.zeros(self.P, dtype=np.float64)
+        check(lib().rska_batch_results(self._h, ctypes.c_void_p(it.ctypes.data),
+                                       ctypes.c_void_p(rr.ctypes.data)), "rska_batch_results")
+        return it, rr
+
+    def get_x(self):
+        total = int(self.x_off[-1])
+        x = torch.empty(total, dtype=torch.float32, device=self.device)
+        z = torch.empty(total, dtype=torch.float32, device=self.device)
+        check(lib().rska_batch_get_x(self._h, _dptr(x), _dptr(z)), "rska_batch_get_x")
+        return x, z
+
+    def get_tables(self):
+        rows = int(sum(int(v) for v in self._host[1]))
+        nu = torch.empty(rows, dtype=torch.float64, device=self.device)
+        thr = torch.empty(rows, dtype=torch.int32, device=self.device)
+        alias = torch.empty(rows, dtype=torch.int32, device=self.device)
+        check(lib().rska_batch_get_tables(self._h, _dptr(nu), _dptr(thr), _dptr(alias)),
+              "rska_batch_get_tables")
+        return nu, thr, alias

@@ -56,7 +56,8 @@ def gaussian_problem(m: int, n: int, s: int, seed: int, noise: float = 0.0,
     s = min(s, n)
     support = rng.choice(n, size=s, replace=False)
     xhat[support] = rng.standard_normal(s)
-    b64 = A[:, :n].astype(np.float64) @ xhat
+    # b = A xhat in FP64; only the support columns of A contribute
+    b64 = A[:, support].astype(np.float64) @ xhat[support]
     if noise > 0.0:
         g = rng.standard_normal(m)
         b64 = b64 + noise * np.linalg.norm(b64) * g / np.linalg.norm(g)
@@ -79,3 +80,25 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
     lsb = (u >> 16) & 1
     r = ((u + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
     return r.view(np.float32)
+
+
+def pack_batch(problems):
+    """Concatenate Problems for the batched interface: returns (A_flat, a_off,
+    m, n, lda, b_flat, b_off) with every A_p starting on a 16-byte boundary."""
+    a_off, b_off, m, n, lda = [], [], [], [], []
+    total_a = total_b = 0
+    for pr in problems:
+        a_off.append(total_a)
+        b_off.append(total_b)
+        m.append(pr.m)
+        n.append(pr.n)
+        lda.append(pr.lda)
+        total_a += round_up(pr.m * pr.lda, 4)
+        total_b += pr.m
+    A = np.zeros(total_a, dtype=np.float32)
+    b = np.zeros(total_b, dtype=np.float32)
+    for pr, ao, bo in zip(problems, a_off, b_off):
+        A[ao:ao + pr.m * pr.lda] = pr.A.ravel()
+        b[bo:bo + pr.m] = pr.b
+    as64 = lambda v: np.asarray(v, dtype=np.int64)
+    return A, as64(a_off), as64(m), as64(n), as64(lda), b, as64(b_off)
