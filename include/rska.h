@@ -203,7 +203,7 @@ int rska_batch_setup(rska_batch **out, int32_t P, const float *A, const int64_t 
 /*
  * rska_batch_solve -- from z_p = 0, iterate every problem until its relative
  * residual ||A_p x - b_p|| / ||b_p|| <= tol (checked every check_every
- * iterations, 0 = ceil(m_p/eta); the exact FP64-accumulated check runs only
+ * iterations, 0 = ceil(m_p/eta); the exact FP64 check runs only
  * when a running estimate from the sampled residuals is within 4 tol) or
  * until max_iters.  tol = 0 runs exactly max_iters iterations on every problem.
  * One CTA per problem, problems taken largest first.  Asynchronous.

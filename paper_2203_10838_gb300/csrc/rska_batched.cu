@@ -16,8 +16,8 @@
 // Stopping: every C_p iterations the CTA first looks at an unbiased estimate
 // of ||A_p x - b_p||^2 built for free from the sampled residuals
 // (sum of r_s^2 / (eta p_s) over the window, p_s = ||a_s||^2 / W_p); only when
-// it is within (4 tol)^2 ||b_p||^2 does it run the exact check (FP32
-// products, FP64 accumulation, one pass over A_p).  Every device-side wait is
+// it is within (4 tol)^2 ||b_p||^2 does it run the exact check (FP64, one
+// pass over A_p).  Every device-side wait is
 // bounded.
 #include <algorithm>
 #include <cmath>
@@ -469,18 +469,20 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
         }
         consumer_sync();
         if (s_gate) {
-          // exact check: one warp per row, FP32 products within a lane, FP64 across
+          // exact check in FP64: one warp per row, products and sums in FP64
           double acc = 0.0;
           for (int i = warp; i < m; i += BCW) {
             const float4* row = reinterpret_cast<const float4*>(Ap + (int64_t)i * lda);
-            float part = 0.f;
+            double d = 0.0;
             for (int64_t c4 = lane; c4 < n4; c4 += 32) {
               float4 v = __ldg(row + c4);
               if (c4 == n4 - 1) v = mask_tail(v, c4, n);
-              const float4 zv = zsh[c4];  // column c4 lives at [c4 / BC][c4 % BC]
-              part += dot4(v, soft_shrink4(zv, lam));
+              const float4 xv = soft_shrink4(zsh[c4], lam);  // column c4 lives at [c4 / BC][c4 % BC]
+              d = fma((double)v.x, (double)xv.x, d);
+              d = fma((double)v.y, (double)xv.y, d);
+              d = fma((double)v.z, (double)xv.z, d);
+              d = fma((double)v.w, (double)xv.w, d);
             }
-            double d = (double)part;
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
             if (lane == 0) {
