@@ -49,7 +49,7 @@ def test_batched_parity_fixed_iterations(env):
     torch, orc, BatchSolver = env
     probs = make_batch(SHAPES, 3000)
     A, a_off, m, n, lda, b, b_off = pack_batch(probs)
-    lam, eta, t, seed, K = 0.5, 32, 16.0, 99, 60
+    lam, eta, t, seed, K = 0.5, 32, 1.0, 99, 60  # t = 1 is admissible for every shape here
     Ad = torch.from_numpy(A).cuda()
     bd = torch.from_numpy(b).cuda()
     with BatchSolver(Ad, bd, a_off, m, n, lda, b_off, lam, eta, t, seed) as bs:
