@@ -102,3 +102,42 @@ def pack_batch(problems):
         b[bo:bo + pr.m] = pr.b
     as64 = lambda v: np.asarray(v, dtype=np.int64)
     return A, as64(a_off), as64(m), as64(n), as64(lda), b, as64(b_off)
+
+
+def batched_problem_set(P: int, seed: int, m_lo: int = 200, m_hi: int = 4000, threads: int = 0):
+    """The batched workload of independent Gaussian systems, generated straight
+    into packed arrays: m_p log-uniform in [m_lo, m_hi], n_p = m_p / 2 rounded
+    to a multiple of 8, s_p = n_p / 20, problem p drawn exactly as
+    gaussian_problem(m_p, n_p, s_p, seed + 1 + p).  Returns (A_flat, a_off, m,
+    n, lda, b_flat, b_off, xhats)."""
+    import concurrent.futures
+    import os
+    ms, ns = batched_sizes(P, seed, m_lo, m_hi)
+    ldas = np.array([round_up(int(v), 4) for v in ns], dtype=np.int64)
+    sizes = np.array([round_up(int(mm) * int(ll), 4) for mm, ll in zip(ms, ldas)], dtype=np.int64)
+    a_off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    b_off = np.concatenate([[0], np.cumsum(ms)[:-1]]).astype(np.int64)
+    A = np.empty(int(sizes.sum()), dtype=np.float32)
+    b = np.empty(int(ms.sum()), dtype=np.float32)
+    xhats = [None] * P
+
+    def make(p):
+        m, n, lda = int(ms[p]), int(ns[p]), int(ldas[p])
+        view = A[a_off[p]:a_off[p] + m * lda].reshape(m, lda)
+        rng = np.random.default_rng(seed + 1 + p)
+        if lda == n:
+            rng.standard_normal(out=view, dtype=np.float32)
+        else:
+            view[:, :n] = rng.standard_normal((m, n), dtype=np.float32)
+            view[:, n:] = 0.0
+        s = max(1, n // 20)
+        xhat = np.zeros(n, dtype=np.float64)
+        support = rng.choice(n, size=s, replace=False)
+        xhat[support] = rng.standard_normal(s)
+        b[b_off[p]:b_off[p] + m] = (view[:, support].astype(np.float64) @ xhat[support])
+        xhats[p] = xhat
+
+    workers = threads or min(32, os.cpu_count() or 4)
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        list(ex.map(make, range(P)))
+    return A, a_off, ms.astype(np.int64), ns.astype(np.int64), ldas, b, b_off, xhats
