@@ -515,6 +515,111 @@ def run_batched(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# unrolled workload: 64 problems, K = 200 iterations, forward + adjoint
+# --------------------------------------------------------------------------
+U_P, U_M, U_N, U_NNZ, U_K, U_ETA, U_CK, U_LAM, U_T, U_SEED = 64, 2048, 1024, 50, 200, 64, 20, 1.0, 32.0, 11
+
+
+def naive_unrolled_torch(torch, A, b, lam, t, tau, inv_nu, eta):
+    """Unrolled RSKA written with torch ops and differentiated by autograd:
+    the comparator for the hand-written adjoint (not the product path)."""
+    z = torch.zeros(A.shape[1], device=A.device)
+    for k in range(tau.shape[0]):
+        x = torch.sign(z) * torch.relu(z.abs() - lam)
+        rows = A.index_select(0, tau[k])
+        r = rows @ x - b.index_select(0, tau[k])
+        z = z - (t / eta) * (rows.t() @ (r * inv_nu.index_select(0, tau[k])))
+    return torch.sign(z) * torch.relu(z.abs() - lam)
+
+
+def run_unrolled(args):
+    import torch
+
+    from paper_2203_10838_gb300 import build
+    from synth import gaussian_problem, pack_batch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    from paper_2203_10838_gb300.rska import Solver, Unrolled
+    probs = [gaussian_problem(U_M, U_N, U_NNZ, seed=700 + i + 1000 * rank, noise=0.01)
+             for i in range(U_P)]
+    A, a_off, m, n, lda, b, b_off = pack_batch(probs)
+    Ad = torch.from_numpy(A).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    un = Unrolled(Ad, a_off, m, n, lda, b_off, U_ETA, U_SEED, U_K, U_CK, stream=stream)
+    bd = torch.from_numpy(b).to(dev).requires_grad_(True)
+    lam = torch.full((U_P,), U_LAM, device=dev, requires_grad=True)
+    t = torch.full((U_P,), U_T, device=dev, requires_grad=True)
+    xhat = torch.zeros(int(un.x_off[-1]), device=dev)
+    for p, pr in enumerate(probs):
+        xhat[int(un.x_off[p]):int(un.x_off[p]) + pr.n] = torch.from_numpy(pr.xhat.astype(np.float32))
+
+    def step():
+        bd.grad = lam.grad = t.grad = None
+        x = un(bd, lam, t)
+        loss = 0.5 * ((x - xhat) ** 2).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # rows read: K forward, K - K/c recompute, K adjoint steps of eta rows each
+    row_reads = U_P * U_ETA * (U_K + (U_K - U_K // U_CK) + U_K)
+    value = row_reads / (ms / 1000.0) * world
+    hbm_peak, peak_kind = load_peaks()
+    achieved = row_reads * (4.0 * U_N) / (ms / 1000.0) / 1e9
+    # naive torch autograd comparator on 4 problems, scaled to 64
+    sub = 4
+    t_naive = 0.0
+    for p in range(sub):
+        pr = probs[p]
+        Ap = torch.from_numpy(pr.A[:, :pr.n].copy()).to(dev)
+        bp = torch.from_numpy(pr.b).to(dev).requires_grad_(True)
+        nu = (Ap.double() ** 2).sum(1)
+        inv_nu = (1.0 / nu).float()
+        with Solver(torch.from_numpy(pr.A).to(dev), torch.from_numpy(pr.b).to(dev), U_LAM, U_ETA,
+                    U_T, U_SEED, n=pr.n) as sp:
+            tau = sp.get_indices(0, U_K).long()   # problem 0's stream; timing only
+        lam1 = torch.tensor(U_LAM, device=dev, requires_grad=True)
+        t1 = torch.tensor(U_T, device=dev, requires_grad=True)
+        xh = torch.from_numpy(pr.xhat.astype(np.float32)).to(dev)
+        torch.cuda.synchronize(dev)
+        c0 = time.perf_counter()
+        xk = naive_unrolled_torch(torch, Ap, bp, lam1, t1, tau, inv_nu, U_ETA)
+        (0.5 * ((xk - xh) ** 2).sum()).backward()
+        torch.cuda.synchronize(dev)
+        t_naive += time.perf_counter() - c0
+    naive_ms = 1000.0 * t_naive * U_P / sub
+    un.close()
+    line = {"metric": "unrolled RSKA forward + adjoint (64 x 2048x1024, K=200, eta=64)",
+            "value": value, "unit": "row-reads/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "rska_unrolled_64x2048x1024", "P": U_P, "m": U_M, "n": U_N,
+                       "K": U_K, "eta": U_ETA, "ckpt": U_CK, "lambda": U_LAM, "t": U_T},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "peak_kind": f"{peak_kind} (copy bandwidth)",
+                         "kernel": "unrolled_forward_kernel + unrolled_backward_kernel"},
+            "naive_torch_autograd_ms_extrapolated": naive_ms,
+            "speedup_vs_naive_autograd": naive_ms / ms, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -526,7 +631,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-tta", action="store_true")
     ap.add_argument("--skip-sweep", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "unrolled"])
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
                     help="kernel: only the timed persistent-kernel steps (for profiling)")
     ap.add_argument("--iters", type=int, default=None,
@@ -544,6 +649,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "unrolled":
+        return run_unrolled(args)
     return run_gpu(args)
 
 

@@ -230,6 +230,51 @@ int rska_batch_get_tables(rska_batch *bt, double *nu_out, uint32_t *thr_out, int
 /* rska_batch_destroy -- free the batch's device memory. */
 int rska_batch_destroy(rska_batch *bt);
 
+/* ------------------------------------------------------------------------ */
+/* Unrolled form: K iterations of eq. (rska) on P problems (each with its own */
+/* lambda_p, t_p and index stream, counter word 3 = p) and the hand-written   */
+/* adjoint of that computation.  The paper has no gradient; this             */
+/* differentiates the iteration as written, with S_lambda's derivative taken */
+/* as 1[|z| > lambda] in z and -sign(z) 1[|z| > lambda] in lambda.            */
+/* ------------------------------------------------------------------------ */
+typedef struct rska_unrolled rska_unrolled;
+
+/*
+ * rska_unrolled_setup -- FP64 row norms and alias tables of every A_p (laid
+ * out as for rska_batch_setup; a_off, m, n, lda, b_off HOST arrays).  K must
+ * be a multiple of ckpt_every (z is checkpointed every ckpt_every
+ * iterations).  eta <= 1024, n[p] <= 4096.  A is borrowed.  Synchronizes.
+ */
+int rska_unrolled_setup(rska_unrolled **out, int32_t P, const float *A, const int64_t *a_off,
+                        const int64_t *m, const int64_t *n, const int64_t *lda,
+                        const int64_t *b_off, int32_t eta, uint64_t seed, int32_t K,
+                        int32_t ckpt_every, void *stream);
+
+/*
+ * rska_unrolled_forward -- x_K of every problem from z_0 = 0 (x_out packed by
+ * rska_unrolled_offsets, device).  b (device, packed by b_off), lambda and t
+ * (device, P floats each) are borrowed until the matching backward.
+ * Asynchronous.
+ */
+int rska_unrolled_forward(rska_unrolled *u, const float *b, const float *lambda, const float *t,
+                          float *x_out);
+
+/*
+ * rska_unrolled_backward -- given dL/dx_K (gx, device, packed like x_out),
+ * write dL/db (gb, device, packed by b_off; zeroed first), dL/dlambda and
+ * dL/dt (device, P floats each) of the last forward.  Recomputes each
+ * checkpoint segment and replays tau_k from the index contract.
+ * Asynchronous.
+ */
+int rska_unrolled_backward(rska_unrolled *u, const float *gx, float *gb, float *glam, float *gt);
+
+/* rska_unrolled_offsets -- HOST: P+1 offsets of each problem's x in the
+ * packed x_out / gx (n rounded up to 4). */
+int rska_unrolled_offsets(rska_unrolled *u, int64_t *x_off);
+
+/* rska_unrolled_destroy -- free the context's device memory. */
+int rska_unrolled_destroy(rska_unrolled *u);
+
 /*
  * rska_solve_noalloc -- one-shot solve that allocates no device memory.  The
  * paper has no counterpart: this exists for callers that cannot call

@@ -44,6 +44,11 @@ def _declare(lib):
         "rska_batch_get_x": ([P, P, P], c_int),
         "rska_batch_get_tables": ([P, P, P, P], c_int),
         "rska_batch_destroy": ([P], c_int),
+        "rska_unrolled_setup": ([PP, i32, P, P, P, P, P, P, i32, u64, i32, i32, P], c_int),
+        "rska_unrolled_forward": ([P, P, P, P, P], c_int),
+        "rska_unrolled_backward": ([P, P, P, P, P], c_int),
+        "rska_unrolled_offsets": ([P, P], c_int),
+        "rska_unrolled_destroy": ([P], c_int),
         "rska_solve_noalloc": ([P, i64, i64, i64, P, f32, i32, f32, u64, i64, P, P, P], c_int),
         "rska_strerror": ([c_int], ctypes.c_char_p),
     }

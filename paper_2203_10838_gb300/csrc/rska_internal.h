@@ -14,6 +14,7 @@ constexpr int kSolveRegRows = 12;       // row steps a thread may hold in regist
 constexpr int kDotBatch = 6;           // row steps whose partial dots are reduced together
 constexpr int kAccStride = 32;          // floats between two rows' dot accumulators (128 B)
 constexpr int64_t kPresampleDraws = 1 << 21;  // draws pre-sampled per launch (at most)
+constexpr int kUnrolledMaxZ = 4;        // unrolled-gradient kernels: float4 columns per thread (n <= 4096)
 constexpr int kBatchMaxZ = 3;           // batched kernel: float4 columns per consumer thread (n <= 2688)
 constexpr int kRowsMaxZ = 6;            // row-split kernel: float4 columns per consumer thread (n <= 11520)
 

@@ -241,3 +241,74 @@ class BatchSolver:
         check(lib().rska_batch_get_tables(self._h, _dptr(nu), _dptr(thr), _dptr(alias)),
               "rska_batch_get_tables")
         return nu, thr, alias
+
+
+class Unrolled:
+    """K unrolled RSKA iterations on P problems with a hand-written adjoint
+    (rska_unrolled_*).  Layout as for BatchSolver; call it with b (packed,
+    float32 CUDA), lam and t (float32 CUDA tensors of P entries) to get the
+    packed x_K as a differentiable function of (b, lam, t)."""
+
+    def __init__(self, A: torch.Tensor, a_off, m, n, lda, b_off, eta: int, seed: int, K: int,
+                 ckpt_every: int, stream=None):
+        import numpy as np
+        self.A = A
+        self.P = len(m)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = A.device
+        self._host = [np.ascontiguousarray(v, dtype=np.int64) for v in (a_off, m, n, lda, b_off)]
+        ptrs = [ctypes.c_void_p(v.ctypes.data) for v in self._host]
+        h = ctypes.c_void_p()
+        check(lib().rska_unrolled_setup(ctypes.byref(h), self.P, _dptr(A), *ptrs, int(eta),
+                                        int(seed), int(K), int(ckpt_every),
+                                        _stream_ptr(self.stream)), "rska_unrolled_setup")
+        self._h = h
+        self.x_off = np.zeros(self.P + 1, dtype=np.int64)
+        check(lib().rska_unrolled_offsets(self._h, ctypes.c_void_p(self.x_off.ctypes.data)),
+              "rska_unrolled_offsets")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rska_unrolled_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward_raw(self, b, lam, t):
+        x = torch.empty(int(self.x_off[-1]), dtype=torch.float32, device=self.device)
+        check(lib().rska_unrolled_forward(self._h, _dptr(b), _dptr(lam), _dptr(t), _dptr(x)),
+              "rska_unrolled_forward")
+        self._keep = (b, lam, t)
+        return x
+
+    def backward_raw(self, gx):
+        b = self._keep[0]
+        gb = torch.empty_like(b)
+        glam = torch.empty(self.P, dtype=torch.float32, device=self.device)
+        gt = torch.empty(self.P, dtype=torch.float32, device=self.device)
+        check(lib().rska_unrolled_backward(self._h, _dptr(gx.contiguous()), _dptr(gb),
+                                           _dptr(glam), _dptr(gt)), "rska_unrolled_backward")
+        return gb, glam, gt
+
+    def __call__(self, b, lam, t):
+        return RSKAUnrolled.apply(b, lam, t, self)
+
+
+class RSKAUnrolled(torch.autograd.Function):
+    """x_K(b, lambda, t) of K unrolled RSKA iterations; the backward is the
+    library's adjoint kernel (no autograd tape over the iterations)."""
+
+    @staticmethod
+    def forward(ctx, b, lam, t, unrolled):
+        ctx.unrolled = unrolled
+        return unrolled.forward_raw(b.detach().contiguous(), lam.detach().contiguous(),
+                                    t.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, gx):
+        gb, glam, gt = ctx.unrolled.backward_raw(gx)
+        return gb, glam, gt, None

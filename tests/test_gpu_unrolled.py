@@ -1,0 +1,89 @@
+"""GPU parity of the unrolled form and its hand-written adjoint (rska_unrolled_*
+behind a torch.autograd.Function) against the FP64 oracle's reverse-mode
+gradient of the same K iterations (itself pinned to central finite
+differences on the CPU).
+
+Bar: x_K within 1e-4 relative; dL/db, dL/dlambda, dL/dt within 1e-3 relative
+(FP32 forward and adjoint against FP64), for L = 1/2 ||x_K - xhat||^2.
+"""
+import numpy as np
+import pytest
+
+from synth import gaussian_problem, pack_batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_10838_gb300 import build
+    build.build()
+    import oracle
+    oracle.build()
+    from paper_2203_10838_gb300.rska import Unrolled
+    return torch, oracle, Unrolled
+
+
+def rel(a, b):
+    return np.linalg.norm(np.atleast_1d(a - b)) / max(np.linalg.norm(np.atleast_1d(b)), 1e-30)
+
+
+def run(env, shapes, nnz, noise, eta, K, ckpt, lams, ts, seed, check):
+    torch, orc, Unrolled = env
+    probs = [gaussian_problem(m, n, nnz, seed=700 + i, noise=noise)
+             for i, (m, n) in enumerate(shapes)]
+    A, a_off, m, n, lda, b, b_off = pack_batch(probs)
+    Ad = torch.from_numpy(A).cuda()
+    un = Unrolled(Ad, a_off, m, n, lda, b_off, eta, seed, K, ckpt)
+    bd = torch.from_numpy(b).cuda().requires_grad_(True)
+    lam = torch.tensor(lams, dtype=torch.float32, device="cuda", requires_grad=True)
+    t = torch.tensor(ts, dtype=torch.float32, device="cuda", requires_grad=True)
+    x = un(bd, lam, t)
+    xo = un.x_off
+    xhat = torch.zeros_like(x)
+    for p, pr in enumerate(probs):
+        xhat[int(xo[p]):int(xo[p]) + pr.n] = torch.from_numpy(pr.xhat.astype(np.float32))
+    loss = 0.5 * ((x - xhat) ** 2).sum()
+    loss.backward()
+    xg = x.detach().cpu().numpy().astype(np.float64)
+    gb = bd.grad.cpu().numpy().astype(np.float64)
+    glam = lam.grad.cpu().numpy().astype(np.float64)
+    gt = t.grad.cpu().numpy().astype(np.float64)
+    un.close()
+    for p in check:
+        pr = probs[p]
+        Ap = pr.A[:, :pr.n]
+        nu = orc.row_norms(Ap)
+        thr, alias = orc.alias_build(nu)
+        tau = orc.sample(thr, alias, seed=seed, eta=eta, k0=0, K=K, problem=p)
+        lam_p = float(np.float32(lams[p]))
+        t_p = float(np.float32(ts[p]))
+        bp = pr.b.astype(np.float64)
+        z = orc.rska_fixed(Ap, bp, lam_p, t_p, eta, tau, nu=nu)
+        xr = orc.soft_shrink(z, lam_p)
+        xhat_p = pr.xhat.astype(np.float32).astype(np.float64)
+        loss_o, gb_o, glam_o, gt_o = orc.unrolled_grad(Ap, bp, lam_p, t_p, eta, tau, xhat_p, nu=nu)
+        x_p = xg[int(xo[p]):int(xo[p]) + pr.n]
+        assert rel(x_p, xr) <= 1e-4, (p, rel(x_p, xr))
+        gb_p = gb[int(b_off[p]):int(b_off[p]) + pr.m]
+        assert rel(gb_p, gb_o) <= 1e-3, (p, "b", rel(gb_p, gb_o))
+        assert rel(glam[p], glam_o) <= 1e-3, (p, "lambda", glam[p], glam_o)
+        assert rel(gt[p], gt_o) <= 1e-3, (p, "t", gt[p], gt_o)
+
+
+def test_unrolled_gradient_small(env):
+    shapes = [(256, 128), (300, 61), (200, 200), (129, 40)]
+    run(env, shapes, nnz=6, noise=0.01, eta=16, K=40, ckpt=10,
+        lams=[0.2, 0.1, 0.3, 0.05], ts=[4.0, 2.0, 3.0, 1.5], seed=5, check=range(4))
+
+
+def test_unrolled_gradient_full_size_configuration(env):
+    """64 problems of 2048 x 1024, 50 nonzeros, 1% noise, K = 200 unrolled
+    iterations, eta = 64, checkpoints every 20, lambda = 1, t = 32; 6 problems
+    checked against the FP64 oracle gradient."""
+    shapes = [(2048, 1024)] * 64
+    run(env, shapes, nnz=50, noise=0.01, eta=64, K=200, ckpt=20, lams=[1.0] * 64,
+        ts=[32.0] * 64, seed=11, check=[0, 1, 17, 31, 48, 63])
