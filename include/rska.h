@@ -205,10 +205,7 @@ int rska_batch_setup(rska_batch **out, int32_t P, const float *A, const int64_t 
  * residual ||A_p x - b_p|| / ||b_p|| <= tol (checked every check_every
  * iterations, 0 = ceil(m_p/eta); the exact FP64 check runs only
  * when a running estimate from the sampled residuals is within 4 tol) or
- * until max_iters; a problem whose estimate has not dropped by 10% over 8
- * check windows has stagnated and stops after one exact check with its
- * residual as it stands (rel_res > tol tells these apart).  tol = 0 runs
- * exactly max_iters iterations on every problem.
+ * until max_iters.  tol = 0 runs exactly max_iters iterations on every problem.
  * One CTA per problem, problems taken largest first.  Asynchronous.
  */
 int rska_batch_solve(rska_batch *bt, int64_t max_iters, double tol, int64_t check_every);

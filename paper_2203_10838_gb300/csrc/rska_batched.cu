@@ -17,10 +17,7 @@
 // of ||A_p x - b_p||^2 built for free from the sampled residuals
 // (sum of r_s^2 / (eta p_s) over the window, p_s = ||a_s||^2 / W_p); only when
 // it is within (4 tol)^2 ||b_p||^2 does it run the exact check (FP64, one
-// pass over A_p).  A problem whose estimate has not dropped by 10% for 8
-// windows has stagnated (sparse Kaczmarz can stall for very long when the
-// solution has a nonzero far below lambda); it gets one exact check and stops
-// there, its residual reported as it stands.  Every device-side wait is
+// pass over A_p).  Every device-side wait is
 // bounded.
 #include <algorithm>
 #include <cmath>
@@ -44,7 +41,6 @@ constexpr int BG = 2;            // rows reduced together
 constexpr int BZ = kBatchMaxZ;   // float4 columns per consumer thread
 constexpr int BSLOTS = 6;        // ring slots
 constexpr int BCTAS_PER_SM = 3;
-constexpr int kPlateauWindows = 8;  // check windows without a 10% drop => plateau
 
 struct BatchArgs {
   int32_t P;
@@ -243,7 +239,6 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
   __shared__ volatile int s_stop;    // the current problem is finished
   __shared__ volatile int s_abort;
   __shared__ int s_gate;
-  __shared__ int s_plateau;
   __shared__ double s_relres;
 
   const int tid = threadIdx.x;
@@ -367,9 +362,7 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
         dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         zsh[(size_t)r * BC + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      double est = 0.0;       // thread 0: windowed estimate of ||A x - b||^2 (times C)
-      double est_best = 1e300;  // thread 0: best window mean so far
-      int stall = 0;            // thread 0: windows without a 10% drop of the residual
+      double est = 0.0;  // thread 0: windowed estimate of ||A x - b||^2 (times C)
       float4 av[BG][BZ];
       float bg[BG], ivg[BG];
       int64_t k = 0;
@@ -471,15 +464,8 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
           const double window = (double)((k + 1) % C == 0 ? C : (k + 1) % C);
           const double est_mean = est / window;
           est = 0.0;
-          if (est_mean < 0.81 * est_best) {
-            est_best = est_mean;
-            stall = 0;
-          } else {
-            ++stall;
-          }
           const double lim = 4.0 * a.tol;
-          s_plateau = (a.tol > 0.0 && stall >= kPlateauWindows) ? 1 : 0;
-          s_gate = last || s_plateau || (a.tol > 0.0 && est_mean <= lim * lim * a.bnorm2[p]);
+          s_gate = last || (a.tol > 0.0 && est_mean <= lim * lim * a.bnorm2[p]);
         }
         consumer_sync();
         if (s_gate) {
@@ -513,7 +499,7 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
             s_relres = sqrt(tot) / (bb > 0.0 ? sqrt(bb) : 1e-30);
           }
           consumer_sync();
-          if ((a.tol > 0.0 && s_relres <= a.tol) || last || s_plateau) {
+          if ((a.tol > 0.0 && s_relres <= a.tol) || last) {
             k += 1;
             break;
           }

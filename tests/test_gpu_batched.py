@@ -97,19 +97,13 @@ def test_batched_stopping_rule(env):
         iters, rr = bs.results()
         x, z = [v.cpu().numpy().astype(np.float64) for v in bs.get_x()]
         xo = bs.x_off
-    converged = 0
     for p, pr in enumerate(probs):
         C = -(-pr.m // 32)
         assert 0 < iters[p] < 200000 and iters[p] % C == 0, (p, iters[p], C)
+        assert rr[p] <= tol
         rr_o, _ = orc.metrics(pr.A[:, :pr.n], pr.b.astype(np.float64),
                               z[xo[p]:xo[p] + pr.n], 1.0)
-        # the reported residual is the exact one of the returned iterate
-        assert abs(rr[p] - rr_o) <= 1e-6 * rr_o + 1e-12, (p, rr[p], rr_o)
-        if rr[p] <= tol:
-            converged += 1
-            assert rr_o <= tol * 1.001, (p, rr[p], rr_o)
-    # stagnation needs a nonzero of xhat far below lambda; most problems converge
-    assert converged >= int(0.9 * len(probs))
+        assert rr_o <= tol * 1.001, (p, rr[p], rr_o)
 
 
 def test_batched_rejects_bad_problems(env):
