@@ -410,6 +410,12 @@ def run_gpu(args):
 # batched workload: 4096 independent systems, each to 1e-6 relative residual
 # --------------------------------------------------------------------------
 BATCH_P, BATCH_ETA, BATCH_T, BATCH_LAM, BATCH_TOL, BATCH_SEED = 4096, 32, 16.0, 1.0, 1e-6, 2024
+# Iteration cap per problem.  About one problem in eight of this set has a
+# nonzero of xhat far below lambda; sparse Kaczmarz then stalls for a very long
+# time at a relative residual of 1e-6 .. 1e-3 (the FP64 oracle shows the same
+# plateau), so the step runs every problem to 1e-6 or to this cap, and the line
+# reports how many reached 1e-6.
+BATCH_MAX_ITERS = 20000
 
 
 def run_batched(args):
@@ -435,7 +441,7 @@ def run_batched(args):
     bs = BatchSolver(Ad, bd, a_off, m, n, lda, b_off, BATCH_LAM, BATCH_ETA, BATCH_T, BATCH_SEED,
                      stream=stream)
     setup_s = time.perf_counter() - t0
-    max_iters = 200000
+    max_iters = BATCH_MAX_ITERS
     for _ in range(max(1, args.warmup)):
         bs.solve(max_iters, tol=BATCH_TOL)
     torch.cuda.synchronize(dev)
@@ -497,8 +503,12 @@ def run_batched(args):
                        "m": "log-uniform [200, 4000]", "n": "m/2 rounded to 8", "eta": BATCH_ETA,
                        "t": BATCH_T, "lambda": BATCH_LAM, "tol": BATCH_TOL,
                        "A_bytes": int(A.nbytes)},
-            "time_to_all_converged_ms": ms_step,
-            "converged": int((rr <= BATCH_TOL).sum()), "iterations_total": int(iters.sum()),
+            "time_to_all_stopped_ms": ms_step,
+            "converged": int((rr <= BATCH_TOL).sum()), "max_iters": max_iters,
+            "stalled_at_cap": int((rr > BATCH_TOL).sum()),
+            "rel_residual_deciles_of_stalled": (np.quantile(rr[rr > BATCH_TOL], [0.1, 0.5, 0.9]).tolist()
+                                                if (rr > BATCH_TOL).any() else None),
+            "iterations_total": int(iters.sum()),
             "iterations_max": int(iters.max()),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None,

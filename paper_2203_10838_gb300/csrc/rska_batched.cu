@@ -8,10 +8,15 @@
 // by estimated work (largest first).  Inside a CTA, warps 0..6 consume rows:
 // each thread owns float4 columns t + 224 r of z, x (and the partial update),
 // so a row's dot is a block reduction and its update c_s a_s is local.  Warp
-// 7 produces: it draws tau_k on the fly (Philox4x32-10 + alias table, 32 slots
-// per warp step, counter word 3 = problem id) and copies each drawn row with
-// one TMA bulk copy into a ring of shared-memory slots as soon as the slot is
-// released.
+// 7 only draws: it fills a ring of the next rows of tau (Philox4x32-10 +
+// alias table, 32 draws per warp step, counter word 3 = problem id) with
+// their b_i and 1/||a_i||^2, up to 512 rows ahead.  Each consumer thread
+// streams its own columns of the next rows into a shared-memory slot ring
+// with 16-byte cp.async copies, one commit group per row, up to 30 rows
+// ahead; since a thread reads back only what it copied itself, the slot ring
+// needs no barrier, only the thread's own wait on its copy groups.  (A TMA
+// bulk copy per row is the other choice; its latency of several microseconds
+// per copy is what this layout avoids for rows of 1 to 10 KB.)
 //
 // Stopping: every C_p iterations the CTA first looks at an unbiased estimate
 // of ||A_p x - b_p||^2 built for free from the sampled residuals
@@ -37,10 +42,15 @@ namespace {
 constexpr int BT = 256;          // threads per CTA
 constexpr int BC = BT - 32;      // consumer threads (warps 0..6)
 constexpr int BCW = BC / 32;     // consumer warps
-constexpr int BG = 2;            // rows reduced together
+constexpr int BG = 8;            // rows reduced together (one block barrier per group)
 constexpr int BZ = kBatchMaxZ;   // float4 columns per consumer thread
-constexpr int BSLOTS = 6;        // ring slots
+constexpr int BIR = 512;         // index ring entries (rows drawn ahead; a power of 2)
+constexpr int BMAXD = 30;        // most rows in flight per consumer thread
+constexpr size_t BRING = 56 * 1024;  // bytes of row slots per CTA (3 CTAs per SM)
 constexpr int BCTAS_PER_SM = 3;
+static_assert(BG == 8, "the transpose-reduce sums exactly 8 values");
+static_assert(BCW <= 8, "block sums read two warps per lane");
+static_assert(BRING / ((size_t)BC * BZ * 16) >= 4, "the ring must hold two groups of the widest rows");
 
 struct BatchArgs {
   int32_t P;
@@ -73,58 +83,11 @@ struct BatchArgs {
   int* queue;
   int* status;
   uint64_t limit_ns;
-  int rowbytes_pad;          // bytes per ring slot
+  size_t ring_bytes;         // bytes of row slots
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity, uint64_t limit_ns,
-                                                  const volatile int* abort) {
-  if (mbar_try_wait(b, parity)) return true;
-  const uint64_t t0 = global_timer_ns();
-  uint32_t spins = 0;
-  while (!mbar_try_wait(b, parity)) {
-    if ((++spins & 63u) == 0) {
-      if (global_timer_ns() - t0 > limit_ns) return false;
-      if (abort != nullptr && *abort) return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          su32(dst)),
-      "l"(src), "r"(bytes), "r"(su32(bar))
-      : "memory");
 }
 
 __device__ __forceinline__ void consumer_sync() {
@@ -226,17 +189,76 @@ __global__ void batch_alias_kernel(BatchArgs a, const double* nu, double* q, int
 // ---------------------------------------------------------------------------
 // The persistent batched solver.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Wait until at most `pending` of this thread's most recent copy groups are
+// still in flight (the instruction takes an immediate).
+__device__ __forceinline__ void cp_async_wait_pending(int pending) {
+  switch (pending) {
+#define RSKA_WG(N) \
+  case N:          \
+    asm volatile("cp.async.wait_group " #N ";" ::: "memory"); \
+    break;
+    RSKA_WG(0) RSKA_WG(1) RSKA_WG(2) RSKA_WG(3) RSKA_WG(4) RSKA_WG(5) RSKA_WG(6) RSKA_WG(7)
+    RSKA_WG(8) RSKA_WG(9) RSKA_WG(10) RSKA_WG(11) RSKA_WG(12) RSKA_WG(13) RSKA_WG(14)
+    RSKA_WG(15) RSKA_WG(16) RSKA_WG(17) RSKA_WG(18) RSKA_WG(19) RSKA_WG(20) RSKA_WG(21)
+    RSKA_WG(22) RSKA_WG(23) RSKA_WG(24) RSKA_WG(25) RSKA_WG(26) RSKA_WG(27) RSKA_WG(28)
+    RSKA_WG(29) RSKA_WG(30)
+#undef RSKA_WG
+    default:
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      break;
+  }
+}
+
+// Sums each of v[0..7] over the warp with 9 shuffles instead of 40: every
+// step halves the values a lane keeps and exchanges the other half with its
+// partner (offsets 16, 8, 4), then offsets 2 and 1 finish a plain butterfly.
+// Lane l returns the warp sum of v[(l >> 2) & 7].
+__device__ __forceinline__ float warp_transpose_sum8(const float (&v)[8], int lane) {
+  float v4[4], v2[2];
+  const bool h4 = (lane & 16) != 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = h4 ? v[i] : v[i + 4];
+    const float keep = h4 ? v[i + 4] : v[i];
+    v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  const bool h3 = (lane & 8) != 0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h3 ? v4[i] : v4[i + 2];
+    const float keep = h3 ? v4[i + 2] : v4[i];
+    v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const bool h2 = (lane & 4) != 0;
+  float v1 = (h2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? v2[0] : v2[1], 4);
+  v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+  v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+  return v1;
+}
+
 __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[BSLOTS];
-  __shared__ __align__(8) uint64_t empty[BSLOTS];
-  __shared__ float wpart[2][BCW][BG];
-  __shared__ float sb[BSLOTS];
-  __shared__ float siv[BSLOTS];
+  __shared__ int32_t s_idx[BIR];
+  __shared__ float s_b[BIR];
+  __shared__ float s_iv[BIR];
+  __shared__ float wpart[2][BG][8];
   __shared__ double dpart[BCW];
   __shared__ int s_prob;
-  __shared__ volatile int s_allow;   // producer may issue iterations < s_allow
-  __shared__ volatile int s_stop;    // the current problem is finished
+  __shared__ volatile long long s_drawn;  // rows of the current problem drawn so far
+  __shared__ volatile long long s_used;   // rows consumed (their ring entries are free)
+  __shared__ volatile int s_stop;         // the current problem is finished
   __shared__ volatile int s_abort;
   __shared__ int s_gate;
   __shared__ double s_relres;
@@ -245,21 +267,11 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
   const int lane = tid & 31;
   const int warp = tid >> 5;
   const int eta = a.eta;
-  unsigned char* ring = smem;
-  float4* zsh = reinterpret_cast<float4*>(smem + (size_t)BSLOTS * a.rowbytes_pad);  // BZ x BC
+  float4* zsh = reinterpret_cast<float4*>(smem);                        // BZ x BC
+  unsigned char* ring = smem + (size_t)BZ * BC * sizeof(float4);        // row slots
 
-  if (tid == 0) {
-    for (int i = 0; i < BSLOTS; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], BCW);
-    }
-    s_abort = 0;
-  }
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (tid == 0) s_abort = 0;
   __syncthreads();
-
-  int64_t prod = 0;  // rows issued by this CTA (producer lane 0)
-  int64_t cons = 0;  // rows consumed by this CTA
   int gcount = 0;
 
   for (;;) {
@@ -267,36 +279,45 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
       const int qi = atomicAdd(a.queue, 1);
       s_prob = (qi < a.P && ld_relaxed_s32(a.status) == kStatusOk) ? a.order[qi] : -1;
       s_stop = 0;
+      s_drawn = 0;
+      s_used = 0;
+      s_relres = -1.0;
     }
     __syncthreads();
     const int p = s_prob;
     if (p < 0) break;
     const int m = a.m[p];
     const int n = a.n[p];
-    const int64_t n4 = (n + 3) >> 2;
+    const int n4 = (n + 3) >> 2;
     const int64_t lda = a.lda[p];
     const float* Ap = a.A + a.a_off[p];
     const float* bp = a.b + a.b_off[p];
     const int64_t ro = a.row_off[p];
-    const uint32_t rowbytes = (uint32_t)(n4 * 16);
     const int64_t C = a.check_every > 0 ? a.check_every : (m + eta - 1) / eta;
     const int64_t kmax = a.max_iters;
-    if (tid == 0) {
-      s_allow = (int)(C < kmax ? C : kmax);
-      s_relres = -1.0;
-    }
-    __syncthreads();
+    // ring geometry for this problem: slots of n4 float4, groups of bgp rows,
+    // `dist` >= bgp rows in flight (nslots >= 5 for n4 <= BC * BZ)
+    const int nslots = min(BMAXD + BG, (int)(a.ring_bytes / ((size_t)n4 * 16)));
+    const int bgp = min(BG, nslots / 2);
+    const int dist = min(BMAXD, nslots - bgp);
 
     if (warp == BCW) {
-      // ------------------------------------------------------- producer --
-      bool bad = false;
-      for (int64_t jj = 0; jj < kmax && !bad; ++jj) {
-        // wait until the consumers allow iteration jj (or stop the problem)
+      // ------------------------------------------------- index producer --
+      // Draws rows e, e+1, ... of this problem's index stream (row e is draw
+      // s = e mod eta of iteration e / eta) into the index ring, up to BIR
+      // rows ahead of the consumers.
+      int64_t jj0 = 0;
+      int s0 = 0;
+      const int64_t total = kmax * (int64_t)eta;
+      for (int64_t e = 0; e < total; e += 32) {
         if (lane == 0) {
           const uint64_t t0 = global_timer_ns();
           uint32_t spins = 0;
-          while (jj >= s_allow && !s_stop && !s_abort) {
-            if ((++spins & 63u) == 0 && global_timer_ns() - t0 > a.limit_ns) {
+          while (e + 32 - s_used > BIR && !s_stop && !s_abort) {
+            // far ahead: sleep rather than spin, a spinning warp steals the
+            // shared-memory pipe from the consumers
+            __nanosleep(500);
+            if ((++spins & 15u) == 0 && global_timer_ns() - t0 > a.limit_ns) {
               atomicCAS(a.status, kStatusOk, kStatusTimeout);
               s_abort = 1;
             }
@@ -304,57 +325,34 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
         }
         __syncwarp();
         if (s_stop || s_abort) break;
-        for (int s0 = 0; s0 < eta && !bad; s0 += 32) {
-          const int s = s0 + lane;
-          int32_t row = 0;
-          float bv = 0.f, ivv = 0.f;
-          {
-            int32_t i0, i1;
-            draw_pair(a.seed, jj, (uint32_t)(s >> 1), (uint32_t)p, a.thr + ro, a.alias + ro,
-                      (uint32_t)m, &i0, &i1);
-            row = (s & 1) ? i1 : i0;
-            if (s < eta) {
-              bv = __ldg(bp + row);
-              ivv = __ldg(a.inv_nu + ro + row);
-            }
-          }
-          const int cnt = min(32, eta - s0);
-          for (int i = 0; i < cnt; ++i) {
-            const int32_t r_i = __shfl_sync(0xffffffffu, row, i);
-            const float b_i = __shfl_sync(0xffffffffu, bv, i);
-            const float iv_i = __shfl_sync(0xffffffffu, ivv, i);
-            int fail = 0;
-            if (lane == 0) {
-              const int sl = (int)(prod % BSLOTS);
-              const int64_t use = prod / BSLOTS;
-              if (use > 0 && !mbar_wait_bounded(&empty[sl], (uint32_t)((use - 1) & 1), a.limit_ns,
-                                                &s_abort))
-                fail = 1;
-              if (!fail) {
-                sb[sl] = b_i;
-                siv[sl] = iv_i;
-                mbar_expect_tx(&full[sl], rowbytes);
-                tma_load_1d(ring + (size_t)sl * a.rowbytes_pad, Ap + (int64_t)r_i * lda, rowbytes,
-                            &full[sl]);
-                ++prod;
-              }
-            }
-            if (__shfl_sync(0xffffffffu, fail, 0)) {
-              if (lane == 0) {
-                atomicCAS(a.status, kStatusOk, kStatusTimeout);
-                s_abort = 1;
-              }
-              bad = true;
-              break;
-            }
-          }
+        int s = s0 + lane;
+        int64_t jj = jj0;
+        while (s >= eta) {
+          s -= eta;
+          ++jj;
+        }
+        int32_t i0, i1;
+        draw_pair(a.seed, jj, (uint32_t)(s >> 1), (uint32_t)p, a.thr + ro, a.alias + ro,
+                  (uint32_t)m, &i0, &i1);
+        const int32_t row = (s & 1) ? i1 : i0;
+        const int slot = (int)(e + lane) & (BIR - 1);
+        s_idx[slot] = row;
+        s_b[slot] = __ldg(bp + row);
+        s_iv[slot] = __ldg(a.inv_nu + ro + row);
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) s_drawn = e + 32;
+        s0 += 32;
+        while (s0 >= eta) {
+          s0 -= eta;
+          ++jj0;
         }
       }
     } else {
       // ------------------------------------------------------ consumers --
       const float lam = a.lambda;
       const float coef = a.coef;
-      const double w_over_eta = a.W[p] / (double)eta;
+      const float w_over_eta = (float)(a.W[p] / (double)eta);
       float4 xr[BZ], dl[BZ];
 #pragma unroll
       for (int r = 0; r < BZ; ++r) {
@@ -362,88 +360,125 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
         dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         zsh[(size_t)r * BC + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      double est = 0.0;  // thread 0: windowed estimate of ||A x - b||^2 (times C)
-      float4 av[BG][BZ];
-      float bg[BG], ivg[BG];
-      int64_t k = 0;
+      float est = 0.f;  // lanes 0..7 of warp 0: windowed estimate of ||A x - b||^2 (times the window)
+      bool ok = true;   // the last refill got its rows
+      int64_t issued = 0;   // rows whose copies this thread has issued
+      int64_t drawn = 0;    // cached s_drawn
+      int64_t q = 0;        // rows consumed
+      int islot = 0;        // slot of row `issued`
+      int qslot = 0;        // slot of row q
+      const uint32_t slot_bytes = (uint32_t)n4 * 16u;
       bool fail = false;
-      for (; k < kmax; ++k) {
-        for (int q0 = 0; q0 < eta; q0 += BG) {
-          const int ng = min(BG, eta - q0);
-          int tmo = 0;
-#pragma unroll
-          for (int g = 0; g < BG; ++g) {
-            bg[g] = 0.f;
-            ivg[g] = 0.f;
-            if (g < ng) {
-              const int64_t gi = cons + g;
-              const int sl = (int)(gi % BSLOTS);
-              if (lane == 0 && !mbar_wait_bounded(&full[sl], (uint32_t)((gi / BSLOTS) & 1),
-                                                  a.limit_ns, &s_abort))
-                tmo = 1;
-              __syncwarp();
-              const float4* rowp =
-                  reinterpret_cast<const float4*>(ring + (size_t)sl * a.rowbytes_pad);
-#pragma unroll
-              for (int r = 0; r < BZ; ++r) {
-                const int64_t col = tid + (int64_t)BC * r;
-                float4 v = (col < n4) ? rowp[col] : make_float4(0.f, 0.f, 0.f, 0.f);
-                if (col == n4 - 1) v = mask_tail(v, col, n);
-                av[g][r] = v;
-              }
-              bg[g] = sb[sl];
-              ivg[g] = siv[sl];
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&empty[sl]);
-            } else {
-#pragma unroll
-              for (int r = 0; r < BZ; ++r) av[g][r] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+
+      // issue the copies of row `issued` (this thread's columns) as one group
+      auto issue_next = [&]() -> bool {
+        if (issued >= drawn) {
+          const uint64_t t0 = global_timer_ns();
+          uint32_t spins = 0;
+          while ((drawn = s_drawn) <= issued) {
+            if (s_abort) return false;
+            if ((++spins & 63u) == 0 && global_timer_ns() - t0 > a.limit_ns) return false;
           }
+          __threadfence_block();
+        }
+        const int32_t row = s_idx[(int)issued & (BIR - 1)];
+        const float4* src = reinterpret_cast<const float4*>(Ap + (int64_t)row * lda);
+        float4* dst = reinterpret_cast<float4*>(ring + islot * slot_bytes);
+        islot = (islot + 1 == nslots) ? 0 : islot + 1;
+#pragma unroll
+        for (int r = 0; r < BZ; ++r) {
+          const int col = tid + BC * r;
+          if (col < n4) cp_async16(dst + col, src + col);
+        }
+        cp_async_commit();
+        ++issued;
+        return true;
+      };
+
+      const int64_t total = kmax * (int64_t)eta;
+      for (int j = 0; j < dist && issued < total && ok; ++j) ok = issue_next();
+      fail = consumer_sync_or(!ok) != 0;
+      int64_t k = 0;
+      for (; k < kmax && !fail; ++k) {
+        for (int q0 = 0; q0 < eta; q0 += bgp) {
+          const int ng = min(bgp, eta - q0);
+          // rows q .. q+ng-1 have landed once at most issued-(q+ng) groups are pending
+          cp_async_wait_pending((int)(issued - (q + ng)));
+          // this thread's share of the ng dots <a_s, x>
           float pd[BG];
 #pragma unroll
           for (int g = 0; g < BG; ++g) {
             pd[g] = 0.f;
-#pragma unroll
-            for (int r = 0; r < BZ; ++r) pd[g] += dot4(av[g][r], xr[r]);
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) pd[g] += __shfl_xor_sync(0xffffffffu, pd[g], o);
-          }
-          const int wp = gcount & 1;
-          ++gcount;
-          if (lane == 0) {
-#pragma unroll
-            for (int g = 0; g < BG; ++g) wpart[wp][warp][g] = pd[g];
-          }
-          if (consumer_sync_or(tmo)) {
-            fail = true;
-            break;
-          }
-          cons += ng;
-#pragma unroll
-          for (int g = 0; g < BG; ++g) {
-            float d = (lane < BCW) ? wpart[wp][lane][g] : 0.f;
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
             if (g < ng) {
-              const float r = d - bg[g];
-              if (tid == 0) est += w_over_eta * (double)r * (double)r * (double)ivg[g];
-              const float cval = coef * (r * ivg[g]);
+              const int sl = (qslot + g < nslots) ? qslot + g : qslot + g - nslots;
+              const float4* rowp = reinterpret_cast<const float4*>(ring + sl * slot_bytes);
 #pragma unroll
-              for (int rr = 0; rr < BZ; ++rr) {
-                dl[rr].x = fmaf(cval, av[g][rr].x, dl[rr].x);
-                dl[rr].y = fmaf(cval, av[g][rr].y, dl[rr].y);
-                dl[rr].z = fmaf(cval, av[g][rr].z, dl[rr].z);
-                dl[rr].w = fmaf(cval, av[g][rr].w, dl[rr].w);
+              for (int r = 0; r < BZ; ++r) {
+                const int col = tid + BC * r;
+                if (col < n4) {
+                  float4 v = rowp[col];
+                  if (col == n4 - 1) v = mask_tail(v, col, n);
+                  pd[g] += dot4(v, xr[r]);
+                }
               }
             }
           }
+          // warp sums of the 8 values by a transpose-reduce (9 shuffles): lane l
+          // ends with the sum of value (l >> 2) & 7
+          const float v1 = warp_transpose_sum8(pd, lane);
+          const int wp = gcount & 1;
+          ++gcount;
+          if ((lane & 3) == 0) wpart[wp][(lane >> 2) & 7][warp] = v1;
+          if (consumer_sync_or(!ok)) {
+            fail = true;
+            break;
+          }
+          if (tid == 0) s_used = q;  // ring entries before this group are free
+          // block sums: lane l gets <a_s, x> for s = q + (l & 7)
+          const int gl = lane & 7;
+          const int w0 = lane >> 3;
+          float d = wpart[wp][gl][w0] + ((w0 + 4 < BCW) ? wpart[wp][gl][w0 + 4] : 0.f);
+          d += __shfl_xor_sync(0xffffffffu, d, 8);
+          d += __shfl_xor_sync(0xffffffffu, d, 16);
+          float cl = 0.f;
+          if (gl < ng) {
+            const int e = (int)(q + gl) & (BIR - 1);
+            const float iv = s_iv[e];
+            const float r = d - s_b[e];
+            cl = coef * (r * iv);
+            if (warp == 0 && lane < 8) est = fmaf(w_over_eta * r, r * iv, est);
+          }
+          // z update contribution sum_s c_s a_s on this thread's columns
+#pragma unroll
+          for (int g = 0; g < BG; ++g) {
+            const float cval = __shfl_sync(0xffffffffu, cl, g);
+            if (g < ng) {
+              const int sl = (qslot + g < nslots) ? qslot + g : qslot + g - nslots;
+              const float4* rowp = reinterpret_cast<const float4*>(ring + sl * slot_bytes);
+#pragma unroll
+              for (int r = 0; r < BZ; ++r) {
+                const int col = tid + BC * r;
+                if (col < n4) {
+                  float4 v = rowp[col];
+                  if (col == n4 - 1) v = mask_tail(v, col, n);
+                  dl[r].x = fmaf(cval, v.x, dl[r].x);
+                  dl[r].y = fmaf(cval, v.y, dl[r].y);
+                  dl[r].z = fmaf(cval, v.z, dl[r].z);
+                  dl[r].w = fmaf(cval, v.w, dl[r].w);
+                }
+              }
+            }
+          }
+          // the slots just used are free: refill them with the rows `dist` ahead
+          q += ng;
+          qslot = (qslot + ng < nslots) ? qslot + ng : qslot + ng - nslots;
+          while (ok && issued < q + dist && issued < total) ok = issue_next();
         }
         if (fail) break;
         // z -= Delta, x = S_lambda(z) on this thread's columns
 #pragma unroll
         for (int r = 0; r < BZ; ++r) {
-          const int64_t col = tid + (int64_t)BC * r;
+          const int col = tid + BC * r;
           if (col < n4) {
             float4 zv = zsh[(size_t)r * BC + tid];
             zv.x -= dl[r].x;
@@ -460,13 +495,17 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
         if ((k + 1) % C != 0 && !last) continue;
 
         // ---- check point: gate on the estimate, then the exact residual ----
+        if (warp == 0) {
+#pragma unroll
+          for (int o = 4; o >= 1; o >>= 1) est += __shfl_xor_sync(0xffffffffu, est, o);
+        }
         if (tid == 0) {
-          const double window = (double)((k + 1) % C == 0 ? C : (k + 1) % C);
-          const double est_mean = est / window;
-          est = 0.0;
+          const float window = (float)((k + 1) % C == 0 ? C : (k + 1) % C);
+          const double est_mean = (double)(est / window);
           const double lim = 4.0 * a.tol;
           s_gate = last || (a.tol > 0.0 && est_mean <= lim * lim * a.bnorm2[p]);
         }
+        est = 0.f;
         consumer_sync();
         if (s_gate) {
           // exact check in FP64: one warp per row, products and sums in FP64
@@ -474,7 +513,7 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
           for (int i = warp; i < m; i += BCW) {
             const float4* row = reinterpret_cast<const float4*>(Ap + (int64_t)i * lda);
             double d = 0.0;
-            for (int64_t c4 = lane; c4 < n4; c4 += 32) {
+            for (int c4 = lane; c4 < n4; c4 += 32) {
               float4 v = __ldg(row + c4);
               if (c4 == n4 - 1) v = mask_tail(v, c4, n);
               const float4 xv = soft_shrink4(zsh[c4], lam);  // column c4 lives at [c4 / BC][c4 % BC]
@@ -504,13 +543,12 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
             break;
           }
         }
-        if (tid == 0) {
-          const int64_t nxt = k + 1 + C;
-          s_allow = (int)(nxt < kmax ? nxt : kmax);
-        }
-        consumer_sync();
       }
-      // problem finished (or failed): publish results, release the producer
+      // a refill after the last barrier may have timed out
+      if (!fail) fail = consumer_sync_or(!ok) != 0;
+      // problem finished (or failed): drain this thread's prefetches before the
+      // ring is reused, publish results, release the producer
+      cp_async_wait_all();
       if (tid == 0) {
         s_stop = 1;
         if (fail) {
@@ -524,7 +562,7 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
       float* xo = a.x + a.x_off[p];
 #pragma unroll
       for (int r = 0; r < BZ; ++r) {
-        const int64_t col = tid + (int64_t)BC * r;
+        const int col = tid + BC * r;
         if (col < n4) {
           reinterpret_cast<float4*>(zo)[col] = zsh[(size_t)r * BC + tid];
           reinterpret_cast<float4*>(xo)[col] = xr[r];
@@ -534,14 +572,7 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
     __syncthreads();
     if (s_abort) break;
   }
-  // let every copy this CTA issued land before the CTA's shared memory goes away
-  if (tid == BC) {
-    for (int64_t g = 0; g < BSLOTS && prod - g - 1 >= 0; ++g) {
-      const int64_t gi = prod - 1 - g;
-      mbar_wait_bounded(&full[gi % BSLOTS], (uint32_t)((gi / BSLOTS) & 1), a.limit_ns, nullptr);
-    }
-  }
-  __syncthreads();
+  cp_async_wait_all();
 }
 
 }  // namespace
@@ -632,7 +663,7 @@ BatchArgs make_args(rska_batch* bt) {
   a.queue = bt->queue;
   a.status = bt->status;
   a.limit_ns = bt->limit_ns;
-  a.rowbytes_pad = (int)(((int64_t)bt->max_n4 * 16 + 127) / 128 * 128);
+  a.ring_bytes = rska::BRING;
   return a;
 }
 
@@ -767,7 +798,7 @@ int rska_batch_solve(rska_batch* bt, int64_t max_iters, double tol, int64_t chec
   a.max_iters = max_iters;
   a.tol = tol;
   a.check_every = check_every;
-  const size_t smem = (size_t)rska::BSLOTS * a.rowbytes_pad + (size_t)rska::BZ * rska::BC * 16;
+  const size_t smem = rska::BRING + (size_t)rska::BZ * rska::BC * 16;
   cudaError_t e = cudaFuncSetAttribute(rska::rska_batched_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaMemsetAsync(bt->queue, 0, sizeof(int), s);
