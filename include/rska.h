@@ -275,6 +275,81 @@ int rska_unrolled_offsets(rska_unrolled *u, int64_t *x_off);
 /* rska_unrolled_destroy -- free the context's device memory. */
 int rska_unrolled_destroy(rska_unrolled *u);
 
+/* ------------------------------------------------------------------------ */
+/* Shared-A multi-right-hand-side form: R systems A x_j = b_j with one A and */
+/* one index stream tau_k (problem = 0 of the index contract, so tau is the  */
+/* single-system sequence of A).  Iteration k is eq. (rska) for every j at   */
+/* once, i.e. with X = S_lambda(Z) the two products of the matrix form       */
+/* A^T M_k (A x - b) (Sec. 3):                                               */
+/*     Res = A_tau X - B_tau;   Z <- Z - (t/eta) A_tau^T D_tau^-2 Res         */
+/* computed on the tensor cores with BF16 operands and FP32 accumulation.    */
+/* ------------------------------------------------------------------------ */
+typedef struct rska_mrhs rska_mrhs;
+
+/*
+ * rska_mrhs_setup -- FP64 row norms (from the BF16 values, same canonical
+ * order as rska_setup), alias table, and the solver state Z = 0.
+ *   A      device, m x n BF16 (raw 16-bit patterns), row-major, leading
+ *          dimension lda: lda >= n, lda a multiple of 8, A 16-byte aligned.
+ *          Borrowed until rska_mrhs_destroy; never written.
+ *   B      device, R x m FP32, row j = b_j, leading dimension ldb >= m.
+ *          Copied (transposed) during setup; not referenced afterwards.
+ *   lambda, eta, t, seed as for rska_setup; eta <= 4096.
+ * Synchronizes `stream`.  Errors: EINVAL (sizes, alignment, parameter
+ * range), EZEROROW, ENONFINITE (A or B), ENOMEM, ECUDA (including a driver
+ * without cuTensorMapEncodeTiled).
+ */
+int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_t lda,
+                    const float *B, int64_t R, int64_t ldb, float lambda, int32_t eta, float t,
+                    uint64_t seed, void *stream);
+
+/*
+ * rska_mrhs_set_option -- what = 0: terms of the inexact operand (X in the
+ * first product, the scaled residual in the second): 2 (default) = BF16 high
+ * + BF16 low part (relative representation error 2^-17), 1 = one BF16 term
+ * (2^-9).  what = 1: CTAs splitting the first product's contraction over n
+ * (0 = automatic, one wave).  what = 2: device wait limit in microseconds.
+ * what = 3: 1 (default) replays 64-iteration chunks as a CUDA graph, 0
+ * launches every kernel directly.  EINVAL for an unknown `what` or value.
+ */
+int rska_mrhs_set_option(rska_mrhs *h, int what, int64_t value);
+
+/*
+ * rska_mrhs_query -- HOST *value: what = 0 iterations done, 1 CTAs of the
+ * first product's split over n, 2 n padded (multiple of 256), 3 eta padded
+ * (multiple of 128), 4 R padded (multiple of 256), 5 terms (option 0).
+ */
+int rska_mrhs_query(rska_mrhs *h, int what, int64_t *value);
+
+/*
+ * rska_mrhs_solve -- K more iterations (K >= 0) for every right-hand side,
+ * continuing the index stream at the current k.  Asynchronous; a device
+ * timeout is reported by the next rska_mrhs_get_x.  Errors: EINVAL, ECUDA,
+ * or the sticky code of an earlier failure.
+ */
+int rska_mrhs_solve(rska_mrhs *h, int64_t K);
+
+/*
+ * rska_mrhs_get_x -- device, R x n FP32 each (row j = x_j = S_lambda(z_j),
+ * resp. z_j); either may be NULL.  Synchronizes; returns ETIMEOUT if a
+ * device wait of an earlier solve gave up.
+ */
+int rska_mrhs_get_x(rska_mrhs *h, float *x_out, float *z_out);
+
+/* rska_mrhs_get_indices -- tau_k for k = k0 .. k0+K-1 into out (device,
+ * K * eta int32, iteration-major).  Synchronizes. */
+int rska_mrhs_get_indices(rska_mrhs *h, int64_t k0, int64_t K, int32_t *out);
+
+/* rska_mrhs_get_tables -- copies of nu (FP64), thr and alias (device, m
+ * each; any may be NULL).  Synchronizes. */
+int rska_mrhs_get_tables(rska_mrhs *h, double *nu_out, uint32_t *thr_out, int32_t *alias_out);
+
+/* rska_mrhs_reset -- Z = 0, k = 0, clears a sticky error.  Asynchronous. */
+int rska_mrhs_reset(rska_mrhs *h);
+
+/* rska_mrhs_destroy -- free the context's device memory.  Synchronizes. */
+int rska_mrhs_destroy(rska_mrhs *h);
+
 /*
  * rska_solve_noalloc -- one-shot solve that allocates no device memory.  The
  * paper has no counterpart: this exists for callers that cannot call

@@ -16,6 +16,9 @@ What each function follows in the paper (Tondji & Lorenz, arXiv 2203.10838):
   (Sec. 5, variants v1/v2).
 * ``sample``        -- tau_k with replacement (eq. rska, Algorithm 1).
 * ``rska_fixed`` / ``rska`` -- eq. (rska) / Algorithm 1 with w_i = t.
+* ``rska_mrhs``     -- eq. (rska) on every right-hand side b_j of a shared A
+  with one index sequence (the matrix form A^T M_k (A x - b) of Sec. 3 per
+  column).
 * ``metrics``       -- relative residual and error of Sec. 5.
 * ``unrolled_grad`` -- reverse-mode gradient of K unrolled iterations of
   eq. (rska) (the paper has no gradient; this differentiates it as written).
@@ -165,6 +168,19 @@ def rska(A, b, lam: float, eta: int, t: float, seed: int, K: int, k0: int = 0, z
     if rc != 0:
         raise ValueError(f"rska failed ({rc})")
     return z
+
+
+def rska_mrhs(A, B, lam: float, t: float, eta: int, tau, nu=None, rows=None) -> np.ndarray:
+    """Shared-A multi-right-hand-side RSKA: for each right-hand side b_j
+    (row j of B), K = len(tau) iterations of eq. (rska) on (A, b_j) with the
+    one index sequence tau shared by all j -- the update A^T M_k (A x - b) of
+    Sec. 3 applied to every column of X at once.  Returns Z with one row z_j
+    per requested j (``rows``, default all)."""
+    A, lda = _as_A(A)
+    nu = row_norms(A) if nu is None else np.ascontiguousarray(nu, dtype=np.float64)
+    B = np.asarray(B)
+    rows = range(B.shape[0]) if rows is None else rows
+    return np.stack([rska_fixed(A, B[j], lam, t, eta, tau, nu=nu) for j in rows])
 
 
 def soft_shrink(z, lam: float) -> np.ndarray:

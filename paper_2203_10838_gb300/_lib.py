@@ -49,6 +49,15 @@ def _declare(lib):
         "rska_unrolled_backward": ([P, P, P, P, P], c_int),
         "rska_unrolled_offsets": ([P, P], c_int),
         "rska_unrolled_destroy": ([P], c_int),
+        "rska_mrhs_setup": ([PP, P, i64, i64, i64, P, i64, i64, f32, i32, f32, u64, P], c_int),
+        "rska_mrhs_set_option": ([P, c_int, i64], c_int),
+        "rska_mrhs_query": ([P, c_int, ctypes.POINTER(i64)], c_int),
+        "rska_mrhs_solve": ([P, i64], c_int),
+        "rska_mrhs_get_x": ([P, P, P], c_int),
+        "rska_mrhs_get_indices": ([P, i64, i64, P], c_int),
+        "rska_mrhs_get_tables": ([P, P, P, P], c_int),
+        "rska_mrhs_reset": ([P], c_int),
+        "rska_mrhs_destroy": ([P], c_int),
         "rska_solve_noalloc": ([P, i64, i64, i64, P, f32, i32, f32, u64, i64, P, P, P], c_int),
         "rska_strerror": ([c_int], ctypes.c_char_p),
     }

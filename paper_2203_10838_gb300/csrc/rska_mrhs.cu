@@ -1,0 +1,922 @@
+// rska_mrhs.cu -- shared-A multi-right-hand-side RSKA on the tensor cores.
+//
+// R systems A x_j = b_j share A (stored in BF16) and one index stream tau_k.
+// With X = [x_1 .. x_R] = S_lambda(Z), one RSKA step (eq. rska, Algorithm 1
+// with w_i = t, applied to every column at once) is two dense contractions:
+//
+//   Res  = A_tau X - B_tau                    (eta x R,  contraction over n)
+//   Z   -= (t/eta) A_tau^T D_tau^-2 Res       (n x R,    contraction over eta)
+//
+// (the matrix form A^T M_k (A x - b) of the update, Sec. 3).  Both run as
+// tcgen05 MMAs with BF16 operands and FP32 accumulation in tensor memory.
+// Every operand is K-major: Z, X and B are held per right-hand side (row j of
+// Z^T is z_j), tau's rows are gathered each iteration into A_tau (eta x n) and
+// its transpose A_tau^T (n x eta), and the scaled residual is written
+// transposed (R x eta).  The operand that is not exact in BF16 (X in the
+// first product, the scaled residual in the second) is split into a BF16 high
+// part and a BF16 low part (v = hi + lo + O(2^-17 |v|)); both parts are
+// multiplied and accumulated into the same tensor-memory tile.
+//
+// Per iteration: gather -> residual GEMM (split over n, partial tiles added
+// with vector atomics into Res) -> scale (Res - B_tau, times t/(eta nu_i),
+// transposed, split, Res cleared) -> update GEMM (epilogue: z -= d,
+// x = S_lambda(z), x split into hi/lo for the next residual GEMM).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "rska_device.cuh"
+#include "rska_internal.h"
+
+namespace rska {
+namespace {
+
+constexpr int TM = 128;             // tile rows (tensor-memory lanes)
+constexpr int TN = 256;             // tile columns (tensor-memory columns, FP32)
+constexpr int TK = 64;              // k-block: one 128-byte swizzle atom of BF16
+constexpr int GEMM_THREADS = 128;   // warp 0: TMA, warp 1: MMA, warps 0-3: epilogue
+constexpr int GEMM_STAGES = 2;
+constexpr uint32_t TILE_A_BYTES = TM * TK * 2;   // 16 KB
+constexpr uint32_t TILE_B_BYTES = TN * TK * 2;   // 32 KB
+
+enum GemmMode { kResidual = 0, kUpdate = 1 };
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mb_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mb_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false after limit_ns (the caller records
+// the timeout and winds down instead of hanging).
+__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns) {
+  if (mb_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  uint32_t spins = 0;
+  while (!mb_try_wait(b, parity)) {
+    if ((++spins & 255u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the
+// 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart
+// (stride byte offset), descriptor version 1, swizzle mode 2 (128 B).  The
+// leading byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor for kind::f16: D FP32, A and B BF16, both K-major,
+// M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 tensor-memory lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
+// v = hi + lo with hi = bf16(v), lo = bf16(v - hi) (round to nearest even).
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  *hi = h;
+  *lo = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+struct GemmArgs {
+  int nsplit;          // 1: the inexact operand as one BF16 term, 2: hi + lo
+  int kb_total;        // k-blocks (of TK) in the contraction
+  int kb_per_cta;      // k-blocks per CTA along grid.z (residual GEMM: split over n)
+  float* out;          // residual GEMM: Res, rows of ld_out floats (added atomically)
+  int64_t ld_out;
+  float* zt;           // update GEMM: Z^T, X_hi^T, X_lo^T, rows of ldz
+  __nv_bfloat16* xhi;
+  __nv_bfloat16* xlo;
+  int64_t ldz;
+  float lambda;
+  int* status;
+  uint64_t limit_ns;
+};
+
+// One 128 x 256 output tile per CTA, D = sum_k A[m][k] B[n][k] over this CTA's
+// k-blocks, accumulated in tensor memory.  kResidual: A = A_tau (mapA0), B =
+// X^T hi (mapB0) and lo (mapB1); D is added into Res.  kUpdate: A = scaled
+// residual^T hi (mapA0) and lo (mapA1), B = A_tau^T (mapB0); Z^T -= D, then
+// x = S_lambda(z) split into X_hi^T / X_lo^T.
+template <int MODE>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    mrhs_gemm_kernel(const __grid_constant__ CUtensorMap mapA0,
+                     const __grid_constant__ CUtensorMap mapA1,
+                     const __grid_constant__ CUtensorMap mapB0,
+                     const __grid_constant__ CUtensorMap mapB1, GemmArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[GEMM_STAGES];
+  __shared__ __align__(8) uint64_t empty[GEMM_STAGES];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_err;
+  __shared__ int s_issued, s_consumed;
+
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const bool splitA = (MODE == kUpdate) && a.nsplit == 2;
+  const bool splitB = (MODE == kResidual) && a.nsplit == 2;
+  const uint32_t a_bytes = TILE_A_BYTES * (splitA ? 2u : 1u);
+  const uint32_t b_bytes = TILE_B_BYTES * (splitB ? 2u : 1u);
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const int m0 = blockIdx.x * TM;
+  const int n0 = blockIdx.y * TN;
+  const int kb0 = blockIdx.z * a.kb_per_cta;
+  const int nkb = max(0, min(a.kb_total, kb0 + a.kb_per_cta) - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < GEMM_STAGES; ++i) {
+      mb_init(&full[i], 1);
+      mb_init(&empty[i], 1);
+    }
+    mb_init(&done, 1);
+    s_err = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(&s_tmem)),
+                 "r"((uint32_t)TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    int it = 0;
+    for (; it < nkb; ++it) {
+      const int st = it % GEMM_STAGES;
+      const int use = it / GEMM_STAGES;
+      if (use > 0 && !mb_wait(&empty[st], (uint32_t)((use - 1) & 1), a.limit_ns)) {
+        s_err = 1;
+        break;
+      }
+      unsigned char* base = smem + (size_t)st * stage_bytes;
+      const int k = (kb0 + it) * TK;
+      mb_expect_tx(&full[st], stage_bytes);
+      tma_load_2d(base, &mapA0, k, m0, &full[st]);
+      if (splitA) tma_load_2d(base + TILE_A_BYTES, &mapA1, k, m0, &full[st]);
+      tma_load_2d(base + a_bytes, &mapB0, k, n0, &full[st]);
+      if (splitB) tma_load_2d(base + a_bytes + TILE_B_BYTES, &mapB1, k, n0, &full[st]);
+    }
+    s_issued = it;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    int it = 0;
+    for (; it < nkb; ++it) {
+      const int st = it % GEMM_STAGES;
+      if (!mb_wait(&full[st], (uint32_t)((it / GEMM_STAGES) & 1), a.limit_ns)) {
+        s_err = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t abase = saddr(smem + (size_t)st * stage_bytes);
+      const uint32_t bbase = abase + a_bytes;
+#pragma unroll
+      for (int kk = 0; kk < TK / 16; ++kk) {
+        // advancing K by 16 BF16 = 32 bytes inside the swizzle atom
+        const uint64_t da = desc_sw128(abase) + (uint64_t)(2 * kk);
+        const uint64_t db = desc_sw128(bbase) + (uint64_t)(2 * kk);
+        mma_bf16(tmem, da, db, kIdesc, (it > 0 || kk > 0) ? 1u : 0u);
+        if (splitA) mma_bf16(tmem, desc_sw128(abase + TILE_A_BYTES) + (uint64_t)(2 * kk), db, kIdesc, 1u);
+        if (splitB) mma_bf16(tmem, da, desc_sw128(bbase + TILE_B_BYTES) + (uint64_t)(2 * kk), kIdesc, 1u);
+      }
+      mma_commit(&empty[st]);
+    }
+    s_consumed = it;
+    mma_commit(&done);
+  }
+
+  // ---- epilogue: all 128 threads, thread t owns tensor-memory lane t ----
+  if (!mb_wait(&done, 0u, a.limit_ns)) s_err = 1;
+  tc_fence_after();
+  __syncthreads();
+  const bool ok = (s_err == 0) && nkb > 0;
+  const int64_t row = m0 + warp * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  if (ok) {
+#pragma unroll 1
+    for (int c = 0; c < TN / 32; ++c) {
+      float v[32];
+      tmem_ld32(trow + (uint32_t)(c * 32), v);
+      const int64_t col0 = n0 + c * 32;
+      if (MODE == kResidual) {
+        float* p = a.out + row * a.ld_out + col0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red_add_v4(p + 4 * q, v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else {
+        float4* zp = reinterpret_cast<float4*>(a.zt + row * a.ldz + col0);
+        uint4 hi4[4], lo4[4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float4 z = zp[q];
+          z.x -= v[4 * q];
+          z.y -= v[4 * q + 1];
+          z.z -= v[4 * q + 2];
+          z.w -= v[4 * q + 3];
+          zp[q] = z;
+          __nv_bfloat16 h[4], l[4];
+          split_bf16(soft_shrink(z.x, a.lambda), &h[0], &l[0]);
+          split_bf16(soft_shrink(z.y, a.lambda), &h[1], &l[1]);
+          split_bf16(soft_shrink(z.z, a.lambda), &h[2], &l[2]);
+          split_bf16(soft_shrink(z.w, a.lambda), &h[3], &l[3]);
+          uint32_t* hw = reinterpret_cast<uint32_t*>(&hi4[q >> 1]);
+          uint32_t* lw = reinterpret_cast<uint32_t*>(&lo4[q >> 1]);
+          const int o = (q & 1) * 2;
+          hw[o] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+          hw[o + 1] = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+          lw[o] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+          lw[o + 1] = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
+        }
+        uint4* hp = reinterpret_cast<uint4*>(a.xhi + row * a.ldz + col0);
+        uint4* lp = reinterpret_cast<uint4*>(a.xlo + row * a.ldz + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          hp[q] = hi4[q];
+          lp[q] = lo4[q];
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && !ok && nkb > 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
+  // let every issued copy land before the shared memory goes away
+  if (threadIdx.x == 0) {
+    for (int it = s_consumed; it < s_issued; ++it)
+      mb_wait(&full[it % GEMM_STAGES], (uint32_t)((it / GEMM_STAGES) & 1), a.limit_ns);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)TN)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Setup and per-iteration helper kernels.
+// ---------------------------------------------------------------------------
+
+// ||a_i||^2 in FP64 from the BF16 values, in the same canonical order as the
+// FP32 setup (lane L sums j = L mod 32 ascending with exact squares, then the
+// 32 partials are folded with xor offsets 16, 8, 4, 2, 1).
+__global__ void mrhs_row_norms_kernel(const __nv_bfloat16* __restrict__ A, int64_t m, int64_t n,
+                                      int64_t lda, double* __restrict__ nu,
+                                      float* __restrict__ inv_nu, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < m; i += nwarps) {
+    const __nv_bfloat16* row = A + i * lda;
+    double p = 0.0;
+    bool finite = true;
+    for (int64_t j = lane; j < n; j += 32) {
+      const float a = __bfloat162float(row[j]);
+      finite = finite && isfinite(a);
+      const double ad = (double)a;
+      p = __fma_rn(ad, ad, p);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+    finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) {
+      if (!finite || !isfinite(p))
+        atomicCAS(status, kStatusOk, kStatusNonFinite);
+      else if (p == 0.0)
+        atomicCAS(status, kStatusOk, kStatusZeroRow);
+      nu[i] = p;
+      inv_nu[i] = (p > 0.0) ? (float)__ddiv_rn(1.0, p) : 0.0f;
+    }
+  }
+}
+
+// Bt[i][j] = B[j][i] (B: R rows of ldb, one right-hand side per row; Bt: m
+// rows of ldbt); columns j >= R of Bt are zero.  Flags non-finite entries.
+__global__ void mrhs_transpose_b_kernel(const float* __restrict__ B, int64_t R, int64_t m,
+                                        int64_t ldb, float* __restrict__ Bt, int64_t ldbt,
+                                        int* status) {
+  __shared__ float tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;  // equation
+  const int64_t j0 = (int64_t)blockIdx.y * 32;  // right-hand side
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  bool bad = false;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t j = j0 + r, i = i0 + tx;
+    float v = 0.f;
+    if (j < R && i < m) {
+      v = B[j * ldb + i];
+      bad = bad || !isfinite(v);
+    }
+    tile[r][tx] = v;
+  }
+  if (bad) atomicCAS(status, kStatusOk, kStatusNonFinite);
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + tx;
+    if (i < m && j < ldbt) Bt[i * ldbt + j] = tile[tx][r];
+  }
+}
+
+// A_tau[s][i] = A[tau_s][i] and A_tau^T[i][s] for one 64 x 64 tile;
+// s >= eta or i >= n give zeros.  256 threads.
+__global__ void mrhs_gather_kernel(const __nv_bfloat16* __restrict__ A, int64_t n, int64_t lda,
+                                   const int32_t* __restrict__ tau, int32_t eta,
+                                   __nv_bfloat16* __restrict__ Atau, int64_t ld_atau,
+                                   __nv_bfloat16* __restrict__ AtauT, int64_t ld_atauT) {
+  __shared__ __nv_bfloat16 tile[64][66];
+  const int64_t s0 = (int64_t)blockIdx.x * 64;
+  const int64_t i0 = (int64_t)blockIdx.y * 64;
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int rep = 0; rep < 2; ++rep) {
+    const int e = t + 256 * rep;
+    const int r = e >> 3, c8 = e & 7;
+    const int64_t s = s0 + r, i = i0 + 8 * c8;
+    union {
+      uint4 u;
+      __nv_bfloat16 h[8];
+    } v;
+    v.u = make_uint4(0u, 0u, 0u, 0u);
+    if (s < eta) {
+      const __nv_bfloat16* src = A + (int64_t)__ldg(tau + s) * lda + i;
+      if (i + 8 <= n) {
+        v.u = __ldg(reinterpret_cast<const uint4*>(src));
+      } else {
+        for (int q = 0; q < 8; ++q)
+          if (i + q < n) v.h[q] = src[q];
+      }
+    }
+    *reinterpret_cast<uint4*>(Atau + s * ld_atau + i) = v.u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tile[r][8 * c8 + q] = v.h[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int rep = 0; rep < 2; ++rep) {
+    const int e = t + 256 * rep;
+    const int r = e >> 3, c8 = e & 7;  // r: column i0 + r, c8: rows s0 + 8 c8 ..
+    union {
+      uint4 u;
+      __nv_bfloat16 h[8];
+    } v;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v.h[q] = tile[8 * c8 + q][r];
+    *reinterpret_cast<uint4*>(AtauT + (i0 + r) * ld_atauT + s0 + 8 * c8) = v.u;
+  }
+}
+
+// Scaled residual, transposed and split: for s < eta, j < R
+//   v = (t/eta) (Res[s][j] - b_j[tau_s]) / ||a_{tau_s}||^2,  Rt{hi,lo}[j][s] = split(v)
+// and zeros elsewhere; Res is cleared for the next residual GEMM.  32 x 8 threads
+// per 32 x 32 tile.
+__global__ void mrhs_scale_kernel(float* __restrict__ Res, int64_t ld_res,
+                                  const float* __restrict__ Bt, int64_t ldbt,
+                                  const float* __restrict__ inv_nu, const int32_t* __restrict__ tau,
+                                  int32_t eta, int64_t R, float coef,
+                                  __nv_bfloat16* __restrict__ Rhi, __nv_bfloat16* __restrict__ Rlo,
+                                  int64_t ld_rt) {
+  __shared__ float tile[32][33];
+  const int64_t s0 = (int64_t)blockIdx.x * 32;
+  const int64_t j0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t s = s0 + r, j = j0 + tx;
+    float* rp = Res + s * ld_res + j;
+    float v = 0.f;
+    if (s < eta && j < R) {
+      const int32_t row = __ldg(tau + s);
+      v = coef * ((*rp - __ldg(Bt + (int64_t)row * ldbt + j)) * __ldg(inv_nu + row));
+    }
+    *rp = 0.f;
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t j = j0 + r, s = s0 + tx;
+    __nv_bfloat16 h, l;
+    split_bf16(tile[tx][r], &h, &l);
+    Rhi[j * ld_rt + s] = h;
+    Rlo[j * ld_rt + s] = l;
+  }
+}
+
+}  // namespace
+}  // namespace rska
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+using rska::GemmArgs;
+
+struct rska_mrhs {
+  const __nv_bfloat16* A = nullptr;
+  int64_t m = 0, n = 0, lda = 0, R = 0;
+  float lambda = 0.f, t = 1.f;
+  int32_t eta = 1;
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int64_t n_p = 0, eta_p = 0, R_p = 0;
+  // owned device memory
+  double* nu = nullptr;
+  float* inv_nu = nullptr;
+  uint32_t* thr = nullptr;
+  int32_t* alias = nullptr;
+  float* Bt = nullptr;               // m x R_p
+  __nv_bfloat16* Atau = nullptr;     // eta_p x n_p
+  __nv_bfloat16* AtauT = nullptr;    // n_p x eta_p
+  __nv_bfloat16* Xhi = nullptr;      // R_p x n_p
+  __nv_bfloat16* Xlo = nullptr;
+  __nv_bfloat16* Rhi = nullptr;      // R_p x eta_p
+  __nv_bfloat16* Rlo = nullptr;
+  float* Zt = nullptr;               // R_p x n_p
+  float* Res = nullptr;              // eta_p x R_p
+  int32_t* idx = nullptr;            // tau for up to idx_cap iterations
+  int64_t idx_cap = 0;
+  int* status = nullptr;
+  CUtensorMap mapAtau, mapX[2], mapR[2], mapAtauT;
+  // options and state
+  int nsplit = 2;
+  int ksplit = 0;                    // residual GEMM CTAs along n (0: automatic)
+  int use_graph = 1;
+  int64_t k_host = 0;
+  int sticky = RSKA_OK;
+  uint64_t limit_ns = 2000000000ull;
+  cudaGraphExec_t graph = nullptr;   // one chunk of idx_cap iterations
+  int graph_nsplit = -1, graph_ksplit = -1;
+};
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// Row-major BF16 matrix (rows x cols, ld elements per row), boxes of 64
+// columns (128 bytes, 128-byte swizzle) by box_rows rows.
+bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+              uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)rska::TK, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t round_up(int64_t v, int64_t k) { return (v + k - 1) / k * k; }
+
+void mrhs_free(rska_mrhs* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  void* ptrs[] = {h->nu, h->inv_nu, h->thr, h->alias, h->Bt,  h->Atau, h->AtauT, h->Xhi,
+                  h->Xlo, h->Rhi,   h->Rlo, h->Zt,    h->Res, h->idx,  h->status};
+  for (void* p : ptrs) cudaFree(p);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+size_t gemm_smem(int mode, int nsplit) {
+  const size_t a = rska::TILE_A_BYTES * ((mode == rska::kUpdate && nsplit == 2) ? 2 : 1);
+  const size_t b = rska::TILE_B_BYTES * ((mode == rska::kResidual && nsplit == 2) ? 2 : 1);
+  return rska::GEMM_STAGES * (a + b) + 1024;
+}
+
+int residual_splits(const rska_mrhs* h, int* kb_per) {
+  const int kb_total = (int)(h->n_p / rska::TK);
+  const int tiles = (int)((h->eta_p / rska::TM) * (h->R_p / rska::TN));
+  int S = h->ksplit > 0 ? h->ksplit : std::max(1, h->num_sms / std::max(1, tiles));
+  S = std::min(S, kb_total);
+  *kb_per = (kb_total + S - 1) / S;
+  return (kb_total + *kb_per - 1) / *kb_per;
+}
+
+// The four launches of iterations [it0, it0 + cnt) of the current tau chunk.
+cudaError_t enqueue_iterations(rska_mrhs* h, int64_t it0, int64_t cnt) {
+  cudaStream_t s = h->stream;
+  int kb_per = 1;
+  const int S = residual_splits(h, &kb_per);
+  GemmArgs g1;
+  std::memset(&g1, 0, sizeof(g1));
+  g1.nsplit = h->nsplit;
+  g1.kb_total = (int)(h->n_p / rska::TK);
+  g1.kb_per_cta = kb_per;
+  g1.out = h->Res;
+  g1.ld_out = h->R_p;
+  g1.status = h->status;
+  g1.limit_ns = h->limit_ns;
+  GemmArgs g2 = g1;
+  g2.kb_total = (int)(h->eta_p / rska::TK);
+  g2.kb_per_cta = g2.kb_total;
+  g2.out = nullptr;
+  g2.zt = h->Zt;
+  g2.xhi = h->Xhi;
+  g2.xlo = h->Xlo;
+  g2.ldz = h->n_p;
+  g2.lambda = h->lambda;
+  const size_t sm1 = gemm_smem(rska::kResidual, h->nsplit);
+  const size_t sm2 = gemm_smem(rska::kUpdate, h->nsplit);
+  const dim3 ggrid((unsigned)(h->eta_p / 64), (unsigned)(h->n_p / 64));
+  const dim3 grid1((unsigned)(h->eta_p / rska::TM), (unsigned)(h->R_p / rska::TN), (unsigned)S);
+  const dim3 sgrid((unsigned)(h->eta_p / 32), (unsigned)(h->R_p / 32));
+  const dim3 grid2((unsigned)(h->R_p / rska::TM), (unsigned)(h->n_p / rska::TN), 1);
+  const float coef = h->t / (float)h->eta;
+  for (int64_t it = it0; it < it0 + cnt; ++it) {
+    const int32_t* tau = h->idx + it * h->eta;
+    rska::mrhs_gather_kernel<<<ggrid, 256, 0, s>>>(h->A, h->n, h->lda, tau, h->eta, h->Atau,
+                                                   h->n_p, h->AtauT, h->eta_p);
+    rska::mrhs_gemm_kernel<rska::kResidual><<<grid1, rska::GEMM_THREADS, sm1, s>>>(
+        h->mapAtau, h->mapAtau, h->mapX[0], h->mapX[1], g1);
+    rska::mrhs_scale_kernel<<<sgrid, dim3(32, 8), 0, s>>>(h->Res, h->R_p, h->Bt, h->R_p,
+                                                          h->inv_nu, tau, h->eta, h->R, coef,
+                                                          h->Rhi, h->Rlo, h->eta_p);
+    rska::mrhs_gemm_kernel<rska::kUpdate><<<grid2, rska::GEMM_THREADS, sm2, s>>>(
+        h->mapR[0], h->mapR[1], h->mapAtauT, h->mapAtauT, g2);
+  }
+  return cudaGetLastError();
+}
+
+__global__ void mrhs_out_kernel(const float* __restrict__ Zt, int64_t ldz, int64_t R, int64_t n,
+                                float lambda, float* __restrict__ x, float* __restrict__ z) {
+  const int64_t total = R * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, i = e - j * n;
+    const float v = Zt[j * ldz + i];
+    if (z) z[e] = v;
+    if (x) x[e] = rska::soft_shrink(v, lambda);
+  }
+}
+
+int fail(rska_mrhs* h, cudaError_t e) {
+  h->sticky = (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+  return h->sticky;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_t lda,
+                    const float* B, int64_t R, int64_t ldb, float lambda, int32_t eta, float t,
+                    uint64_t seed, void* stream) {
+  if (!out) return RSKA_EINVAL;
+  *out = nullptr;
+  if (!A || !B || m < 1 || n < 1 || R < 1 || lda < n || (lda % 8) != 0 || ldb < m || eta < 1 ||
+      eta > rska::kMaxEta || !(lambda >= 0.f) || !std::isfinite(lambda) || !(t > 0.f) ||
+      !std::isfinite(t) || m > 0x7fffffff || (reinterpret_cast<uintptr_t>(A) % 16) != 0)
+    return RSKA_EINVAL;
+  rska_mrhs* h = new (std::nothrow) rska_mrhs;
+  if (!h) return RSKA_ENOMEM;
+  h->A = static_cast<const __nv_bfloat16*>(A);
+  h->m = m;
+  h->n = n;
+  h->lda = lda;
+  h->R = R;
+  h->lambda = lambda;
+  h->t = t;
+  h->eta = eta;
+  h->seed = seed;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->n_p = round_up(n, rska::TN);
+  h->eta_p = round_up(eta, rska::TM);
+  h->R_p = round_up(R, rska::TN);
+  h->idx_cap = 64;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t xs = (size_t)h->R_p * h->n_p;
+  const size_t as = (size_t)h->eta_p * h->n_p;
+  const size_t rs = (size_t)h->R_p * h->eta_p;
+  double* q = nullptr;
+  int32_t* stk = nullptr;
+  if (e == cudaSuccess &&
+      ((e = dalloc(&h->nu, m)) != cudaSuccess || (e = dalloc(&h->inv_nu, m)) != cudaSuccess ||
+       (e = dalloc(&h->thr, m)) != cudaSuccess || (e = dalloc(&h->alias, m)) != cudaSuccess ||
+       (e = dalloc(&h->Bt, (size_t)m * h->R_p)) != cudaSuccess ||
+       (e = dalloc(&h->Atau, as)) != cudaSuccess || (e = dalloc(&h->AtauT, as)) != cudaSuccess ||
+       (e = dalloc(&h->Xhi, xs)) != cudaSuccess || (e = dalloc(&h->Xlo, xs)) != cudaSuccess ||
+       (e = dalloc(&h->Rhi, rs)) != cudaSuccess || (e = dalloc(&h->Rlo, rs)) != cudaSuccess ||
+       (e = dalloc(&h->Zt, xs)) != cudaSuccess || (e = dalloc(&h->Res, rs)) != cudaSuccess ||
+       (e = dalloc(&h->idx, (size_t)h->idx_cap * eta)) != cudaSuccess ||
+       (e = dalloc(&h->status, 1)) != cudaSuccess || (e = dalloc(&q, m)) != cudaSuccess ||
+       (e = dalloc(&stk, m)) != cudaSuccess)) {
+  }
+  cudaStream_t s = h->stream;
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Atau, 0, as * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->AtauT, 0, as * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Xhi, 0, xs * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Xlo, 0, xs * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Rhi, 0, rs * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Rlo, 0, rs * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Zt, 0, xs * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Res, 0, rs * 4, s);
+  if (e == cudaSuccess) {
+    const int64_t blocks = std::min<int64_t>((m + 7) / 8, (int64_t)h->num_sms * 32);
+    rska::mrhs_row_norms_kernel<<<(unsigned)blocks, 256, 0, s>>>(h->A, m, n, lda, h->nu,
+                                                                 h->inv_nu, h->status);
+    rska::mrhs_transpose_b_kernel<<<dim3((unsigned)((m + 31) / 32), (unsigned)(h->R_p / 32)),
+                                    dim3(32, 8), 0, s>>>(B, R, m, ldb, h->Bt, h->R_p, h->status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = rska::launch_alias_build(h->nu, m, h->thr, h->alias, q, stk, h->status, s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(q);
+  cudaFree(stk);
+  int rc = RSKA_OK;
+  if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+  else if (st != 0) rc = st;
+  if (rc == RSKA_OK &&
+      !(make_map(&h->mapAtau, h->Atau, h->eta_p, h->n_p, h->n_p, rska::TM) &&
+        make_map(&h->mapX[0], h->Xhi, h->R_p, h->n_p, h->n_p, rska::TN) &&
+        make_map(&h->mapX[1], h->Xlo, h->R_p, h->n_p, h->n_p, rska::TN) &&
+        make_map(&h->mapR[0], h->Rhi, h->R_p, h->eta_p, h->eta_p, rska::TM) &&
+        make_map(&h->mapR[1], h->Rlo, h->R_p, h->eta_p, h->eta_p, rska::TM) &&
+        make_map(&h->mapAtauT, h->AtauT, h->n_p, h->eta_p, h->eta_p, rska::TN)))
+    rc = RSKA_ECUDA;
+  if (rc == RSKA_OK &&
+      (cudaFuncSetAttribute(rska::mrhs_gemm_kernel<rska::kResidual>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)gemm_smem(rska::kResidual, 2)) != cudaSuccess ||
+       cudaFuncSetAttribute(rska::mrhs_gemm_kernel<rska::kUpdate>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)gemm_smem(rska::kUpdate, 2)) != cudaSuccess))
+    rc = RSKA_ECUDA;
+  if (rc != RSKA_OK) {
+    mrhs_free(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return RSKA_OK;
+}
+
+int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
+  if (!h) return RSKA_EINVAL;
+  switch (what) {
+    case 0:
+      if (value != 1 && value != 2) return RSKA_EINVAL;
+      h->nsplit = (int)value;
+      return RSKA_OK;
+    case 1:
+      if (value < 0 || value > 4096) return RSKA_EINVAL;
+      h->ksplit = (int)value;
+      return RSKA_OK;
+    case 2:
+      if (value < 1) return RSKA_EINVAL;
+      h->limit_ns = (uint64_t)value * 1000ull;
+      return RSKA_OK;
+    case 3:
+      if (value != 0 && value != 1) return RSKA_EINVAL;
+      h->use_graph = (int)value;
+      return RSKA_OK;
+    default:
+      return RSKA_EINVAL;
+  }
+}
+
+int rska_mrhs_query(rska_mrhs* h, int what, int64_t* value) {
+  if (!h || !value) return RSKA_EINVAL;
+  int kb_per = 1;
+  switch (what) {
+    case 0: *value = h->k_host; return RSKA_OK;
+    case 1: *value = residual_splits(h, &kb_per); return RSKA_OK;
+    case 2: *value = h->n_p; return RSKA_OK;
+    case 3: *value = h->eta_p; return RSKA_OK;
+    case 4: *value = h->R_p; return RSKA_OK;
+    case 5: *value = h->nsplit; return RSKA_OK;
+    default: return RSKA_EINVAL;
+  }
+}
+
+int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
+  if (!h || K < 0) return RSKA_EINVAL;
+  if (h->sticky) return h->sticky;
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaSuccess;
+  for (int64_t done = 0; done < K && e == cudaSuccess;) {
+    const int64_t cnt = std::min(h->idx_cap, K - done);
+    e = rska::launch_indices(h->thr, h->alias, h->m, h->seed, 0, h->k_host + done, cnt, h->eta,
+                             h->idx, s);
+    if (e != cudaSuccess) break;
+    if (cnt == h->idx_cap && h->use_graph) {
+      if (!h->graph || h->graph_nsplit != h->nsplit || h->graph_ksplit != h->ksplit) {
+        if (h->graph) {
+          cudaGraphExecDestroy(h->graph);
+          h->graph = nullptr;
+        }
+        cudaStream_t cap = nullptr;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          cudaStream_t user = h->stream;
+          h->stream = cap;
+          const cudaError_t e1 = enqueue_iterations(h, 0, cnt);
+          h->stream = user;
+          e = cudaStreamEndCapture(cap, &g);
+          if (e == cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (cap) cudaStreamDestroy(cap);
+        if (e != cudaSuccess) break;
+        h->graph_nsplit = h->nsplit;
+        h->graph_ksplit = h->ksplit;
+      }
+      e = cudaGraphLaunch(h->graph, s);
+    } else {
+      e = enqueue_iterations(h, 0, cnt);
+    }
+    done += cnt;
+  }
+  if (e != cudaSuccess) return fail(h, e);
+  h->k_host += K;
+  return RSKA_OK;
+}
+
+int rska_mrhs_get_x(rska_mrhs* h, float* x_out, float* z_out) {
+  if (!h) return RSKA_EINVAL;
+  cudaStream_t s = h->stream;
+  const int64_t total = h->R * h->n;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
+  mrhs_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(h->Zt, h->n_p, h->R, h->n, h->lambda, x_out,
+                                                   z_out);
+  int st = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h, e);
+  if (st != 0) h->sticky = st;
+  return st;
+}
+
+int rska_mrhs_get_indices(rska_mrhs* h, int64_t k0, int64_t K, int32_t* out) {
+  if (!h || !out || k0 < 0 || K < 0) return RSKA_EINVAL;
+  cudaError_t e = rska::launch_indices(h->thr, h->alias, h->m, h->seed, 0, k0, K, h->eta, out,
+                                       h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? RSKA_OK : RSKA_ECUDA;
+}
+
+int rska_mrhs_get_tables(rska_mrhs* h, double* nu_out, uint32_t* thr_out, int32_t* alias_out) {
+  if (!h) return RSKA_EINVAL;
+  cudaStream_t s = h->stream;
+  const size_t m = (size_t)h->m;
+  cudaError_t e = cudaSuccess;
+  if (nu_out) e = cudaMemcpyAsync(nu_out, h->nu, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && thr_out)
+    e = cudaMemcpyAsync(thr_out, h->thr, m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && alias_out)
+    e = cudaMemcpyAsync(alias_out, h->alias, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? RSKA_OK : RSKA_ECUDA;
+}
+
+int rska_mrhs_reset(rska_mrhs* h) {
+  if (!h) return RSKA_EINVAL;
+  cudaStream_t s = h->stream;
+  const size_t xs = (size_t)h->R_p * h->n_p;
+  const size_t rs = (size_t)h->R_p * h->eta_p;
+  cudaError_t e = cudaMemsetAsync(h->Zt, 0, xs * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Xhi, 0, xs * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Xlo, 0, xs * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Res, 0, rs * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return fail(h, e);
+  h->k_host = 0;
+  h->sticky = RSKA_OK;
+  return RSKA_OK;
+}
+
+int rska_mrhs_destroy(rska_mrhs* h) {
+  if (!h) return RSKA_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  mrhs_free(h);
+  delete h;
+  return RSKA_OK;
+}
+
+}  // extern "C"

@@ -243,6 +243,91 @@ class BatchSolver:
         return nu, thr, alias
 
 
+MRHS_OPTION = {"terms": 0, "ksplit": 1, "watchdog_us": 2, "graph": 3}
+MRHS_QUERY = {"k": 0, "ksplit": 1, "n_pad": 2, "eta_pad": 3, "R_pad": 4, "terms": 5}
+
+
+class MultiRHS:
+    """Shared-A multi-right-hand-side RSKA on the tensor cores (rska_mrhs_*).
+
+    A: (m, lda) torch.bfloat16 CUDA tensor (lda a multiple of 8; the first n
+    columns are the matrix, n defaults to lda), borrowed by the library and
+    kept alive here.  B: (R, m) float32 CUDA tensor, row j = b_j (copied
+    during setup).  Results come back as (R, n) tensors, row j = x_j.
+    """
+
+    def __init__(self, A: torch.Tensor, B: torch.Tensor, lam: float, eta: int, t: float,
+                 seed: int, n: int | None = None, stream: torch.cuda.Stream | None = None):
+        if A.dtype != torch.bfloat16 or B.dtype != torch.float32:
+            raise ValueError("A must be bfloat16 and B float32")
+        if A.dim() != 2 or B.dim() != 2 or B.shape[1] != A.shape[0]:
+            raise ValueError("A must be (m, lda) and B (R, m)")
+        self.A = A
+        self.m, self.lda = A.shape
+        self.R = B.shape[0]
+        self.n = self.lda if n is None else int(n)
+        self.eta, self.lam, self.t, self.seed = int(eta), float(lam), float(t), int(seed)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = A.device
+        h = ctypes.c_void_p()
+        check(lib().rska_mrhs_setup(ctypes.byref(h), _dptr(A), self.m, self.n, self.lda, _dptr(B),
+                                    self.R, B.shape[1], self.lam, self.eta, self.t, self.seed,
+                                    _stream_ptr(self.stream)), "rska_mrhs_setup")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rska_mrhs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, K: int):
+        check(lib().rska_mrhs_solve(self._h, int(K)), "rska_mrhs_solve")
+
+    def get_x(self):
+        x = torch.empty((self.R, self.n), dtype=torch.float32, device=self.device)
+        z = torch.empty((self.R, self.n), dtype=torch.float32, device=self.device)
+        check(lib().rska_mrhs_get_x(self._h, _dptr(x), _dptr(z)), "rska_mrhs_get_x")
+        return x, z
+
+    def get_indices(self, k0: int, K: int) -> torch.Tensor:
+        out = torch.empty((K, self.eta), dtype=torch.int32, device=self.device)
+        check(lib().rska_mrhs_get_indices(self._h, int(k0), int(K), _dptr(out)),
+              "rska_mrhs_get_indices")
+        return out
+
+    def get_tables(self):
+        nu = torch.empty(self.m, dtype=torch.float64, device=self.device)
+        thr = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        alias = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        check(lib().rska_mrhs_get_tables(self._h, _dptr(nu), _dptr(thr), _dptr(alias)),
+              "rska_mrhs_get_tables")
+        return nu, thr, alias
+
+    def reset(self):
+        check(lib().rska_mrhs_reset(self._h), "rska_mrhs_reset")
+
+    def set_option(self, what: str, value: int):
+        check(lib().rska_mrhs_set_option(self._h, MRHS_OPTION[what], int(value)),
+              "rska_mrhs_set_option")
+
+    def query(self, what: str) -> int:
+        v = ctypes.c_int64()
+        check(lib().rska_mrhs_query(self._h, MRHS_QUERY[what], ctypes.byref(v)), "rska_mrhs_query")
+        return int(v.value)
+
+
 class Unrolled:
     """K unrolled RSKA iterations on P problems with a hand-written adjoint
     (rska_unrolled_*).  Layout as for BatchSolver; call it with b (packed,

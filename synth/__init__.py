@@ -141,3 +141,50 @@ def batched_problem_set(P: int, seed: int, m_lo: int = 200, m_hi: int = 4000, th
     with concurrent.futures.ThreadPoolExecutor(workers) as ex:
         list(ex.map(make, range(P)))
     return A, a_off, ms.astype(np.int64), ns.astype(np.int64), ldas, b, b_off, xhats
+
+
+@dataclass
+class MultiProblem:
+    A16: np.ndarray     # (m, lda) uint16: the BF16 bit patterns of A (padding columns zero)
+    A: np.ndarray       # (m, lda) float32 holding exactly the same BF16 values
+    B: np.ndarray       # (R, m) float32, row j = b_j
+    B64: np.ndarray     # (R, m) float64 right-hand sides before rounding to float32
+    Xhat: np.ndarray    # (R, n) float64 planted sparse solutions
+    n: int
+
+    @property
+    def m(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def R(self) -> int:
+        return self.B.shape[0]
+
+
+def multi_rhs_problem(m: int, n: int, R: int, s: int, seed: int, scale: float | None = None,
+                      lda: int | None = None) -> MultiProblem:
+    """Shared-A multi-right-hand-side workload: A i.i.d. N(0, scale^2) (scale
+    defaults to 1/sqrt(n)) rounded to BF16, R planted solutions xhat_j with s
+    nonzeros N(0, 1) at uniformly drawn positions, and b_j = A_bf16 xhat_j
+    computed in FP64 from the BF16 values (so xhat_j solves the stored
+    system exactly) then rounded to float32.  ``lda`` defaults to n rounded up
+    to a multiple of 8; padding columns are zero."""
+    if lda is None:
+        lda = round_up(n, 8)
+    if scale is None:
+        scale = 1.0 / np.sqrt(n)
+    rng = np.random.default_rng(seed)
+    A = np.zeros((m, lda), dtype=np.float32)
+    A[:, :n] = rng.standard_normal((m, n), dtype=np.float32) * np.float32(scale)
+    A = bf16_round(A)
+    A16 = (A.view(np.uint32) >> 16).astype(np.uint16)
+    s = min(s, n)
+    Xhat = np.zeros((R, n), dtype=np.float64)
+    for j in range(R):
+        support = rng.choice(n, size=s, replace=False)
+        Xhat[j, support] = rng.standard_normal(s)
+    B64 = np.empty((R, m), dtype=np.float64)
+    XT = Xhat.T.copy()
+    for r0 in range(0, m, 2048):
+        B64[:, r0:r0 + 2048] = (A[r0:r0 + 2048, :n].astype(np.float64) @ XT).T
+    return MultiProblem(A16=A16, A=A, B=B64.astype(np.float32), B64=B64, Xhat=Xhat, n=n)

@@ -82,3 +82,38 @@ def test_null_context_is_rejected(L):
     assert L.rska_metrics(None, None, None, None) == 1
     k = ctypes.c_int64()
     assert L.rska_iteration(None, ctypes.byref(k)) == 1
+
+
+@pytest.mark.parametrize("args", [
+    dict(A=None),
+    dict(B=None),
+    dict(m=0),
+    dict(n=0),
+    dict(R=0),
+    dict(lda=8, n=16),       # lda < n
+    dict(lda=20, n=16),      # lda not a multiple of 8
+    dict(ldb=50),            # ldb < m
+    dict(eta=0),
+    dict(eta=4097),
+    dict(lam=-1.0),
+    dict(t=0.0),
+    dict(A=ctypes.c_void_p(0x10008)),   # A not 16-byte aligned
+])
+def test_mrhs_setup_rejects_bad_arguments_before_touching_the_device(L, args):
+    p = dict(A=FAKE, B=FAKE, m=100, n=16, lda=16, R=4, ldb=100, lam=1.0, eta=8, t=1.0)
+    p.update(args)
+    h = ctypes.c_void_p(0xDEAD)
+    rc = L.rska_mrhs_setup(ctypes.byref(h), p["A"], p["m"], p["n"], p["lda"], p["B"], p["R"],
+                           p["ldb"], p["lam"], p["eta"], p["t"], 0, None)
+    assert rc == 1
+    assert h.value is None
+
+
+def test_mrhs_null_context_is_rejected(L):
+    assert L.rska_mrhs_solve(None, 1) == 1
+    assert L.rska_mrhs_get_x(None, None, None) == 1
+    assert L.rska_mrhs_set_option(None, 0, 2) == 1
+    assert L.rska_mrhs_reset(None) == 1
+    assert L.rska_mrhs_destroy(None) == 1
+    v = ctypes.c_int64()
+    assert L.rska_mrhs_query(None, 0, ctypes.byref(v)) == 1
