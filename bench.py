@@ -630,6 +630,148 @@ def run_unrolled(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# shared-A multi-RHS workload on the tensor cores
+# --------------------------------------------------------------------------
+MR_M, MR_N, MR_R, MR_S, MR_ETA, MR_T, MR_LAM, MR_K, MR_PSEED, MR_SEED = (
+    16384, 8192, 512, 400, 256, 128.0, 1.0, 128, 1, 0)
+
+
+def run_mrhs(args):
+    import torch
+
+    from paper_2203_10838_gb300 import build
+    from synth import multi_rhs_problem
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    from paper_2203_10838_gb300.rska import MultiRHS, Solver
+    t0 = time.perf_counter()
+    p = multi_rhs_problem(MR_M, MR_N, MR_R, MR_S, seed=MR_PSEED + rank)
+    gen_s = time.perf_counter() - t0
+    A16_host = torch.from_numpy(p.A16.view(np.int16)).pin_memory()
+    B_host = torch.from_numpy(p.B).pin_memory()
+    A = A16_host.to(dev).view(torch.bfloat16)
+    B = B_host.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    h = MultiRHS(A, B, MR_LAM, MR_ETA, MR_T, MR_SEED, n=MR_N, stream=stream)
+
+    def step():
+        h.reset()
+        h.solve(MR_K)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    updates = MR_ETA * MR_R * MR_K
+    value = updates / (ms / 1000.0) * world
+    flops = 4.0 * MR_ETA * MR_N * MR_R * MR_K   # the two products, multiply-add = 2 flops
+    achieved = flops / (ms / 1000.0) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    # accuracy of the timed solve: relative residual and error per right-hand side (FP64)
+    x, _ = h.get_x()
+    A64 = A.double()
+    res = (x.double() @ A64[:, :MR_N].t()) - torch.from_numpy(p.B64).to(dev)
+    rr = (res.norm(dim=1) / torch.from_numpy(p.B64).to(dev).norm(dim=1)).cpu().numpy()
+    xh = torch.from_numpy(p.Xhat).to(dev)
+    re = ((x.double() - xh).norm(dim=1) / xh.norm(dim=1)).cpu().numpy()
+    del A64, res
+    terms = h.query("terms")
+    ksplit = h.query("ksplit")
+    # end to end through the public API: H2D of A and B, setup, K iterations, D2H of X
+    torch.cuda.synchronize(dev)
+    c0 = time.perf_counter()
+    A_e = A16_host.to(dev, non_blocking=True).view(torch.bfloat16)
+    B_e = B_host.to(dev, non_blocking=True)
+    with MultiRHS(A_e, B_e, MR_LAM, MR_ETA, MR_T, MR_SEED, n=MR_N, stream=stream) as he:
+        he.solve(MR_K)
+        xe = he.get_x()[0].cpu()
+    e2e_s = time.perf_counter() - c0
+    del A_e, B_e
+    # comparator: the single-system GPU solver looped over right-hand sides
+    A32 = torch.from_numpy(p.A).to(dev)
+    sub = 4
+    torch.cuda.synchronize(dev)
+    c0 = time.perf_counter()
+    for j in range(sub):
+        with Solver(A32, B[j].contiguous(), MR_LAM, MR_ETA, MR_T, MR_SEED, n=MR_N,
+                    stream=stream) as sp:
+            sp.solve(MR_K)
+            sp.get_x()
+    torch.cuda.synchronize(dev)
+    loop_s = (time.perf_counter() - c0) * MR_R / sub
+    del A32
+    h.close()
+    cpu = None
+    if not args.skip_cpu:
+        import oracle
+        oracle.build()
+        A_np = np.ascontiguousarray(p.A[:, :MR_N])
+        nu = oracle.row_norms(A_np)
+        thr, alias = oracle.alias_build(nu)
+        Kc = 8
+        tau = oracle.sample(thr, alias, seed=MR_SEED, eta=MR_ETA, k0=0, K=Kc)
+        c0 = time.perf_counter()
+        done = 0
+        for j in range(MR_R):
+            oracle.rska_fixed(A_np, p.B[j].astype(np.float64), MR_LAM, MR_T, MR_ETA, tau, nu=nu)
+            done += 1
+            if time.perf_counter() - c0 > args.ref_seconds:
+                break
+        el = time.perf_counter() - c0
+        cpu = {"value": done * Kc * MR_ETA / el, "unit": "row-updates/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"{Kc} iterations on each of the first {done} right-hand sides "
+                         f"({el:.1f} s, FP64, single thread)"}
+    line = {"metric": "shared-A multi-RHS RSKA row-updates/s (16384x8192 BF16 A, 512 RHS, "
+                      "eta=256)",
+            "value": value, "unit": "row-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands, f32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": "rska_mrhs_16384x8192_R512", "m": MR_M, "n": MR_N, "R": MR_R,
+                       "nnz": MR_S, "eta": MR_ETA, "t": MR_T, "lambda": MR_LAM,
+                       "iters_per_step": MR_K, "terms": terms, "ksplit": ksplit,
+                       "l2": "A is 256 MB (> L2); rows of A are sampled at random"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": "measured cuBLAS bf16, sustained",
+                         "kernel": "whole iteration (gather, residual GEMM, scale, update GEMM)",
+                         "flops_per_iteration": 4.0 * MR_ETA * MR_N * MR_R,
+                         "executed_mma_flops_factor": terms},
+            "accuracy": {"rel_residual_median": float(np.median(rr)),
+                         "rel_residual_max": float(rr.max()),
+                         "rel_error_median": float(np.median(re)),
+                         "after_iterations": MR_K},
+            "e2e": {"value": updates / e2e_s, "unit": "row-updates/s",
+                    "h2d_bytes_per_step": int(p.A16.nbytes + p.B.nbytes),
+                    "d2h_bytes_per_step": int(xe.numel() * 4),
+                    "includes": "H2D of A (BF16) and B, setup (FP64 norms + alias table), "
+                                "K iterations, D2H of X"},
+            "plain_per_rhs_gpu": {"value_s_extrapolated": loop_s,
+                                  "impl": "single-system solver (FP32 copy of the BF16 A) looped "
+                                          "over 4 right-hand sides, scaled to 512",
+                                  "speedup_of_mrhs": loop_s / (ms / 1000.0)},
+            "gpu_launches": 4 * MR_K * args.steps + 2 * args.steps,
+            "prep": {"generate_s": gen_s},
+            "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -641,7 +783,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-tta", action="store_true")
     ap.add_argument("--skip-sweep", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "unrolled"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "unrolled", "mrhs"])
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
                     help="kernel: only the timed persistent-kernel steps (for profiling)")
     ap.add_argument("--iters", type=int, default=None,
@@ -661,6 +803,8 @@ def main():
         return run_batched(args)
     if args.workload == "unrolled":
         return run_unrolled(args)
+    if args.workload == "mrhs":
+        return run_mrhs(args)
     return run_gpu(args)
 
 

@@ -41,7 +41,7 @@ namespace {
 constexpr int TM = 128;             // tile rows (tensor-memory lanes)
 constexpr int TN = 256;             // tile columns (tensor-memory columns, FP32)
 constexpr int TK = 64;              // k-block: one 128-byte swizzle atom of BF16
-constexpr int GEMM_THREADS = 128;   // warp 0: TMA, warp 1: MMA, warps 0-3: epilogue
+constexpr int GEMM_THREADS = 256;   // warp 0: TMA, warp 1: MMA, all 8 warps: epilogue
 constexpr int GEMM_STAGES = 2;
 constexpr uint32_t TILE_A_BYTES = TM * TK * 2;   // 16 KB
 constexpr uint32_t TILE_B_BYTES = TN * TK * 2;   // 32 KB
@@ -284,19 +284,36 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     mma_commit(&done);
   }
 
-  // ---- epilogue: all 128 threads, thread t owns tensor-memory lane t ----
+  // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (row
+  // m0 + 32 (w % 4) + lane) and the column half w / 4 of the tile ----
+  const int quarter = warp & 3;
+  const int c_begin = (warp >> 2) * (TN / 64);
+  const int c_end = c_begin + TN / 64;
+  const int64_t row = m0 + quarter * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+  // the update's z tile does not depend on the products: fetch the first
+  // chunk while the MMAs run
+  float4 zc[8], zn[8];
+  if (MODE == kUpdate && nkb > 0) {
+    const float4* zp = reinterpret_cast<const float4*>(a.zt + row * a.ldz + n0 + c_begin * 32);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) zc[q] = zp[q];
+  }
   if (!mb_wait(&done, 0u, a.limit_ns)) s_err = 1;
   tc_fence_after();
   __syncthreads();
   const bool ok = (s_err == 0) && nkb > 0;
-  const int64_t row = m0 + warp * 32 + lane;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
   if (ok) {
 #pragma unroll 1
-    for (int c = 0; c < TN / 32; ++c) {
+    for (int c = c_begin; c < c_end; ++c) {
+      const int64_t col0 = n0 + c * 32;
+      if (MODE == kUpdate && c + 1 < c_end) {
+        const float4* zp = reinterpret_cast<const float4*>(a.zt + row * a.ldz + col0 + 32);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) zn[q] = zp[q];
+      }
       float v[32];
       tmem_ld32(trow + (uint32_t)(c * 32), v);
-      const int64_t col0 = n0 + c * 32;
       if (MODE == kResidual) {
         float* p = a.out + row * a.ld_out + col0;
 #pragma unroll
@@ -306,7 +323,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         uint4 hi4[4], lo4[4];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          float4 z = zp[q];
+          float4 z = zc[q];
           z.x -= v[4 * q];
           z.y -= v[4 * q + 1];
           z.z -= v[4 * q + 2];
@@ -332,6 +349,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           hp[q] = hi4[q];
           lp[q] = lo4[q];
         }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) zc[q] = zn[q];
       }
     }
   }
@@ -521,8 +540,8 @@ struct rska_mrhs {
   uint32_t* thr = nullptr;
   int32_t* alias = nullptr;
   float* Bt = nullptr;               // m x R_p
-  __nv_bfloat16* Atau = nullptr;     // eta_p x n_p
-  __nv_bfloat16* AtauT = nullptr;    // n_p x eta_p
+  __nv_bfloat16* Atau[2] = {nullptr, nullptr};    // eta_p x n_p, double-buffered
+  __nv_bfloat16* AtauT[2] = {nullptr, nullptr};   // n_p x eta_p
   __nv_bfloat16* Xhi = nullptr;      // R_p x n_p
   __nv_bfloat16* Xlo = nullptr;
   __nv_bfloat16* Rhi = nullptr;      // R_p x eta_p
@@ -532,7 +551,11 @@ struct rska_mrhs {
   int32_t* idx = nullptr;            // tau for up to idx_cap iterations
   int64_t idx_cap = 0;
   int* status = nullptr;
-  CUtensorMap mapAtau, mapX[2], mapR[2], mapAtauT;
+  CUtensorMap mapAtau[2], mapX[2], mapR[2], mapAtauT[2];
+  // the gather of iteration k+1 runs on `side` while iteration k computes
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_gathered[2] = {nullptr, nullptr},
+              ev_used[2] = {nullptr, nullptr};
   // options and state
   int nsplit = 2;
   int ksplit = 0;                    // residual GEMM CTAs along n (0: automatic)
@@ -584,8 +607,14 @@ int64_t round_up(int64_t v, int64_t k) { return (v + k - 1) / k * k; }
 
 void mrhs_free(rska_mrhs* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void* ptrs[] = {h->nu, h->inv_nu, h->thr, h->alias, h->Bt,  h->Atau, h->AtauT, h->Xhi,
-                  h->Xlo, h->Rhi,   h->Rlo, h->Zt,    h->Res, h->idx,  h->status};
+  cudaEvent_t evs[] = {h->ev_fork, h->ev_gathered[0], h->ev_gathered[1], h->ev_used[0],
+                       h->ev_used[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (h->side) cudaStreamDestroy(h->side);
+  void* ptrs[] = {h->nu,       h->inv_nu,   h->thr, h->alias, h->Bt,  h->Atau[0], h->Atau[1],
+                  h->AtauT[0], h->AtauT[1], h->Xhi, h->Xlo,   h->Rhi, h->Rlo,     h->Zt,
+                  h->Res,      h->idx,      h->status};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -609,9 +638,11 @@ int residual_splits(const rska_mrhs* h, int* kb_per) {
   return (kb_total + *kb_per - 1) / *kb_per;
 }
 
-// The four launches of iterations [it0, it0 + cnt) of the current tau chunk.
-cudaError_t enqueue_iterations(rska_mrhs* h, int64_t it0, int64_t cnt) {
-  cudaStream_t s = h->stream;
+// The launches of iterations [0, cnt) of the current tau chunk on stream s.
+// Iteration k uses A_tau buffer k % 2; its gather runs on the side stream as
+// soon as iteration k-2 (the buffer's previous user) is done, overlapping
+// iteration k-1's products.
+cudaError_t enqueue_iterations(rska_mrhs* h, int64_t cnt, cudaStream_t s) {
   int kb_per = 1;
   const int S = residual_splits(h, &kb_per);
   GemmArgs g1;
@@ -639,19 +670,40 @@ cudaError_t enqueue_iterations(rska_mrhs* h, int64_t it0, int64_t cnt) {
   const dim3 sgrid((unsigned)(h->eta_p / 32), (unsigned)(h->R_p / 32));
   const dim3 grid2((unsigned)(h->R_p / rska::TM), (unsigned)(h->n_p / rska::TN), 1);
   const float coef = h->t / (float)h->eta;
-  for (int64_t it = it0; it < it0 + cnt; ++it) {
-    const int32_t* tau = h->idx + it * h->eta;
-    rska::mrhs_gather_kernel<<<ggrid, 256, 0, s>>>(h->A, h->n, h->lda, tau, h->eta, h->Atau,
-                                                   h->n_p, h->AtauT, h->eta_p);
+  cudaStream_t side = h->side;
+  auto gather = [&](int64_t k) -> cudaError_t {
+    const int b = (int)(k & 1);
+    if (k >= 2) {
+      cudaError_t e = cudaStreamWaitEvent(side, h->ev_used[b], 0);
+      if (e != cudaSuccess) return e;
+    }
+    rska::mrhs_gather_kernel<<<ggrid, 256, 0, side>>>(h->A, h->n, h->lda, h->idx + k * h->eta,
+                                                      h->eta, h->Atau[b], h->n_p, h->AtauT[b],
+                                                      h->eta_p);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_gathered[b], side);
+    return e;
+  };
+  cudaError_t e = cudaEventRecord(h->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side, h->ev_fork, 0);
+  if (e == cudaSuccess && cnt > 0) e = gather(0);
+  for (int64_t k = 0; k < cnt && e == cudaSuccess; ++k) {
+    const int b = (int)(k & 1);
+    const int32_t* tau = h->idx + k * h->eta;
+    e = cudaStreamWaitEvent(s, h->ev_gathered[b], 0);
+    if (e != cudaSuccess) break;
     rska::mrhs_gemm_kernel<rska::kResidual><<<grid1, rska::GEMM_THREADS, sm1, s>>>(
-        h->mapAtau, h->mapAtau, h->mapX[0], h->mapX[1], g1);
+        h->mapAtau[b], h->mapAtau[b], h->mapX[0], h->mapX[1], g1);
+    if (k + 1 < cnt && (e = gather(k + 1)) != cudaSuccess) break;
     rska::mrhs_scale_kernel<<<sgrid, dim3(32, 8), 0, s>>>(h->Res, h->R_p, h->Bt, h->R_p,
                                                           h->inv_nu, tau, h->eta, h->R, coef,
                                                           h->Rhi, h->Rlo, h->eta_p);
     rska::mrhs_gemm_kernel<rska::kUpdate><<<grid2, rska::GEMM_THREADS, sm2, s>>>(
-        h->mapR[0], h->mapR[1], h->mapAtauT, h->mapAtauT, g2);
+        h->mapR[0], h->mapR[1], h->mapAtauT[b], h->mapAtauT[b], g2);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_used[b], s);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 __global__ void mrhs_out_kernel(const float* __restrict__ Zt, int64_t ldz, int64_t R, int64_t n,
@@ -712,7 +764,9 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
       ((e = dalloc(&h->nu, m)) != cudaSuccess || (e = dalloc(&h->inv_nu, m)) != cudaSuccess ||
        (e = dalloc(&h->thr, m)) != cudaSuccess || (e = dalloc(&h->alias, m)) != cudaSuccess ||
        (e = dalloc(&h->Bt, (size_t)m * h->R_p)) != cudaSuccess ||
-       (e = dalloc(&h->Atau, as)) != cudaSuccess || (e = dalloc(&h->AtauT, as)) != cudaSuccess ||
+       (e = dalloc(&h->Atau[0], as)) != cudaSuccess || (e = dalloc(&h->Atau[1], as)) != cudaSuccess ||
+       (e = dalloc(&h->AtauT[0], as)) != cudaSuccess ||
+       (e = dalloc(&h->AtauT[1], as)) != cudaSuccess ||
        (e = dalloc(&h->Xhi, xs)) != cudaSuccess || (e = dalloc(&h->Xlo, xs)) != cudaSuccess ||
        (e = dalloc(&h->Rhi, rs)) != cudaSuccess || (e = dalloc(&h->Rlo, rs)) != cudaSuccess ||
        (e = dalloc(&h->Zt, xs)) != cudaSuccess || (e = dalloc(&h->Res, rs)) != cudaSuccess ||
@@ -722,8 +776,16 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
   }
   cudaStream_t s = h->stream;
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->Atau, 0, as * 2, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->AtauT, 0, as * 2, s);
+  for (int b = 0; b < 2; ++b) {
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Atau[b], 0, as * 2, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->AtauT[b], 0, as * 2, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  for (int b = 0; b < 2; ++b) {
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_gathered[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_used[b], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Xhi, 0, xs * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Xlo, 0, xs * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Rhi, 0, rs * 2, s);
@@ -749,12 +811,14 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
   if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
   else if (st != 0) rc = st;
   if (rc == RSKA_OK &&
-      !(make_map(&h->mapAtau, h->Atau, h->eta_p, h->n_p, h->n_p, rska::TM) &&
+      !(make_map(&h->mapAtau[0], h->Atau[0], h->eta_p, h->n_p, h->n_p, rska::TM) &&
+        make_map(&h->mapAtau[1], h->Atau[1], h->eta_p, h->n_p, h->n_p, rska::TM) &&
+        make_map(&h->mapAtauT[0], h->AtauT[0], h->n_p, h->eta_p, h->eta_p, rska::TN) &&
+        make_map(&h->mapAtauT[1], h->AtauT[1], h->n_p, h->eta_p, h->eta_p, rska::TN) &&
         make_map(&h->mapX[0], h->Xhi, h->R_p, h->n_p, h->n_p, rska::TN) &&
         make_map(&h->mapX[1], h->Xlo, h->R_p, h->n_p, h->n_p, rska::TN) &&
         make_map(&h->mapR[0], h->Rhi, h->R_p, h->eta_p, h->eta_p, rska::TM) &&
-        make_map(&h->mapR[1], h->Rlo, h->R_p, h->eta_p, h->eta_p, rska::TM) &&
-        make_map(&h->mapAtauT, h->AtauT, h->n_p, h->eta_p, h->eta_p, rska::TN)))
+        make_map(&h->mapR[1], h->Rlo, h->R_p, h->eta_p, h->eta_p, rska::TM)))
     rc = RSKA_ECUDA;
   if (rc == RSKA_OK &&
       (cudaFuncSetAttribute(rska::mrhs_gemm_kernel<rska::kResidual>,
@@ -832,10 +896,7 @@ int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
         e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          cudaStream_t user = h->stream;
-          h->stream = cap;
-          const cudaError_t e1 = enqueue_iterations(h, 0, cnt);
-          h->stream = user;
+          const cudaError_t e1 = enqueue_iterations(h, cnt, cap);
           e = cudaStreamEndCapture(cap, &g);
           if (e == cudaSuccess) e = e1;
         }
@@ -848,7 +909,7 @@ int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
       }
       e = cudaGraphLaunch(h->graph, s);
     } else {
-      e = enqueue_iterations(h, 0, cnt);
+      e = enqueue_iterations(h, cnt, s);
     }
     done += cnt;
   }
