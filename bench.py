@@ -62,6 +62,21 @@ def dist_env():
     return rank, world, local
 
 
+def init_group(world):
+    """One process per GPU: a process group only for the barrier and the
+    maximum over ranks of the timed region (no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+
+def barrier(world):
+    import torch.distributed as dist
+    if world > 1 and dist.is_initialized():
+        dist.barrier()
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -425,6 +440,7 @@ def run_batched(args):
     from synth import batched_problem_set
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    init_group(world)
     dev = torch.device("cuda", local)
     build.build()
     from paper_2203_10838_gb300.rska import BatchSolver, Solver
@@ -447,6 +463,7 @@ def run_batched(args):
     torch.cuda.synchronize(dev)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
     clocks = ClockSampler(local)
     ev0.record(stream)
     for _ in range(args.steps):
@@ -455,6 +472,8 @@ def run_batched(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms_step = ev0.elapsed_time(ev1) / args.steps
+    from paper_2203_10838_gb300.shard import max_over_ranks
+    ms_step = max_over_ranks(ms_step, dev)
     iters, rr = bs.results()
     bs.close()
     updates = float(iters.sum()) * BATCH_ETA
@@ -521,7 +540,8 @@ def run_batched(args):
                                       "speedup_of_batched": loop_all_s / (ms_step / 1000.0)},
             "prep": {"generate_s": gen_s, "h2d_s": h2d_s, "setup_s": setup_s},
             "cpu_baseline": cpu, "clocks": clk}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -550,6 +570,7 @@ def run_unrolled(args):
     from synth import gaussian_problem, pack_batch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    init_group(world)
     dev = torch.device("cuda", local)
     build.build()
     from paper_2203_10838_gb300.rska import Solver, Unrolled
@@ -576,6 +597,7 @@ def run_unrolled(args):
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
+    barrier(world)
     clocks = ClockSampler(local)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -586,6 +608,8 @@ def run_unrolled(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    from paper_2203_10838_gb300.shard import max_over_ranks
+    ms = max_over_ranks(ms, dev)
     # rows read: K forward, K - K/c recompute, K adjoint steps of eta rows each
     row_reads = U_P * U_ETA * (U_K + (U_K - U_K // U_CK) + U_K)
     value = row_reads / (ms / 1000.0) * world
@@ -626,7 +650,8 @@ def run_unrolled(args):
                          "kernel": "unrolled_forward_kernel + unrolled_backward_kernel"},
             "naive_torch_autograd_ms_extrapolated": naive_ms,
             "speedup_vs_naive_autograd": naive_ms / ms, "clocks": clk}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -644,6 +669,7 @@ def run_mrhs(args):
     from synth import multi_rhs_problem
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    init_group(world)
     dev = torch.device("cuda", local)
     build.build()
     from paper_2203_10838_gb300.rska import MultiRHS, Solver
@@ -664,6 +690,7 @@ def run_mrhs(args):
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
+    barrier(world)
     clocks = ClockSampler(local)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -674,6 +701,8 @@ def run_mrhs(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    from paper_2203_10838_gb300.shard import max_over_ranks
+    ms = max_over_ranks(ms, dev)
     updates = MR_ETA * MR_R * MR_K
     value = updates / (ms / 1000.0) * world
     flops = 4.0 * MR_ETA * MR_N * MR_R * MR_K   # the two products, multiply-add = 2 flops
@@ -768,7 +797,8 @@ def run_mrhs(args):
             "gpu_launches": 4 * MR_K * args.steps + 2 * args.steps,
             "prep": {"generate_s": gen_s},
             "cpu_baseline": cpu, "clocks": clk}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
