@@ -18,9 +18,10 @@
 // multiplied and accumulated into the same tensor-memory tile.
 //
 // Per iteration: gather -> residual GEMM (split over n, partial tiles added
-// with vector atomics into Res) -> scale (Res - B_tau, times t/(eta nu_i),
-// transposed, split, Res cleared) -> update GEMM (epilogue: z -= d,
-// x = S_lambda(z), x split into hi/lo for the next residual GEMM).
+// into Res by TMA bulk reduce-add) -> scale (Res - B_tau, times t/(eta nu_i),
+// transposed, split, Res cleared) -> update GEMM (epilogue through shared
+// memory and TMA: z -= d, x = S_lambda(z), x split into hi/lo for the next
+// residual GEMM).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -93,6 +94,57 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Bulk tensor store / reduce-add of a shared-memory box to global memory
+// (bulk-group completion), and the L2 prefetch of a box.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(saddr(src))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, const void* src, int x,
+                                                  int y) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], "
+      "[%3];" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(saddr(src))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// All committed bulk groups have finished reading their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// All committed bulk groups are complete (writes performed).
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Generic-proxy shared-memory writes become visible to the async proxy (TMA).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Byte offset of 16-byte chunk `chunk` of row `row` in a box of 128-byte rows
+// written or read by TMA with the 128-byte swizzle (box base 1024-aligned).
+__device__ __forceinline__ uint32_t sw128_off(int row, int chunk) {
+  return (uint32_t)(row * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
 // Shared-memory matrix descriptor of a K-major tile written by TMA with the
 // 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart
 // (stride byte offset), descriptor version 1, swizzle mode 2 (128 B).  The
@@ -154,12 +206,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
-               "f"(d)
-               : "memory");
-}
-
 // v = hi + lo with hi = bf16(v), lo = bf16(v - hi) (round to nearest even).
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -192,11 +238,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     mrhs_gemm_kernel(const __grid_constant__ CUtensorMap mapA0,
                      const __grid_constant__ CUtensorMap mapA1,
                      const __grid_constant__ CUtensorMap mapB0,
-                     const __grid_constant__ CUtensorMap mapB1, GemmArgs a) {
+                     const __grid_constant__ CUtensorMap mapB1,
+                     const __grid_constant__ CUtensorMap mapE0,
+                     const __grid_constant__ CUtensorMap mapE1,
+                     const __grid_constant__ CUtensorMap mapE2, GemmArgs a) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[GEMM_STAGES];
   __shared__ __align__(8) uint64_t empty[GEMM_STAGES];
   __shared__ __align__(8) uint64_t done;
+  __shared__ __align__(8) uint64_t zbar;
   __shared__ uint32_t s_tmem;
   __shared__ int s_err;
   __shared__ int s_issued, s_consumed;
@@ -221,6 +271,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       mb_init(&empty[i], 1);
     }
     mb_init(&done, 1);
+    mb_init(&zbar, 1);
     s_err = 0;
     s_issued = 0;
     s_consumed = 0;
@@ -232,6 +283,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                  "r"((uint32_t)TN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (MODE == kUpdate && threadIdx.x == 64 && nkb > 0) {
+    // the update's z tile does not depend on the products: pull it into L2 now
+    for (int b = 0; b < TN / 32; ++b) tma_prefetch_2d(&mapE0, n0 + 32 * b, m0);
   }
   tc_fence_before();
   __syncthreads();
@@ -284,77 +339,107 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     mma_commit(&done);
   }
 
-  // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (row
-  // m0 + 32 (w % 4) + lane) and the column half w / 4 of the tile ----
+  // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile
+  // row 32 (w % 4) + lane) for its column chunks; tiles go through the (now
+  // free) stage buffers in TMA's 128-byte-swizzled layout ----
   const int quarter = warp & 3;
-  const int c_begin = (warp >> 2) * (TN / 64);
-  const int c_end = c_begin + TN / 64;
-  const int64_t row = m0 + quarter * 32 + lane;
+  const int half = warp >> 2;
+  const int r = quarter * 32 + lane;
   const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-  // the update's z tile does not depend on the products: fetch the first
-  // chunk while the MMAs run
-  float4 zc[8], zn[8];
-  if (MODE == kUpdate && nkb > 0) {
-    const float4* zp = reinterpret_cast<const float4*>(a.zt + row * a.ldz + n0 + c_begin * 32);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) zc[q] = zp[q];
-  }
   if (!mb_wait(&done, 0u, a.limit_ns)) s_err = 1;
   tc_fence_after();
   __syncthreads();
   const bool ok = (s_err == 0) && nkb > 0;
-  if (ok) {
+  unsigned char* epi = smem;
+  if (MODE == kResidual) {
+    // 8 boxes of 128 rows x 32 FP32 columns, added into Res by TMA reduce-add
+    if (ok) {
 #pragma unroll 1
-    for (int c = c_begin; c < c_end; ++c) {
-      const int64_t col0 = n0 + c * 32;
-      if (MODE == kUpdate && c + 1 < c_end) {
-        const float4* zp = reinterpret_cast<const float4*>(a.zt + row * a.ldz + col0 + 32);
+      for (int c = half * 4; c < half * 4 + 4; ++c) {
+        float v[32];
+        tmem_ld32(trow + (uint32_t)(c * 32), v);
+        unsigned char* box = epi + (size_t)c * 16384;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) zn[q] = zp[q];
+        for (int j = 0; j < 8; ++j)
+          *reinterpret_cast<float4*>(box + sw128_off(r, j)) =
+              make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
       }
-      float v[32];
-      tmem_ld32(trow + (uint32_t)(c * 32), v);
-      if (MODE == kResidual) {
-        float* p = a.out + row * a.ld_out + col0;
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && ok) {
+      for (int c = 0; c < TN / 32; ++c) tma_reduce_add_2d(&mapE0, epi + (size_t)c * 16384, n0 + 32 * c, m0);
+      bulk_commit();
+      bulk_wait_all();
+    }
+  } else {
+    // two rounds of 128 columns: z boxes (4 x 16 KB FP32) loaded by TMA, updated
+    // in place, x = S_lambda(z) split into BF16 hi/lo boxes (2 x 16 KB each),
+    // all stored by TMA
+    unsigned char* zreg = epi;
+    unsigned char* hreg = epi + 65536;
+    unsigned char* lreg = epi + 98304;
+#pragma unroll 1
+    for (int round = 0; round < 2 && ok; ++round) {
+      const int cbase = n0 + 128 * round;
+      if (threadIdx.x == 0) {
+        mb_expect_tx(&zbar, 65536u);
+        for (int b = 0; b < 4; ++b) tma_load_2d(zreg + (size_t)b * 16384, &mapE0, cbase + 32 * b, m0, &zbar);
+      }
+      const bool zok = mb_wait(&zbar, (uint32_t)round, a.limit_ns);
+#pragma unroll 1
+      for (int cc = 0; cc < 2; ++cc) {
+        const int c = 2 * half + cc;  // 32-column chunk of this round
+        float v[32];
+        tmem_ld32(trow + (uint32_t)(128 * round + 32 * c), v);
+        unsigned char* zb = zreg + (size_t)c * 16384;
+        uint32_t hw[16], lw[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) red_add_v4(p + 4 * q, v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      } else {
-        float4* zp = reinterpret_cast<float4*>(a.zt + row * a.ldz + col0);
-        uint4 hi4[4], lo4[4];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          float4 z = zc[q];
-          z.x -= v[4 * q];
-          z.y -= v[4 * q + 1];
-          z.z -= v[4 * q + 2];
-          z.w -= v[4 * q + 3];
-          zp[q] = z;
+        for (int j = 0; j < 8; ++j) {
+          float4* zp = reinterpret_cast<float4*>(zb + sw128_off(r, j));
+          float4 z = *zp;
+          z.x -= v[4 * j];
+          z.y -= v[4 * j + 1];
+          z.z -= v[4 * j + 2];
+          z.w -= v[4 * j + 3];
+          *zp = z;
           __nv_bfloat16 h[4], l[4];
           split_bf16(soft_shrink(z.x, a.lambda), &h[0], &l[0]);
           split_bf16(soft_shrink(z.y, a.lambda), &h[1], &l[1]);
           split_bf16(soft_shrink(z.z, a.lambda), &h[2], &l[2]);
           split_bf16(soft_shrink(z.w, a.lambda), &h[3], &l[3]);
-          uint32_t* hw = reinterpret_cast<uint32_t*>(&hi4[q >> 1]);
-          uint32_t* lw = reinterpret_cast<uint32_t*>(&lo4[q >> 1]);
-          const int o = (q & 1) * 2;
-          hw[o] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
-          hw[o + 1] = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
-          lw[o] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
-          lw[o + 1] = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
+          hw[2 * j] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+          hw[2 * j + 1] = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+          lw[2 * j] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+          lw[2 * j + 1] = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
         }
-        uint4* hp = reinterpret_cast<uint4*>(a.xhi + row * a.ldz + col0);
-        uint4* lp = reinterpret_cast<uint4*>(a.xlo + row * a.ldz + col0);
+        // 32 BF16 = 4 chunks of 16 bytes at chunks 4 (c % 2) .. + 3 of box c / 2
+        unsigned char* hb = hreg + (size_t)(c >> 1) * 16384;
+        unsigned char* lb = lreg + (size_t)(c >> 1) * 16384;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          hp[q] = hi4[q];
-          lp[q] = lo4[q];
+          const uint32_t off = sw128_off(r, 4 * (c & 1) + q);
+          *reinterpret_cast<uint4*>(hb + off) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+          *reinterpret_cast<uint4*>(lb + off) = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) zc[q] = zn[q];
       }
+      if (!zok) s_err = 1;
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0 && s_err == 0) {
+        for (int b = 0; b < 4; ++b) tma_store_2d(&mapE0, zreg + (size_t)b * 16384, cbase + 32 * b, m0);
+        for (int b = 0; b < 2; ++b) {
+          tma_store_2d(&mapE1, hreg + (size_t)b * 16384, cbase + 64 * b, m0);
+          tma_store_2d(&mapE2, lreg + (size_t)b * 16384, cbase + 64 * b, m0);
+        }
+        bulk_commit();
+        bulk_wait_read();
+      }
+      __syncthreads();
     }
+    if (threadIdx.x == 0) bulk_wait_all();
   }
-  if (threadIdx.x == 0 && !ok && nkb > 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
+  if (threadIdx.x == 0 && (!ok || s_err) && nkb > 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
   // let every issued copy land before the shared memory goes away
   if (threadIdx.x == 0) {
     for (int it = s_consumed; it < s_issued; ++it)
@@ -552,6 +637,7 @@ struct rska_mrhs {
   int64_t idx_cap = 0;
   int* status = nullptr;
   CUtensorMap mapAtau[2], mapX[2], mapR[2], mapAtauT[2];
+  CUtensorMap mapRes, mapZ, mapXs[2];  // epilogue boxes: Res and Z (FP32), X hi/lo (BF16)
   // the gather of iteration k+1 runs on `side` while iteration k computes
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_gathered[2] = {nullptr, nullptr},
@@ -588,19 +674,21 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// Row-major BF16 matrix (rows x cols, ld elements per row), boxes of 64
-// columns (128 bytes, 128-byte swizzle) by box_rows rows.
+// Row-major matrix (rows x cols, ld elements per row) in boxes of 128-byte
+// rows (64 BF16 or 32 FP32 columns, 128-byte swizzle) by box_rows rows.
 bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
-              uint32_t box_rows) {
+              uint32_t box_rows, bool fp32 = false) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
+  const uint64_t esize = fp32 ? 4 : 2;
   const cuuint64_t dims[2] = {cols, rows};
-  const cuuint64_t strides[1] = {ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)rska::TK, box_rows};
+  const cuuint64_t strides[1] = {ld * esize};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esize), box_rows};
   const cuuint32_t es[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return fn(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int64_t round_up(int64_t v, int64_t k) { return (v + k - 1) / k * k; }
@@ -626,7 +714,8 @@ cudaError_t dalloc(T** p, size_t count) {
 size_t gemm_smem(int mode, int nsplit) {
   const size_t a = rska::TILE_A_BYTES * ((mode == rska::kUpdate && nsplit == 2) ? 2 : 1);
   const size_t b = rska::TILE_B_BYTES * ((mode == rska::kResidual && nsplit == 2) ? 2 : 1);
-  return rska::GEMM_STAGES * (a + b) + 1024;
+  // the epilogue reuses the stage buffers for 128 KB of output boxes
+  return std::max<size_t>(rska::GEMM_STAGES * (a + b), 131072) + 1024;
 }
 
 int residual_splits(const rska_mrhs* h, int* kb_per) {
@@ -693,13 +782,15 @@ cudaError_t enqueue_iterations(rska_mrhs* h, int64_t cnt, cudaStream_t s) {
     e = cudaStreamWaitEvent(s, h->ev_gathered[b], 0);
     if (e != cudaSuccess) break;
     rska::mrhs_gemm_kernel<rska::kResidual><<<grid1, rska::GEMM_THREADS, sm1, s>>>(
-        h->mapAtau[b], h->mapAtau[b], h->mapX[0], h->mapX[1], g1);
+        h->mapAtau[b], h->mapAtau[b], h->mapX[0], h->mapX[1], h->mapRes, h->mapRes, h->mapRes,
+        g1);
     if (k + 1 < cnt && (e = gather(k + 1)) != cudaSuccess) break;
     rska::mrhs_scale_kernel<<<sgrid, dim3(32, 8), 0, s>>>(h->Res, h->R_p, h->Bt, h->R_p,
                                                           h->inv_nu, tau, h->eta, h->R, coef,
                                                           h->Rhi, h->Rlo, h->eta_p);
     rska::mrhs_gemm_kernel<rska::kUpdate><<<grid2, rska::GEMM_THREADS, sm2, s>>>(
-        h->mapR[0], h->mapR[1], h->mapAtauT[b], h->mapAtauT[b], g2);
+        h->mapR[0], h->mapR[1], h->mapAtauT[b], h->mapAtauT[b], h->mapZ, h->mapXs[0],
+        h->mapXs[1], g2);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_used[b], s);
   }
@@ -818,7 +909,11 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
         make_map(&h->mapX[0], h->Xhi, h->R_p, h->n_p, h->n_p, rska::TN) &&
         make_map(&h->mapX[1], h->Xlo, h->R_p, h->n_p, h->n_p, rska::TN) &&
         make_map(&h->mapR[0], h->Rhi, h->R_p, h->eta_p, h->eta_p, rska::TM) &&
-        make_map(&h->mapR[1], h->Rlo, h->R_p, h->eta_p, h->eta_p, rska::TM)))
+        make_map(&h->mapR[1], h->Rlo, h->R_p, h->eta_p, h->eta_p, rska::TM) &&
+        make_map(&h->mapRes, h->Res, h->eta_p, h->R_p, h->R_p, rska::TM, true) &&
+        make_map(&h->mapZ, h->Zt, h->R_p, h->n_p, h->n_p, rska::TM, true) &&
+        make_map(&h->mapXs[0], h->Xhi, h->R_p, h->n_p, h->n_p, rska::TM) &&
+        make_map(&h->mapXs[1], h->Xlo, h->R_p, h->n_p, h->n_p, rska::TM)))
     rc = RSKA_ECUDA;
   if (rc == RSKA_OK &&
       (cudaFuncSetAttribute(rska::mrhs_gemm_kernel<rska::kResidual>,
