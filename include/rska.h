@@ -310,7 +310,10 @@ int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_
  * (2^-9).  what = 1: CTAs splitting the first product's contraction over n
  * (0 = automatic, one wave).  what = 2: device wait limit in microseconds.
  * what = 3: 1 (default) replays 64-iteration chunks as a CUDA graph, 0
- * launches every kernel directly.  EINVAL for an unknown `what` or value.
+ * launches every kernel directly.  what = 4: 1 (default) launches each
+ * kernel of an iteration as a programmatic dependent of the previous one
+ * (its prologue overlaps the previous kernel's tail), 0 orders them fully.
+ * EINVAL for an unknown `what` or value.
  */
 int rska_mrhs_set_option(rska_mrhs *h, int what, int64_t value);
 

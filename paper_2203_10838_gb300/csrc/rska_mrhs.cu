@@ -46,6 +46,7 @@ constexpr int GEMM_THREADS = 256;   // warp 0: TMA, warp 1: MMA, all 8 warps: ep
 constexpr int GEMM_STAGES = 2;
 constexpr uint32_t TILE_A_BYTES = TM * TK * 2;   // 16 KB
 constexpr uint32_t TILE_B_BYTES = TN * TK * 2;   // 32 KB
+constexpr size_t ZREG0 = 131072;                  // update: first half of the z tile (64 KB)
 
 enum GemmMode { kResidual = 0, kUpdate = 1 };
 
@@ -129,9 +130,15 @@ __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-// All committed bulk groups are complete (writes performed).
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+// Programmatic dependent launch: wait until the preceding kernel in the
+// stream has completed and its writes are visible (returns at once for an
+// ordinary launch); let the next kernel start its prologue.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Generic-proxy shared-memory writes become visible to the async proxy (TMA).
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   __shared__ __align__(8) uint64_t full[GEMM_STAGES];
   __shared__ __align__(8) uint64_t empty[GEMM_STAGES];
   __shared__ __align__(8) uint64_t done;
-  __shared__ __align__(8) uint64_t zbar;
+  __shared__ __align__(8) uint64_t zbar[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_err;
   __shared__ int s_issued, s_consumed;
@@ -271,7 +278,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       mb_init(&empty[i], 1);
     }
     mb_init(&done, 1);
-    mb_init(&zbar, 1);
+    mb_init(&zbar[0], 1);
+    mb_init(&zbar[1], 1);
     s_err = 0;
     s_issued = 0;
     s_consumed = 0;
@@ -284,12 +292,21 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (MODE == kUpdate && threadIdx.x == 64 && nkb > 0) {
-    // the update's z tile does not depend on the products: pull it into L2 now
-    for (int b = 0; b < TN / 32; ++b) tma_prefetch_2d(&mapE0, n0 + 32 * b, m0);
-  }
   tc_fence_before();
   __syncthreads();
+  // everything above touches only this CTA's own resources; with a
+  // programmatic launch it overlaps the previous kernel's tail.  From here on
+  // this kernel reads what earlier kernels wrote.
+  pdl_wait();
+  if (threadIdx.x == 0) pdl_launch_dependents();
+  if (MODE == kUpdate && threadIdx.x == 64 && nkb > 0) {
+    // the update's z tile does not depend on the products: its first half
+    // goes to its own shared-memory region now, the second half to L2
+    mb_expect_tx(&zbar[0], 65536u);
+    for (int b = 0; b < 4; ++b)
+      tma_load_2d(smem + ZREG0 + (size_t)b * 16384, &mapE0, n0 + 32 * b, m0, &zbar[0]);
+    for (int b = 4; b < TN / 32; ++b) tma_prefetch_2d(&mapE0, n0 + 32 * b, m0);
+  }
   tc_fence_after();
   const uint32_t tmem = s_tmem;
 
@@ -370,23 +387,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (threadIdx.x == 0 && ok) {
       for (int c = 0; c < TN / 32; ++c) tma_reduce_add_2d(&mapE0, epi + (size_t)c * 16384, n0 + 32 * c, m0);
       bulk_commit();
-      bulk_wait_all();
+      bulk_wait_read();  // the grid's completion orders the global writes
     }
   } else {
-    // two rounds of 128 columns: z boxes (4 x 16 KB FP32) loaded by TMA, updated
-    // in place, x = S_lambda(z) split into BF16 hi/lo boxes (2 x 16 KB each),
-    // all stored by TMA
-    unsigned char* zreg = epi;
-    unsigned char* hreg = epi + 65536;
-    unsigned char* lreg = epi + 98304;
+    // two rounds of 128 columns.  Round 0's z boxes (4 x 16 KB FP32) were
+    // loaded at kernel start into ZREG0; round 1's go into the freed stage
+    // buffers [0, 64 KB).  Each round updates z in place, splits x = S_lambda(z)
+    // into BF16 hi/lo boxes (2 x 16 KB each) staged in [64 KB, 128 KB), and
+    // stores everything with TMA.
+    unsigned char* xreg = epi + 65536;
+    if (threadIdx.x == 0 && ok) {
+      mb_expect_tx(&zbar[1], 65536u);
+      for (int b = 0; b < 4; ++b)
+        tma_load_2d(epi + (size_t)b * 16384, &mapE0, n0 + 128 + 32 * b, m0, &zbar[1]);
+    }
 #pragma unroll 1
     for (int round = 0; round < 2 && ok; ++round) {
       const int cbase = n0 + 128 * round;
-      if (threadIdx.x == 0) {
-        mb_expect_tx(&zbar, 65536u);
-        for (int b = 0; b < 4; ++b) tma_load_2d(zreg + (size_t)b * 16384, &mapE0, cbase + 32 * b, m0, &zbar);
-      }
-      const bool zok = mb_wait(&zbar, (uint32_t)round, a.limit_ns);
+      unsigned char* zreg = (round == 0) ? smem + ZREG0 : epi;
+      const bool zok = mb_wait(&zbar[round], 0u, a.limit_ns);
 #pragma unroll 1
       for (int cc = 0; cc < 2; ++cc) {
         const int c = 2 * half + cc;  // 32-column chunk of this round
@@ -414,8 +433,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           lw[2 * j + 1] = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
         }
         // 32 BF16 = 4 chunks of 16 bytes at chunks 4 (c % 2) .. + 3 of box c / 2
-        unsigned char* hb = hreg + (size_t)(c >> 1) * 16384;
-        unsigned char* lb = lreg + (size_t)(c >> 1) * 16384;
+        unsigned char* hb = xreg + (size_t)(c >> 1) * 16384;
+        unsigned char* lb = xreg + 32768 + (size_t)(c >> 1) * 16384;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t off = sw128_off(r, 4 * (c & 1) + q);
@@ -429,18 +448,18 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       if (threadIdx.x == 0 && s_err == 0) {
         for (int b = 0; b < 4; ++b) tma_store_2d(&mapE0, zreg + (size_t)b * 16384, cbase + 32 * b, m0);
         for (int b = 0; b < 2; ++b) {
-          tma_store_2d(&mapE1, hreg + (size_t)b * 16384, cbase + 64 * b, m0);
-          tma_store_2d(&mapE2, lreg + (size_t)b * 16384, cbase + 64 * b, m0);
+          tma_store_2d(&mapE1, xreg + (size_t)b * 16384, cbase + 64 * b, m0);
+          tma_store_2d(&mapE2, xreg + 32768 + (size_t)b * 16384, cbase + 64 * b, m0);
         }
         bulk_commit();
-        bulk_wait_read();
+        bulk_wait_read();  // the x staging boxes are reused by the next round
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) bulk_wait_all();
   }
   if (threadIdx.x == 0 && (!ok || s_err) && nkb > 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
   // let every issued copy land before the shared memory goes away
+  if (MODE == kUpdate && threadIdx.x == 64 && nkb > 0 && !ok) mb_wait(&zbar[0], 0u, a.limit_ns);
   if (threadIdx.x == 0) {
     for (int it = s_consumed; it < s_issued; ++it)
       mb_wait(&full[it % GEMM_STAGES], (uint32_t)((it / GEMM_STAGES) & 1), a.limit_ns);
@@ -580,6 +599,8 @@ __global__ void mrhs_scale_kernel(float* __restrict__ Res, int64_t ld_res,
   __shared__ float tile[32][33];
   const int64_t s0 = (int64_t)blockIdx.x * 32;
   const int64_t j0 = (int64_t)blockIdx.y * 32;
+  pdl_wait();
+  if (threadIdx.x == 0 && threadIdx.y == 0) pdl_launch_dependents();
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int r = ty; r < 32; r += 8) {
     const int64_t s = s0 + r, j = j0 + tx;
@@ -646,11 +667,12 @@ struct rska_mrhs {
   int nsplit = 2;
   int ksplit = 0;                    // residual GEMM CTAs along n (0: automatic)
   int use_graph = 1;
+  int use_pdl = 1;                   // programmatic dependent launches on the main stream
   int64_t k_host = 0;
   int sticky = RSKA_OK;
   uint64_t limit_ns = 2000000000ull;
   cudaGraphExec_t graph = nullptr;   // one chunk of idx_cap iterations
-  int graph_nsplit = -1, graph_ksplit = -1;
+  int graph_nsplit = -1, graph_ksplit = -1, graph_pdl = -1;
 };
 
 namespace {
@@ -714,8 +736,10 @@ cudaError_t dalloc(T** p, size_t count) {
 size_t gemm_smem(int mode, int nsplit) {
   const size_t a = rska::TILE_A_BYTES * ((mode == rska::kUpdate && nsplit == 2) ? 2 : 1);
   const size_t b = rska::TILE_B_BYTES * ((mode == rska::kResidual && nsplit == 2) ? 2 : 1);
-  // the epilogue reuses the stage buffers for 128 KB of output boxes
-  return std::max<size_t>(rska::GEMM_STAGES * (a + b), 131072) + 1024;
+  // the epilogue reuses the stage buffers for 128 KB of output boxes; the
+  // update also keeps the first half of its z tile in 64 KB of its own
+  return std::max<size_t>(rska::GEMM_STAGES * (a + b), 131072) + (mode == rska::kUpdate ? 65536 : 0) +
+         1024;
 }
 
 int residual_splits(const rska_mrhs* h, int* kb_per) {
@@ -760,6 +784,21 @@ cudaError_t enqueue_iterations(rska_mrhs* h, int64_t cnt, cudaStream_t s) {
   const dim3 grid2((unsigned)(h->R_p / rska::TM), (unsigned)(h->n_p / rska::TN), 1);
   const float coef = h->t / (float)h->eta;
   cudaStream_t side = h->side;
+  // launch on s, as a programmatic dependent of the previous kernel when asked
+  auto launch = [&](auto kernel, dim3 grid, dim3 block, size_t smem, bool programmatic,
+                    auto... args) -> cudaError_t {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = (programmatic && h->use_pdl) ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+  };
   auto gather = [&](int64_t k) -> cudaError_t {
     const int b = (int)(k & 1);
     if (k >= 2) {
@@ -781,17 +820,19 @@ cudaError_t enqueue_iterations(rska_mrhs* h, int64_t cnt, cudaStream_t s) {
     const int32_t* tau = h->idx + k * h->eta;
     e = cudaStreamWaitEvent(s, h->ev_gathered[b], 0);
     if (e != cudaSuccess) break;
-    rska::mrhs_gemm_kernel<rska::kResidual><<<grid1, rska::GEMM_THREADS, sm1, s>>>(
-        h->mapAtau[b], h->mapAtau[b], h->mapX[0], h->mapX[1], h->mapRes, h->mapRes, h->mapRes,
-        g1);
+    // the first kernel after the event wait keeps an ordinary dependency
+    e = launch(rska::mrhs_gemm_kernel<rska::kResidual>, grid1, dim3(rska::GEMM_THREADS), sm1,
+               k > 0, h->mapAtau[b], h->mapAtau[b], h->mapX[0], h->mapX[1], h->mapRes, h->mapRes,
+               h->mapRes, g1);
+    if (e != cudaSuccess) break;
     if (k + 1 < cnt && (e = gather(k + 1)) != cudaSuccess) break;
-    rska::mrhs_scale_kernel<<<sgrid, dim3(32, 8), 0, s>>>(h->Res, h->R_p, h->Bt, h->R_p,
-                                                          h->inv_nu, tau, h->eta, h->R, coef,
-                                                          h->Rhi, h->Rlo, h->eta_p);
-    rska::mrhs_gemm_kernel<rska::kUpdate><<<grid2, rska::GEMM_THREADS, sm2, s>>>(
-        h->mapR[0], h->mapR[1], h->mapAtauT[b], h->mapAtauT[b], h->mapZ, h->mapXs[0],
-        h->mapXs[1], g2);
-    e = cudaGetLastError();
+    e = launch(rska::mrhs_scale_kernel, sgrid, dim3(32, 8), 0, true, h->Res, h->R_p, h->Bt,
+               h->R_p, h->inv_nu, tau, h->eta, h->R, coef, h->Rhi, h->Rlo, h->eta_p);
+    if (e != cudaSuccess) break;
+    e = launch(rska::mrhs_gemm_kernel<rska::kUpdate>, grid2, dim3(rska::GEMM_THREADS), sm2, true,
+               h->mapR[0], h->mapR[1], h->mapAtauT[b], h->mapAtauT[b], h->mapZ, h->mapXs[0],
+               h->mapXs[1], g2);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_used[b], s);
   }
   return e;
@@ -951,6 +992,10 @@ int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
       if (value != 0 && value != 1) return RSKA_EINVAL;
       h->use_graph = (int)value;
       return RSKA_OK;
+    case 4:
+      if (value != 0 && value != 1) return RSKA_EINVAL;
+      h->use_pdl = (int)value;
+      return RSKA_OK;
     default:
       return RSKA_EINVAL;
   }
@@ -981,7 +1026,8 @@ int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
                              h->idx, s);
     if (e != cudaSuccess) break;
     if (cnt == h->idx_cap && h->use_graph) {
-      if (!h->graph || h->graph_nsplit != h->nsplit || h->graph_ksplit != h->ksplit) {
+      if (!h->graph || h->graph_nsplit != h->nsplit || h->graph_ksplit != h->ksplit ||
+          h->graph_pdl != h->use_pdl) {
         if (h->graph) {
           cudaGraphExecDestroy(h->graph);
           h->graph = nullptr;
@@ -1001,6 +1047,7 @@ int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
         if (e != cudaSuccess) break;
         h->graph_nsplit = h->nsplit;
         h->graph_ksplit = h->ksplit;
+        h->graph_pdl = h->use_pdl;
       }
       e = cudaGraphLaunch(h->graph, s);
     } else {

@@ -243,7 +243,7 @@ class BatchSolver:
         return nu, thr, alias
 
 
-MRHS_OPTION = {"terms": 0, "ksplit": 1, "watchdog_us": 2, "graph": 3}
+MRHS_OPTION = {"terms": 0, "ksplit": 1, "watchdog_us": 2, "graph": 3, "pdl": 4}
 MRHS_QUERY = {"k": 0, "ksplit": 1, "n_pad": 2, "eta_pad": 3, "R_pad": 4, "terms": 5}
 
 
