@@ -445,7 +445,8 @@ def run_batched(args):
     build.build()
     from paper_2203_10838_gb300.rska import BatchSolver, Solver
     t0 = time.perf_counter()
-    A, a_off, m, n, lda, b, b_off, xhats = batched_problem_set(BATCH_P, BATCH_SEED + rank)
+    P = args.batch_p
+    A, a_off, m, n, lda, b, b_off, xhats = batched_problem_set(P, BATCH_SEED + rank)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     Ad = torch.from_numpy(A).to(dev)
@@ -457,9 +458,11 @@ def run_batched(args):
     bs = BatchSolver(Ad, bd, a_off, m, n, lda, b_off, BATCH_LAM, BATCH_ETA, BATCH_T, BATCH_SEED,
                      stream=stream)
     setup_s = time.perf_counter() - t0
-    max_iters = BATCH_MAX_ITERS
+    # --iters K: every problem runs exactly K iterations (no stopping test)
+    max_iters = args.iters if args.iters is not None else BATCH_MAX_ITERS
+    tol = 0.0 if args.iters is not None else BATCH_TOL
     for _ in range(max(1, args.warmup)):
-        bs.solve(max_iters, tol=BATCH_TOL)
+        bs.solve(max_iters, tol=tol)
     torch.cuda.synchronize(dev)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -467,7 +470,7 @@ def run_batched(args):
     clocks = ClockSampler(local)
     ev0.record(stream)
     for _ in range(args.steps):
-        bs.solve(max_iters, tol=BATCH_TOL)
+        bs.solve(max_iters, tol=tol)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
@@ -482,18 +485,18 @@ def run_batched(args):
     row_bytes = float((iters * BATCH_ETA * (4.0 * n + 12.0)).sum())
     achieved = row_bytes / (ms_step / 1000.0) / 1e9
     # per-problem comparator: the single-system solver looped over a subset
-    sub = list(range(0, BATCH_P, BATCH_P // 32))
+    sub = list(range(0, P, max(1, P // 32)))
     t_loop = 0.0
-    for p in sub:
+    for p in (sub if args.mode != "kernel" else []):
         mp, np_, lp = int(m[p]), int(n[p]), int(lda[p])
         Ap = Ad[int(a_off[p]):int(a_off[p]) + mp * lp].view(mp, lp)
         bp = bd[int(b_off[p]):int(b_off[p]) + mp]
         torch.cuda.synchronize(dev)
         c0 = time.perf_counter()
         with Solver(Ap, bp, BATCH_LAM, BATCH_ETA, BATCH_T, BATCH_SEED, n=np_, stream=stream) as sp:
-            sp.solve_until(max_iters, -(-mp // BATCH_ETA), BATCH_TOL)
+            sp.solve_until(max_iters, -(-mp // BATCH_ETA), tol) if tol > 0 else sp.solve(max_iters)
         t_loop += time.perf_counter() - c0
-    loop_all_s = t_loop * BATCH_P / len(sub)
+    loop_all_s = t_loop * P / len(sub) if args.mode != "kernel" else None
     cpu = None
     if not args.skip_cpu:
         import oracle
@@ -514,19 +517,20 @@ def run_batched(args):
                "sample": f"{done_updates // BATCH_ETA} iterations over the first problems of a "
                          f"32-problem subset, each run for the iterations the GPU needed "
                          f"({el:.1f} s)"}
-    line = {"metric": "batched RSKA: 4096 Gaussian systems to 1e-6 relative residual",
+    line = {"metric": (f"batched RSKA: {P} Gaussian systems to 1e-6 relative residual" if tol > 0
+                       else f"batched RSKA: {P} Gaussian systems, {max_iters} iterations each"),
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(1, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "rska_batched_4096", "P": BATCH_P,
+            "config": {"workload": f"rska_batched_{P}", "P": P,
                        "m": "log-uniform [200, 4000]", "n": "m/2 rounded to 8", "eta": BATCH_ETA,
-                       "t": BATCH_T, "lambda": BATCH_LAM, "tol": BATCH_TOL,
+                       "t": BATCH_T, "lambda": BATCH_LAM, "tol": tol,
                        "A_bytes": int(A.nbytes)},
             "time_to_all_stopped_ms": ms_step,
             "converged": int((rr <= BATCH_TOL).sum()), "max_iters": max_iters,
-            "stalled_at_cap": int((rr > BATCH_TOL).sum()),
+            "stalled_at_cap": int((rr > BATCH_TOL).sum()) if tol > 0 else None,
             "rel_residual_deciles_of_stalled": (np.quantile(rr[rr > BATCH_TOL], [0.1, 0.5, 0.9]).tolist()
-                                                if (rr > BATCH_TOL).any() else None),
+                                                if tol > 0 and (rr > BATCH_TOL).any() else None),
             "iterations_total": int(iters.sum()),
             "iterations_max": int(iters.max()),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -534,9 +538,9 @@ def run_batched(args):
                          "peak_kind": f"{peak_kind} (copy bandwidth)",
                          "kernel": "rska_batched_kernel",
                          "note": "row bytes of all iterations; exact residual checks not counted"},
-            "plain_per_problem_gpu": {"value_s_extrapolated": loop_all_s,
-                                      "impl": "single-system solver looped, 32-problem subset "
-                                              "scaled to 4096",
+            "plain_per_problem_gpu": None if loop_all_s is None else {"value_s_extrapolated": loop_all_s,
+                                      "impl": f"single-system solver looped, {len(sub)}-problem "
+                                              f"subset scaled to {P}",
                                       "speedup_of_batched": loop_all_s / (ms_step / 1000.0)},
             "prep": {"generate_s": gen_s, "h2d_s": h2d_s, "setup_s": setup_s},
             "cpu_baseline": cpu, "clocks": clk}
@@ -616,7 +620,7 @@ def run_unrolled(args):
     hbm_peak, peak_kind = load_peaks()
     achieved = row_reads * (4.0 * U_N) / (ms / 1000.0) / 1e9
     # naive torch autograd comparator on 4 problems, scaled to 64
-    sub = 4
+    sub = 4 if args.mode != "kernel" else 0
     t_naive = 0.0
     for p in range(sub):
         pr = probs[p]
@@ -636,7 +640,7 @@ def run_unrolled(args):
         (0.5 * ((xk - xh) ** 2).sum()).backward()
         torch.cuda.synchronize(dev)
         t_naive += time.perf_counter() - c0
-    naive_ms = 1000.0 * t_naive * U_P / sub
+    naive_ms = 1000.0 * t_naive * U_P / sub if sub else None
     un.close()
     line = {"metric": "unrolled RSKA forward + adjoint (64 x 2048x1024, K=200, eta=64)",
             "value": value, "unit": "row-reads/s", "n_gpus": world, "steps": args.steps,
@@ -649,7 +653,7 @@ def run_unrolled(args):
                          "peak_kind": f"{peak_kind} (copy bandwidth)",
                          "kernel": "unrolled_forward_kernel + unrolled_backward_kernel"},
             "naive_torch_autograd_ms_extrapolated": naive_ms,
-            "speedup_vs_naive_autograd": naive_ms / ms, "clocks": clk}
+            "speedup_vs_naive_autograd": naive_ms / ms if naive_ms else None, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -710,6 +714,13 @@ def run_mrhs(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    if args.mode == "kernel":
+        h.close()
+        if rank == 0:
+            print(json.dumps({"metric": "shared-A multi-RHS RSKA (kernel-only run for profiling)",
+                              "ms_per_step": ms, "iters_per_step": MR_K,
+                              "tflops": achieved}), flush=True)
+        return 0
     # accuracy of the timed solve: relative residual and error per right-hand side (FP64)
     x, _ = h.get_x()
     A64 = A.double()
@@ -816,6 +827,8 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batched", "unrolled", "mrhs"])
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
                     help="kernel: only the timed persistent-kernel steps (for profiling)")
+    ap.add_argument("--batch-p", type=int, default=BATCH_P,
+                    help="batched workload: number of problems (default 4096)")
     ap.add_argument("--iters", type=int, default=None,
                     help="iterations per step (default 300; profiling uses fewer)")
     args = ap.parse_args()
