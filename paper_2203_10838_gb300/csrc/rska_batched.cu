@@ -5,24 +5,28 @@
 // is satisfied").
 //
 // One CTA owns one problem at a time and takes problems from a queue sorted
-// by estimated work (largest first).  Inside a CTA, warps 0..6 consume rows:
-// each thread owns float4 columns t + 224 r of z, x (and the partial update),
-// so a row's dot is a block reduction and its update c_s a_s is local.  Warp
-// 7 only draws: it fills a ring of the next rows of tau (Philox4x32-10 +
-// alias table, 32 draws per warp step, counter word 3 = problem id) with
-// their b_i and 1/||a_i||^2, up to 512 rows ahead.  Each consumer thread
-// streams its own columns of the next rows into a shared-memory slot ring
-// with 16-byte cp.async copies, one commit group per row, up to 30 rows
-// ahead; since a thread reads back only what it copied itself, the slot ring
-// needs no barrier, only the thread's own wait on its copy groups.  (A TMA
-// bulk copy per row is the other choice; its latency of several microseconds
-// per copy is what this layout avoids for rows of 1 to 10 KB.)
+// by estimated work (largest first).  Warp 7 only draws: it fills a ring of
+// the next rows of tau (Philox4x32-10 + alias table, 32 draws per warp step,
+// counter word 3 = problem id) with their b_i and 1/||a_i||^2, up to 512 rows
+// ahead of the last completed iteration, and sleeps when it is ahead.  Warps
+// 0..6 consume rows whole: warp w takes rows s = w, w + 7, ... of every tau_k,
+// streams each with 16-byte cp.async copies into its own ring of shared-memory
+// slots (each lane copies and later reads back only its own columns, so no
+// barrier guards the ring), computes the dot by shuffles and accumulates
+// c_s a_s into its share of the update in registers.  At the end of an
+// iteration the shares are added into one shared vector and every consumer
+// thread applies z -= update, x = S_lambda(z) to a slice of the columns: two
+// block barriers per iteration, none per row.  (A TMA bulk copy per row and a
+// column split of every row over all warps were the earlier designs; their
+// per-row copy latency and per-row instruction and barrier overhead is what
+// this layout removes.)
 //
 // Stopping: every C_p iterations the CTA first looks at an unbiased estimate
 // of ||A_p x - b_p||^2 built for free from the sampled residuals
 // (sum of r_s^2 / (eta p_s) over the window, p_s = ||a_s||^2 / W_p); only when
-// it is within (4 tol)^2 ||b_p||^2 does it run the exact check (FP64, one
-// pass over A_p).  Every device-side wait is
+// it is within (4 tol)^2 ||b_p||^2 does it run the exact check (one pass over
+// A_p; dot products by compensated FP32 Dot2, sums in FP64 -- FP64 arithmetic
+// is slow on this GPU).  Every device-side wait is
 // bounded.
 #include <algorithm>
 #include <cmath>
@@ -42,15 +46,16 @@ namespace {
 constexpr int BT = 256;          // threads per CTA
 constexpr int BC = BT - 32;      // consumer threads (warps 0..6)
 constexpr int BCW = BC / 32;     // consumer warps
-constexpr int BG = 8;            // rows reduced together (one block barrier per group)
-constexpr int BZ = kBatchMaxZ;   // float4 columns per consumer thread
 constexpr int BIR = 512;         // index ring entries (rows drawn ahead; a power of 2)
-constexpr int BMAXD = 30;        // most rows in flight per consumer thread
-constexpr size_t BRING = 56 * 1024;  // bytes of row slots per CTA (3 CTAs per SM)
-constexpr int BCTAS_PER_SM = 3;
-static_assert(BG == 8, "the transpose-reduce sums exactly 8 values");
-static_assert(BCW <= 8, "block sums read two warps per lane");
-static_assert(BRING / ((size_t)BC * BZ * 16) >= 4, "the ring must hold two groups of the widest rows");
+constexpr int BMAXNZ = 21;       // float4 columns per lane: n <= 32 * 21 * 4 = 2688
+constexpr int BRS_MAX = 16;      // ring slots per warp
+constexpr size_t BVEC = (size_t)BMAXNZ * 32 * 16;       // bytes of z, x or the update
+constexpr size_t BRING_OFF = 3 * BVEC;                  // rows start after z, x, update
+constexpr size_t BRING_WARP = 24 * 1024;                // row slots of one consumer warp
+constexpr size_t BSMEM = BRING_OFF + BCW * BRING_WARP;  // dynamic shared memory per CTA
+constexpr int BMAX_ETA = 448;    // rows of one iteration stay inside the index ring
+static_assert(BRING_WARP / BVEC >= 2, "every warp holds two of the widest rows");
+static_assert(BMAX_ETA + 32 <= BIR, "an iteration's rows fit the index ring");
 
 struct BatchArgs {
   int32_t P;
@@ -83,7 +88,6 @@ struct BatchArgs {
   int* queue;
   int* status;
   uint64_t limit_ns;
-  size_t ring_bytes;         // bytes of row slots
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -221,91 +225,308 @@ __device__ __forceinline__ void cp_async_wait_pending(int pending) {
   }
 }
 
-// Sums each of v[0..7] over the warp with 9 shuffles instead of 40: every
-// step halves the values a lane keeps and exchanges the other half with its
-// partner (offsets 16, 8, 4), then offsets 2 and 1 finish a plain butterfly.
-// Lane l returns the warp sum of v[(l >> 2) & 7].
-__device__ __forceinline__ float warp_transpose_sum8(const float (&v)[8], int lane) {
-  float v4[4], v2[2];
-  const bool h4 = (lane & 16) != 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float send = h4 ? v[i] : v[i + 4];
-    const float keep = h4 ? v[i + 4] : v[i];
-    v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  const bool h3 = (lane & 8) != 0;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float send = h3 ? v4[i] : v4[i + 2];
-    const float keep = h3 ? v4[i + 2] : v4[i];
-    v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  const bool h2 = (lane & 4) != 0;
-  float v1 = (h2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? v2[0] : v2[1], 4);
-  v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
-  v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-  return v1;
+// One step of Dot2 (Ogita, Rump and Oishi, "Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26(6), 2005): the product a*b split exactly into
+// h + r by a fused multiply-add (TwoProduct), h added to the running sum p by
+// Knuth's TwoSum with the rounding error q, and q + r gathered in c.  p + c is
+// the dot product as if computed in twice the working precision.
+__device__ __forceinline__ void dot2_acc(float a, float b, float& p, float& c) {
+  const float h = __fmul_rn(a, b);
+  const float r = __fmaf_rn(a, b, -h);
+  const float s = __fadd_rn(p, h);
+  const float z = __fsub_rn(s, p);
+  const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(s, z)), __fsub_rn(h, z));
+  p = s;
+  c = __fadd_rn(c, __fadd_rn(q, r));
 }
 
-__global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ int32_t s_idx[BIR];
-  __shared__ float s_b[BIR];
-  __shared__ float s_iv[BIR];
-  __shared__ float wpart[2][BG][8];
-  __shared__ double dpart[BCW];
-  __shared__ int s_prob;
-  __shared__ volatile long long s_drawn;  // rows of the current problem drawn so far
-  __shared__ volatile long long s_used;   // rows consumed (their ring entries are free)
-  __shared__ volatile int s_stop;         // the current problem is finished
-  __shared__ volatile int s_abort;
-  __shared__ int s_gate;
-  __shared__ double s_relres;
+// Shared state of the CTA's current problem.
+struct BatchShared {
+  int32_t idx[BIR];
+  float b[BIR];
+  float iv[BIR];
+  float est[BCW];
+  double dpart[BCW];
+  int prob;
+  volatile long long drawn;  // rows of the current problem drawn so far
+  volatile long long used;   // rows whose iteration is complete (ring entries free)
+  volatile int stop;         // the current problem is finished
+  volatile int abort;
+  int gate;
+  double relres;
+};
 
+// The consumer side for one problem with n4 <= 32 NZ: warp w takes rows
+// s = w, w + 7, ... of every tau_k; lane l owns float4 columns l + 32 j of
+// x (registers), of its share of the update (registers) and of every row it
+// copies (shared-memory ring slots of its warp, filled by its own cp.async
+// and read back only by itself, so the ring needs no barrier).  Per row: the
+// warp's dot <a_s, x> by shuffles, c_s = (t/eta) (<a_s, x> - b_s)/||a_s||^2,
+// update += c_s a_s.  Per iteration: the warps' updates are added into one
+// shared vector, then z -= update, x = S_lambda(z) (two consumer barriers).
+template <int NZ>
+__device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned char* smem, int p,
+                                int64_t* iters_out, double* relres_out, bool* fail_out) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
   const int eta = a.eta;
-  float4* zsh = reinterpret_cast<float4*>(smem);                        // BZ x BC
-  unsigned char* ring = smem + (size_t)BZ * BC * sizeof(float4);        // row slots
+  const int m = a.m[p];
+  const int n = a.n[p];
+  const int n4 = (n + 3) >> 2;
+  const int64_t lda = a.lda[p];
+  const float* Ap = a.A + a.a_off[p];
+  const float* bp = a.b + a.b_off[p];
+  const int64_t C = a.check_every > 0 ? a.check_every : (m + eta - 1) / eta;
+  const int64_t kmax = a.max_iters;
+  const float lam = a.lambda;
+  const float coef = a.coef;
+  const float w_over_eta = (float)(a.W[p] / (double)eta);
+  float4* zsh = reinterpret_cast<float4*>(smem);
+  float4* xsh = zsh + BMAXNZ * 32;
+  float4* dsh = xsh + BMAXNZ * 32;
+  const uint32_t slot_bytes = (uint32_t)n4 * 16u;
+  const int RS = min(BRS_MAX, (int)(BRING_WARP / slot_bytes));  // ring slots of this warp
+  unsigned char* ring = smem + BRING_OFF + (size_t)warp * BRING_WARP;
+  // rows of this warp per iteration
+  const int cw = (eta > warp) ? (eta - warp + BCW - 1) / BCW : 0;
+  const int64_t trows = (int64_t)cw * kmax;  // rows of this warp over all iterations
 
-  if (tid == 0) s_abort = 0;
+  float4 xr[NZ], dl[NZ];
+#pragma unroll
+  for (int j = 0; j < NZ; ++j) {
+    xr[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float est = 0.f;  // lane 0: this warp's share of the windowed residual estimate
+  int64_t issued = 0;   // rows of this warp whose copies this lane has issued
+  int64_t drawn = 0;    // cached S.drawn
+  bool fail = false;
+  // the next row to issue, kept incrementally (no 64-bit divisions per row):
+  // its global sequence number, its position in the iteration and its slot
+  int64_t e_iss = warp;
+  int i_iss = 0;
+  int slot_iss = 0;
+
+  // copy the next row of this warp into its ring slot (one commit group);
+  // with `block`, wait until the producer has drawn it
+  auto issue_row = [&](bool block) -> int {
+    const int64_t e = e_iss;
+    if (e >= drawn) {
+      drawn = S.drawn;
+      if (e >= drawn) {
+        if (!block) return 0;
+        const uint64_t t0 = global_timer_ns();
+        uint32_t spins = 0;
+        while ((drawn = S.drawn) <= e) {
+          if (S.abort) return -1;
+          if ((++spins & 63u) == 0 && global_timer_ns() - t0 > a.limit_ns) return -1;
+        }
+      }
+      __threadfence_block();
+    }
+    const int32_t row = S.idx[(int)e & (BIR - 1)];
+    const float4* src = reinterpret_cast<const float4*>(Ap + (int64_t)row * lda);
+    float4* dst = reinterpret_cast<float4*>(ring + (size_t)slot_iss * slot_bytes);
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+      const int col = lane + 32 * j;
+      if (col < n4) cp_async16(dst + col, src + col);
+    }
+    cp_async_commit();
+    ++issued;
+    slot_iss = (slot_iss + 1 == RS) ? 0 : slot_iss + 1;
+    if (++i_iss == cw) {
+      i_iss = 0;
+      e_iss += eta - BCW * (cw - 1);  // first row of this warp in the next iteration
+    } else {
+      e_iss += BCW;
+    }
+    return 1;
+  };
+
+  int64_t t = 0;  // rows of this warp consumed
+  int slot_t = 0; // ring slot of row t
+  int64_t k = 0;
+  for (; k < kmax && !fail; ++k) {
+    for (int i = 0; i < cw; ++i, ++t, slot_t = (slot_t + 1 == RS) ? 0 : slot_t + 1) {
+      // row t must be in flight; keep up to RS rows in flight when drawn
+      while (issued <= t) {
+        if (issue_row(true) < 0) {
+          fail = true;
+          break;
+        }
+      }
+      if (fail) break;
+      while (issued < t + RS && issued < trows && issue_row(false) > 0) {
+      }
+      { const int64_t pend = issued - t - 1; cp_async_wait_pending(pend < 30 ? (int)pend : 30); }
+      const int64_t e = k * eta + warp + BCW * i;
+      const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)slot_t * slot_bytes);
+      float d = 0.f;
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        const int col = lane + 32 * j;
+        if (col < n4) {
+          float4 v = rowp[col];
+          if (col == n4 - 1) v = mask_tail(v, col, n);
+          d += dot4(v, xr[j]);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      const int ei = (int)e & (BIR - 1);
+      const float iv = S.iv[ei];
+      const float r = d - S.b[ei];
+      if (lane == 0) est = fmaf(w_over_eta * r, r * iv, est);
+      const float cval = coef * (r * iv);
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        const int col = lane + 32 * j;
+        if (col < n4) {
+          float4 v = rowp[col];
+          if (col == n4 - 1) v = mask_tail(v, col, n);
+          dl[j].x = fmaf(cval, v.x, dl[j].x);
+          dl[j].y = fmaf(cval, v.y, dl[j].y);
+          dl[j].z = fmaf(cval, v.z, dl[j].z);
+          dl[j].w = fmaf(cval, v.w, dl[j].w);
+        }
+      }
+    }
+    // every consumer thread reaches the barriers below whether it failed or not
+    // ---- end of iteration k: update = sum of the warps' shares ----
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+      const int col = lane + 32 * j;
+      if (col < n4) {
+        float* dp = reinterpret_cast<float*>(dsh + col);
+        atomicAdd(dp + 0, dl[j].x);
+        atomicAdd(dp + 1, dl[j].y);
+        atomicAdd(dp + 2, dl[j].z);
+        atomicAdd(dp + 3, dl[j].w);
+      }
+      dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (consumer_sync_or(fail ? 1 : 0)) {
+      fail = true;
+      break;
+    }
+    if (tid == 0) S.used = (k + 1) * (int64_t)eta;
+    for (int c4 = tid; c4 < n4; c4 += BC) {
+      float4 zv = zsh[c4];
+      const float4 dv = dsh[c4];
+      zv.x -= dv.x;
+      zv.y -= dv.y;
+      zv.z -= dv.z;
+      zv.w -= dv.w;
+      zv = mask_tail(zv, c4, n);
+      zsh[c4] = zv;
+      xsh[c4] = soft_shrink4(zv, lam);
+      dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (lane == 0) S.est[warp] = est;
+    consumer_sync();
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+      const int col = lane + 32 * j;
+      xr[j] = (col < n4) ? xsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const bool last = (k + 1 == kmax);
+    if ((k + 1) % C != 0 && !last) continue;
+
+    // ---- check point: gate on the estimate, then the exact residual ----
+    if (tid == 0) {
+      float tot = 0.f;
+      for (int w = 0; w < BCW; ++w) tot += S.est[w];
+      const float window = (float)((k + 1) % C == 0 ? C : (k + 1) % C);
+      const double est_mean = (double)(tot / window);
+      const double lim = 4.0 * a.tol;
+      S.gate = last || (a.tol > 0.0 && est_mean <= lim * lim * a.bnorm2[p]);
+    }
+    est = 0.f;
+    consumer_sync();
+    if (S.gate) {
+      // exact check: one warp per row; each lane's share of <a_i, x> by the
+      // compensated dot product Dot2 (FP32, as accurate as twice the working
+      // precision), the lanes' shares and r_i^2 summed in FP64
+      double acc = 0.0;
+      for (int i = warp; i < m; i += BCW) {
+        const float4* row = reinterpret_cast<const float4*>(Ap + (int64_t)i * lda);
+        float ph = 0.f, pl = 0.f;
+        for (int c4 = lane; c4 < n4; c4 += 32) {
+          float4 v = __ldg(row + c4);
+          if (c4 == n4 - 1) v = mask_tail(v, c4, n);
+          const float4 xv = xsh[c4];
+          dot2_acc(v.x, xv.x, ph, pl);
+          dot2_acc(v.y, xv.y, ph, pl);
+          dot2_acc(v.z, xv.z, ph, pl);
+          dot2_acc(v.w, xv.w, ph, pl);
+        }
+        double dd = (double)ph + (double)pl;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        if (lane == 0) {
+          const double ri = dd - (double)__ldg(bp + i);
+          acc += ri * ri;
+        }
+      }
+      if (lane == 0) S.dpart[warp] = acc;
+      consumer_sync();
+      if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < BCW; ++w) tot += S.dpart[w];
+        const double bb = a.bnorm2[p];
+        S.relres = sqrt(tot) / (bb > 0.0 ? sqrt(bb) : 1e-30);
+      }
+      consumer_sync();
+      if ((a.tol > 0.0 && S.relres <= a.tol) || last) {
+        k += 1;
+        break;
+      }
+    }
+  }
+  // drain this thread's prefetched rows before the ring is reused
+  cp_async_wait_all();
+  *iters_out = k;
+  *relres_out = S.relres;
+  *fail_out = fail;
+
+}
+
+__global__ void __launch_bounds__(BT, 1) rska_batched_kernel(BatchArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ BatchShared S;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int eta = a.eta;
+  if (tid == 0) S.abort = 0;
   __syncthreads();
-  int gcount = 0;
 
   for (;;) {
     if (tid == 0) {
       const int qi = atomicAdd(a.queue, 1);
-      s_prob = (qi < a.P && ld_relaxed_s32(a.status) == kStatusOk) ? a.order[qi] : -1;
-      s_stop = 0;
-      s_drawn = 0;
-      s_used = 0;
-      s_relres = -1.0;
+      S.prob = (qi < a.P && ld_relaxed_s32(a.status) == kStatusOk) ? a.order[qi] : -1;
+      S.stop = 0;
+      S.drawn = 0;
+      S.used = 0;
+      S.relres = -1.0;
     }
     __syncthreads();
-    const int p = s_prob;
+    const int p = S.prob;
     if (p < 0) break;
     const int m = a.m[p];
     const int n = a.n[p];
     const int n4 = (n + 3) >> 2;
-    const int64_t lda = a.lda[p];
-    const float* Ap = a.A + a.a_off[p];
     const float* bp = a.b + a.b_off[p];
     const int64_t ro = a.row_off[p];
-    const int64_t C = a.check_every > 0 ? a.check_every : (m + eta - 1) / eta;
     const int64_t kmax = a.max_iters;
-    // ring geometry for this problem: slots of n4 float4, groups of bgp rows,
-    // `dist` >= bgp rows in flight (nslots >= 5 for n4 <= BC * BZ)
-    const int nslots = min(BMAXD + BG, (int)(a.ring_bytes / ((size_t)n4 * 16)));
-    const int bgp = min(BG, nslots / 2);
-    const int dist = min(BMAXD, nslots - bgp);
 
     if (warp == BCW) {
       // ------------------------------------------------- index producer --
       // Draws rows e, e+1, ... of this problem's index stream (row e is draw
-      // s = e mod eta of iteration e / eta) into the index ring, up to BIR
-      // rows ahead of the consumers.
+      // s = e mod eta of iteration e / eta) with b and 1/||a||^2 into the
+      // index ring, up to BIR rows ahead of the last completed iteration.
       int64_t jj0 = 0;
       int s0 = 0;
       const int64_t total = kmax * (int64_t)eta;
@@ -313,18 +534,18 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
         if (lane == 0) {
           const uint64_t t0 = global_timer_ns();
           uint32_t spins = 0;
-          while (e + 32 - s_used > BIR && !s_stop && !s_abort) {
+          while (e + 32 - S.used > BIR && !S.stop && !S.abort) {
             // far ahead: sleep rather than spin, a spinning warp steals the
             // shared-memory pipe from the consumers
             __nanosleep(500);
             if ((++spins & 15u) == 0 && global_timer_ns() - t0 > a.limit_ns) {
               atomicCAS(a.status, kStatusOk, kStatusTimeout);
-              s_abort = 1;
+              S.abort = 1;
             }
           }
         }
         __syncwarp();
-        if (s_stop || s_abort) break;
+        if (S.stop || S.abort) break;
         int s = s0 + lane;
         int64_t jj = jj0;
         while (s >= eta) {
@@ -336,12 +557,12 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
                   (uint32_t)m, &i0, &i1);
         const int32_t row = (s & 1) ? i1 : i0;
         const int slot = (int)(e + lane) & (BIR - 1);
-        s_idx[slot] = row;
-        s_b[slot] = __ldg(bp + row);
-        s_iv[slot] = __ldg(a.inv_nu + ro + row);
+        S.idx[slot] = row;
+        S.b[slot] = __ldg(bp + row);
+        S.iv[slot] = __ldg(a.inv_nu + ro + row);
         __syncwarp();
         __threadfence_block();
-        if (lane == 0) s_drawn = e + 32;
+        if (lane == 0) S.drawn = e + 32;
         s0 += 32;
         while (s0 >= eta) {
           s0 -= eta;
@@ -350,227 +571,50 @@ __global__ void __launch_bounds__(BT, BCTAS_PER_SM) rska_batched_kernel(BatchArg
       }
     } else {
       // ------------------------------------------------------ consumers --
-      const float lam = a.lambda;
-      const float coef = a.coef;
-      const float w_over_eta = (float)(a.W[p] / (double)eta);
-      float4 xr[BZ], dl[BZ];
-#pragma unroll
-      for (int r = 0; r < BZ; ++r) {
-        xr[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        zsh[(size_t)r * BC + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4* zsh = reinterpret_cast<float4*>(smem);
+      float4* xsh = zsh + BMAXNZ * 32;
+      float4* dsh = xsh + BMAXNZ * 32;
+      for (int c4 = tid; c4 < n4; c4 += BC) {
+        zsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        xsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      float est = 0.f;  // lanes 0..7 of warp 0: windowed estimate of ||A x - b||^2 (times the window)
-      bool ok = true;   // the last refill got its rows
-      int64_t issued = 0;   // rows whose copies this thread has issued
-      int64_t drawn = 0;    // cached s_drawn
-      int64_t q = 0;        // rows consumed
-      int islot = 0;        // slot of row `issued`
-      int qslot = 0;        // slot of row q
-      const uint32_t slot_bytes = (uint32_t)n4 * 16u;
+      consumer_sync();
+      const int nz = (n4 + 31) >> 5;
+      int64_t iters = 0;
+      double relres = -1.0;
       bool fail = false;
-
-      // issue the copies of row `issued` (this thread's columns) as one group
-      auto issue_next = [&]() -> bool {
-        if (issued >= drawn) {
-          const uint64_t t0 = global_timer_ns();
-          uint32_t spins = 0;
-          while ((drawn = s_drawn) <= issued) {
-            if (s_abort) return false;
-            if ((++spins & 63u) == 0 && global_timer_ns() - t0 > a.limit_ns) return false;
-          }
-          __threadfence_block();
-        }
-        const int32_t row = s_idx[(int)issued & (BIR - 1)];
-        const float4* src = reinterpret_cast<const float4*>(Ap + (int64_t)row * lda);
-        float4* dst = reinterpret_cast<float4*>(ring + islot * slot_bytes);
-        islot = (islot + 1 == nslots) ? 0 : islot + 1;
-#pragma unroll
-        for (int r = 0; r < BZ; ++r) {
-          const int col = tid + BC * r;
-          if (col < n4) cp_async16(dst + col, src + col);
-        }
-        cp_async_commit();
-        ++issued;
-        return true;
-      };
-
-      const int64_t total = kmax * (int64_t)eta;
-      for (int j = 0; j < dist && issued < total && ok; ++j) ok = issue_next();
-      fail = consumer_sync_or(!ok) != 0;
-      int64_t k = 0;
-      for (; k < kmax && !fail; ++k) {
-        for (int q0 = 0; q0 < eta; q0 += bgp) {
-          const int ng = min(bgp, eta - q0);
-          // rows q .. q+ng-1 have landed once at most issued-(q+ng) groups are pending
-          cp_async_wait_pending((int)(issued - (q + ng)));
-          // this thread's share of the ng dots <a_s, x>
-          float pd[BG];
-#pragma unroll
-          for (int g = 0; g < BG; ++g) {
-            pd[g] = 0.f;
-            if (g < ng) {
-              const int sl = (qslot + g < nslots) ? qslot + g : qslot + g - nslots;
-              const float4* rowp = reinterpret_cast<const float4*>(ring + sl * slot_bytes);
-#pragma unroll
-              for (int r = 0; r < BZ; ++r) {
-                const int col = tid + BC * r;
-                if (col < n4) {
-                  float4 v = rowp[col];
-                  if (col == n4 - 1) v = mask_tail(v, col, n);
-                  pd[g] += dot4(v, xr[r]);
-                }
-              }
-            }
-          }
-          // warp sums of the 8 values by a transpose-reduce (9 shuffles): lane l
-          // ends with the sum of value (l >> 2) & 7
-          const float v1 = warp_transpose_sum8(pd, lane);
-          const int wp = gcount & 1;
-          ++gcount;
-          if ((lane & 3) == 0) wpart[wp][(lane >> 2) & 7][warp] = v1;
-          if (consumer_sync_or(!ok)) {
-            fail = true;
-            break;
-          }
-          if (tid == 0) s_used = q;  // ring entries before this group are free
-          // block sums: lane l gets <a_s, x> for s = q + (l & 7)
-          const int gl = lane & 7;
-          const int w0 = lane >> 3;
-          float d = wpart[wp][gl][w0] + ((w0 + 4 < BCW) ? wpart[wp][gl][w0 + 4] : 0.f);
-          d += __shfl_xor_sync(0xffffffffu, d, 8);
-          d += __shfl_xor_sync(0xffffffffu, d, 16);
-          float cl = 0.f;
-          if (gl < ng) {
-            const int e = (int)(q + gl) & (BIR - 1);
-            const float iv = s_iv[e];
-            const float r = d - s_b[e];
-            cl = coef * (r * iv);
-            if (warp == 0 && lane < 8) est = fmaf(w_over_eta * r, r * iv, est);
-          }
-          // z update contribution sum_s c_s a_s on this thread's columns
-#pragma unroll
-          for (int g = 0; g < BG; ++g) {
-            const float cval = __shfl_sync(0xffffffffu, cl, g);
-            if (g < ng) {
-              const int sl = (qslot + g < nslots) ? qslot + g : qslot + g - nslots;
-              const float4* rowp = reinterpret_cast<const float4*>(ring + sl * slot_bytes);
-#pragma unroll
-              for (int r = 0; r < BZ; ++r) {
-                const int col = tid + BC * r;
-                if (col < n4) {
-                  float4 v = rowp[col];
-                  if (col == n4 - 1) v = mask_tail(v, col, n);
-                  dl[r].x = fmaf(cval, v.x, dl[r].x);
-                  dl[r].y = fmaf(cval, v.y, dl[r].y);
-                  dl[r].z = fmaf(cval, v.z, dl[r].z);
-                  dl[r].w = fmaf(cval, v.w, dl[r].w);
-                }
-              }
-            }
-          }
-          // the slots just used are free: refill them with the rows `dist` ahead
-          q += ng;
-          qslot = (qslot + ng < nslots) ? qslot + ng : qslot + ng - nslots;
-          while (ok && issued < q + dist && issued < total) ok = issue_next();
-        }
-        if (fail) break;
-        // z -= Delta, x = S_lambda(z) on this thread's columns
-#pragma unroll
-        for (int r = 0; r < BZ; ++r) {
-          const int col = tid + BC * r;
-          if (col < n4) {
-            float4 zv = zsh[(size_t)r * BC + tid];
-            zv.x -= dl[r].x;
-            zv.y -= dl[r].y;
-            zv.z -= dl[r].z;
-            zv.w -= dl[r].w;
-            zv = mask_tail(zv, col, n);
-            zsh[(size_t)r * BC + tid] = zv;
-            xr[r] = soft_shrink4(zv, lam);
-          }
-          dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const bool last = (k + 1 == kmax);
-        if ((k + 1) % C != 0 && !last) continue;
-
-        // ---- check point: gate on the estimate, then the exact residual ----
-        if (warp == 0) {
-#pragma unroll
-          for (int o = 4; o >= 1; o >>= 1) est += __shfl_xor_sync(0xffffffffu, est, o);
-        }
-        if (tid == 0) {
-          const float window = (float)((k + 1) % C == 0 ? C : (k + 1) % C);
-          const double est_mean = (double)(est / window);
-          const double lim = 4.0 * a.tol;
-          s_gate = last || (a.tol > 0.0 && est_mean <= lim * lim * a.bnorm2[p]);
-        }
-        est = 0.f;
-        consumer_sync();
-        if (s_gate) {
-          // exact check in FP64: one warp per row, products and sums in FP64
-          double acc = 0.0;
-          for (int i = warp; i < m; i += BCW) {
-            const float4* row = reinterpret_cast<const float4*>(Ap + (int64_t)i * lda);
-            double d = 0.0;
-            for (int c4 = lane; c4 < n4; c4 += 32) {
-              float4 v = __ldg(row + c4);
-              if (c4 == n4 - 1) v = mask_tail(v, c4, n);
-              const float4 xv = soft_shrink4(zsh[c4], lam);  // column c4 lives at [c4 / BC][c4 % BC]
-              d = fma((double)v.x, (double)xv.x, d);
-              d = fma((double)v.y, (double)xv.y, d);
-              d = fma((double)v.z, (double)xv.z, d);
-              d = fma((double)v.w, (double)xv.w, d);
-            }
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            if (lane == 0) {
-              const double ri = d - (double)__ldg(bp + i);
-              acc += ri * ri;
-            }
-          }
-          if (lane == 0) dpart[warp] = acc;
-          consumer_sync();
-          if (tid == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < BCW; ++w) tot += dpart[w];
-            const double bb = a.bnorm2[p];
-            s_relres = sqrt(tot) / (bb > 0.0 ? sqrt(bb) : 1e-30);
-          }
-          consumer_sync();
-          if ((a.tol > 0.0 && s_relres <= a.tol) || last) {
-            k += 1;
-            break;
-          }
-        }
-      }
-      // a refill after the last barrier may have timed out
-      if (!fail) fail = consumer_sync_or(!ok) != 0;
-      // problem finished (or failed): drain this thread's prefetches before the
-      // ring is reused, publish results, release the producer
-      cp_async_wait_all();
+      if (nz <= 1)
+        consume_problem<1>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 2)
+        consume_problem<2>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 4)
+        consume_problem<4>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 8)
+        consume_problem<8>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 16)
+        consume_problem<16>(a, S, smem, p, &iters, &relres, &fail);
+      else
+        consume_problem<BMAXNZ>(a, S, smem, p, &iters, &relres, &fail);
+      // problem finished (or failed): publish results, release the producer
       if (tid == 0) {
-        s_stop = 1;
+        S.stop = 1;
         if (fail) {
           atomicCAS(a.status, kStatusOk, kStatusTimeout);
-          s_abort = 1;
+          S.abort = 1;
         }
-        a.iters[p] = k;
-        a.relres[p] = s_relres;
+        a.iters[p] = iters;
+        a.relres[p] = relres;
       }
-      float* zo = a.z + a.x_off[p];
-      float* xo = a.x + a.x_off[p];
-#pragma unroll
-      for (int r = 0; r < BZ; ++r) {
-        const int col = tid + BC * r;
-        if (col < n4) {
-          reinterpret_cast<float4*>(zo)[col] = zsh[(size_t)r * BC + tid];
-          reinterpret_cast<float4*>(xo)[col] = xr[r];
-        }
+      float4* zo = reinterpret_cast<float4*>(a.z + a.x_off[p]);
+      float4* xo = reinterpret_cast<float4*>(a.x + a.x_off[p]);
+      for (int c4 = tid; c4 < n4; c4 += BC) {
+        zo[c4] = zsh[c4];
+        xo[c4] = xsh[c4];
       }
     }
     __syncthreads();
-    if (s_abort) break;
+    if (S.abort) break;
   }
   cp_async_wait_all();
 }
@@ -663,7 +707,6 @@ BatchArgs make_args(rska_batch* bt) {
   a.queue = bt->queue;
   a.status = bt->status;
   a.limit_ns = bt->limit_ns;
-  a.ring_bytes = rska::BRING;
   return a;
 }
 
@@ -682,6 +725,7 @@ int rska_batch_setup(rska_batch** out, int32_t P, const float* A, const int64_t*
       !std::isfinite(t))
     return RSKA_EINVAL;
   if ((reinterpret_cast<uintptr_t>(A) % 16) != 0) return RSKA_EINVAL;
+  if (eta > rska::BMAX_ETA) return RSKA_EUNSUPPORTED;
   std::vector<int32_t> hm(P), hn(P);
   std::vector<int64_t> row_off(P), x_off(P + 1);
   int64_t rows = 0, xs = 0;
@@ -691,7 +735,7 @@ int rska_batch_setup(rska_batch** out, int32_t P, const float* A, const int64_t*
         a_off[p] < 0 || b_off[p] < 0 || m[p] > 0x7fffffff)
       return RSKA_EINVAL;
     const int64_t n4 = (n[p] + 3) / 4;
-    if (n4 > (int64_t)rska::BC * rska::BZ) return RSKA_EUNSUPPORTED;
+    if (n4 > (int64_t)32 * rska::BMAXNZ) return RSKA_EUNSUPPORTED;
     hm[p] = (int32_t)m[p];
     hn[p] = (int32_t)n[p];
     row_off[p] = rows;
@@ -798,7 +842,7 @@ int rska_batch_solve(rska_batch* bt, int64_t max_iters, double tol, int64_t chec
   a.max_iters = max_iters;
   a.tol = tol;
   a.check_every = check_every;
-  const size_t smem = rska::BRING + (size_t)rska::BZ * rska::BC * 16;
+  const size_t smem = rska::BSMEM;
   cudaError_t e = cudaFuncSetAttribute(rska::rska_batched_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaMemsetAsync(bt->queue, 0, sizeof(int), s);
