@@ -192,7 +192,7 @@ typedef struct rska_batch rska_batch;
  *   b       device, borrowed: b_p at element offset b_off[p] (m[p] floats).
  *   a_off, m, n, lda, b_off   HOST arrays of P entries (copied).
  *   lambda, eta, t, seed      shared by all problems, as for rska_setup.
- * Limits: n[p] <= 2688.  Synchronizes.  Errors: EINVAL, EUNSUPPORTED, ENOMEM,
+ * Limits: n[p] <= 2688, eta <= 448.  Synchronizes.  Errors: EINVAL, EUNSUPPORTED, ENOMEM,
  * ECUDA, and EZEROROW / ENONFINITE of the first failing problem.
  */
 int rska_batch_setup(rska_batch **out, int32_t P, const float *A, const int64_t *a_off,
@@ -203,10 +203,14 @@ int rska_batch_setup(rska_batch **out, int32_t P, const float *A, const int64_t 
 /*
  * rska_batch_solve -- from z_p = 0, iterate every problem until its relative
  * residual ||A_p x - b_p|| / ||b_p|| <= tol (checked every check_every
- * iterations, 0 = ceil(m_p/eta); the exact FP64 check runs only
- * when a running estimate from the sampled residuals is within 4 tol) or
- * until max_iters.  tol = 0 runs exactly max_iters iterations on every problem.
- * One CTA per problem, problems taken largest first.  Asynchronous.
+ * iterations, 0 = ceil(m_p/eta)) or until max_iters.  The exact check (dot
+ * products by compensated FP32 summation, accurate as if in twice the
+ * working precision; sums of squares in FP64) runs only when a running
+ * estimate from the sampled residuals is within 4 tol, and after an exact
+ * check that does not stop the problem the next 1, 3, 7 or 15 passing check
+ * points are skipped.  tol = 0 runs exactly max_iters iterations on every
+ * problem (the reported residual is that of the last iterate).  One CTA per
+ * problem at a time, problems taken largest first.  Asynchronous.
  */
 int rska_batch_solve(rska_batch *bt, int64_t max_iters, double tol, int64_t check_every);
 

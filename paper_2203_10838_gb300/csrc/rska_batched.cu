@@ -26,7 +26,9 @@
 // (sum of r_s^2 / (eta p_s) over the window, p_s = ||a_s||^2 / W_p); only when
 // it is within (4 tol)^2 ||b_p||^2 does it run the exact check (one pass over
 // A_p; dot products by compensated FP32 Dot2, sums in FP64 -- FP64 arithmetic
-// is slow on this GPU).  Every device-side wait is
+// is slow on this GPU).  After an exact check that does not stop the problem,
+// the next 1, 3, 7, 15 (at most) passing windows are skipped, so a problem
+// hovering just above tol does not pay a pass over A_p every window.  Every device-side wait is
 // bounded.
 #include <algorithm>
 #include <cmath>
@@ -253,6 +255,8 @@ struct BatchShared {
   volatile int stop;         // the current problem is finished
   volatile int abort;
   int gate;
+  int skip;                  // passing windows to skip before the next exact check
+  int backoff;               // next value of skip after a failed exact check
   double relres;
 };
 
@@ -363,16 +367,21 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       { const int64_t pend = issued - t - 1; cp_async_wait_pending(pend < 30 ? (int)pend : 30); }
       const int64_t e = k * eta + warp + BCW * i;
       const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)slot_t * slot_bytes);
-      float d = 0.f;
+      // four independent partial sums keep the FMA chain short
+      float dp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
         if (col < n4) {
           float4 v = rowp[col];
           if (col == n4 - 1) v = mask_tail(v, col, n);
-          d += dot4(v, xr[j]);
+          dp[j & 3] = fmaf(v.x, xr[j].x, dp[j & 3]);
+          dp[j & 3] = fmaf(v.y, xr[j].y, dp[j & 3]);
+          dp[j & 3] = fmaf(v.z, xr[j].z, dp[j & 3]);
+          dp[j & 3] = fmaf(v.w, xr[j].w, dp[j & 3]);
         }
       }
+      float d = (dp[0] + dp[1]) + (dp[2] + dp[3]);
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       const int ei = (int)e & (BIR - 1);
@@ -441,7 +450,12 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       const float window = (float)((k + 1) % C == 0 ? C : (k + 1) % C);
       const double est_mean = (double)(tot / window);
       const double lim = 4.0 * a.tol;
-      S.gate = last || (a.tol > 0.0 && est_mean <= lim * lim * a.bnorm2[p]);
+      const bool open = a.tol > 0.0 && est_mean <= lim * lim * a.bnorm2[p];
+      // after an exact check that did not stop the problem, skip the next
+      // 1, 2, 4, .. 16 windows whose estimate passes (the estimate hovers
+      // near the gate while the residual is just above tol)
+      S.gate = last || (open && S.skip == 0);
+      if (open && S.skip > 0) --S.skip;
     }
     est = 0.f;
     consumer_sync();
@@ -453,14 +467,26 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       for (int i = warp; i < m; i += BCW) {
         const float4* row = reinterpret_cast<const float4*>(Ap + (int64_t)i * lda);
         float ph = 0.f, pl = 0.f;
-        for (int c4 = lane; c4 < n4; c4 += 32) {
-          float4 v = __ldg(row + c4);
-          if (c4 == n4 - 1) v = mask_tail(v, c4, n);
-          const float4 xv = xsh[c4];
-          dot2_acc(v.x, xv.x, ph, pl);
-          dot2_acc(v.y, xv.y, ph, pl);
-          dot2_acc(v.z, xv.z, ph, pl);
-          dot2_acc(v.w, xv.w, ph, pl);
+        // 4 loads per lane in flight at a time
+        for (int j0 = 0; j0 < NZ; j0 += 4) {
+          float4 v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c4 = lane + 32 * (j0 + u);
+            v[u] = (j0 + u < NZ && c4 < n4) ? __ldg(row + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c4 == n4 - 1) v[u] = mask_tail(v[u], c4, n);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c4 = lane + 32 * (j0 + u);
+            if (j0 + u < NZ && c4 < n4) {
+              const float4 xv = xsh[c4];
+              dot2_acc(v[u].x, xv.x, ph, pl);
+              dot2_acc(v[u].y, xv.y, ph, pl);
+              dot2_acc(v[u].z, xv.z, ph, pl);
+              dot2_acc(v[u].w, xv.w, ph, pl);
+            }
+          }
         }
         double dd = (double)ph + (double)pl;
 #pragma unroll
@@ -482,6 +508,10 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       if ((a.tol > 0.0 && S.relres <= a.tol) || last) {
         k += 1;
         break;
+      }
+      if (tid == 0) {
+        S.skip = S.backoff;
+        S.backoff = min(2 * S.backoff + 1, 15);
       }
     }
   }
@@ -511,6 +541,8 @@ __global__ void __launch_bounds__(BT, 1) rska_batched_kernel(BatchArgs a) {
       S.drawn = 0;
       S.used = 0;
       S.relres = -1.0;
+      S.skip = 0;
+      S.backoff = 1;
     }
     __syncthreads();
     const int p = S.prob;
