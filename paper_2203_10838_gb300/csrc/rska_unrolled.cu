@@ -67,6 +67,9 @@ struct UnrolledArgs {
   float* gb;                 // dL/db, packed by b_off
   float* glam;               // per problem
   float* gt;                 // per problem
+  int32_t* tidx;             // row-form kernels: tau_k per problem and iteration, [P][K][eta]
+  float* tiv;                // 1/||a||^2 at tau_k, same layout
+  float* tb;                 // b at tau_k for the current b, same layout
 };
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
@@ -412,6 +415,44 @@ __global__ void __launch_bounds__(UT, 1) unrolled_backward_kernel(UnrolledArgs a
   }
 }
 
+// tau_k of every problem and iteration (index contract, counter word 3 = p)
+// and 1/||a||^2 at the drawn rows: drawn once at setup, replayed by the
+// forward, the recomputation and the reverse sweep.
+__global__ void unrolled_presample_kernel(UnrolledArgs a) {
+  const int npairs = (a.eta + 1) >> 1;
+  const int64_t per_p = (int64_t)a.K * npairs;
+  const int64_t total = per_p * a.P;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / per_p);
+    const int64_t r = e - (int64_t)p * per_p;
+    const int k = (int)(r / npairs);
+    const int q = (int)(r - (int64_t)k * npairs);
+    const int64_t ro = a.row_off[p];
+    int32_t i0, i1;
+    draw_pair(a.seed, k, (uint32_t)q, (uint32_t)p, a.thr + ro, a.alias + ro, (uint32_t)a.m[p], &i0,
+              &i1);
+    const int64_t base = ((int64_t)p * a.K + k) * a.eta;
+    a.tidx[base + 2 * q] = i0;
+    a.tiv[base + 2 * q] = a.inv_nu[ro + i0];
+    if (2 * q + 1 < a.eta) {
+      a.tidx[base + 2 * q + 1] = i1;
+      a.tiv[base + 2 * q + 1] = a.inv_nu[ro + i1];
+    }
+  }
+}
+
+// b at tau_k for the b of this forward.
+__global__ void unrolled_gather_b_kernel(UnrolledArgs a) {
+  const int64_t per_p = (int64_t)a.K * a.eta;
+  const int64_t total = per_p * a.P;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / per_p);
+    a.tb[e] = a.b[a.b_off[p] + a.tidx[e]];
+  }
+}
+
 __global__ void unrolled_norms_kernel(UnrolledArgs a, double* nu, float* inv_nu, int* pstat) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -459,6 +500,470 @@ __global__ void unrolled_alias_kernel(UnrolledArgs a, const double* nu, double* 
   vose_sequential<int32_t>(q + ro, stk + ro, m, thr + ro, alias + ro);
 }
 
+// ---------------------------------------------------------------------------
+// Row form (n <= 1024, eta <= 256): every row is consumed whole by one warp.
+// Warp w takes rows s = w, w + 8, ... of each tau_k; lane l owns float4
+// columns l + 32 j of x (and g in the adjoint) and of its share of the update
+// in registers, and streams its own columns of its rows into its warp's slot
+// ring with 16-byte cp.async (it reads back only what it copied, so the ring
+// needs no barrier).  The dots are warp shuffles; the warps' shares of the
+// update meet in shared memory once per iteration (two barriers).  tau_k, b
+// and 1/||a||^2 come from arrays filled once (tau) and per forward (b); the
+// next iteration's entries are loaded during the current one.
+// ---------------------------------------------------------------------------
+constexpr int RW_ETA = 256;                              // largest eta of the row form
+constexpr int RW_N4 = 256;                               // largest n/4 of the row form
+constexpr size_t RW_VEC = (size_t)RW_N4 * 16;            // bytes of one vector
+constexpr size_t RW_RING = 22 * 1024;                    // row slots of one warp
+constexpr size_t RW_SMEM = 4 * RW_VEC + UW * RW_RING;    // z, x, update, g, rings
+constexpr int RW_RS_MAX = 8;
+
+struct RowIdx {
+  int32_t idx[2][RW_ETA];
+  float b[2][RW_ETA];
+  float iv[2][RW_ETA];
+};
+
+__device__ __forceinline__ void ucp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void ucp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void ucp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void ucp_wait_pending(int pending) {
+  switch (pending) {
+#define RSKA_UWG(N) \
+  case N:           \
+    asm volatile("cp.async.wait_group " #N ";" ::: "memory"); \
+    break;
+    RSKA_UWG(0) RSKA_UWG(1) RSKA_UWG(2) RSKA_UWG(3) RSKA_UWG(4) RSKA_UWG(5) RSKA_UWG(6)
+    RSKA_UWG(7)
+#undef RSKA_UWG
+    default:
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      break;
+  }
+}
+
+// Entries (index, b, 1/||a||^2) of iteration k of problem p, one per thread.
+__device__ __forceinline__ void fetch_entry(const UnrolledArgs& a, int p, int k, int32_t& idx,
+                                            float& bv, float& iv) {
+  const int s = threadIdx.x;
+  if (s < a.eta) {
+    const int64_t e = ((int64_t)p * a.K + k) * a.eta + s;
+    idx = __ldg(a.tidx + e);
+    bv = __ldg(a.tb + e);
+    iv = __ldg(a.tiv + e);
+  }
+}
+
+__device__ __forceinline__ void put_entry(const UnrolledArgs& a, RowIdx& I, int buf, int32_t idx,
+                                          float bv, float iv) {
+  const int s = threadIdx.x;
+  if (s < a.eta) {
+    I.idx[buf][s] = idx;
+    I.b[buf][s] = bv;
+    I.iv[buf][s] = iv;
+  }
+}
+
+// The rows of one warp in processing order, streamed through its ring.
+struct WarpRows {
+  unsigned char* ring;
+  uint32_t slot_bytes;
+  int RS, cw, count;
+  int iq, ii, islot, cslot;   // next row to issue (iteration position, row), slots
+  int allowed;                // iterations whose entries are visible in I
+  int64_t issued, t;          // rows issued / consumed by this lane
+
+  template <int NZ>
+  __device__ __forceinline__ bool issue(const ProbCtx& c, const RowIdx& I, int lane, int warp) {
+    if (cw == 0 || iq >= count || iq > allowed) return false;
+    const int32_t row = I.idx[iq & 1][warp + UW * ii];
+    const float4* src = reinterpret_cast<const float4*>(c.Ap + (int64_t)row * c.lda);
+    float4* dst = reinterpret_cast<float4*>(ring + (size_t)islot * slot_bytes);
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+      const int col = lane + 32 * j;
+      if (col < c.n4) ucp_async16(dst + col, src + col);
+    }
+    ucp_commit();
+    ++issued;
+    islot = (islot + 1 == RS) ? 0 : islot + 1;
+    if (++ii == cw) {
+      ii = 0;
+      ++iq;
+    }
+    return true;
+  }
+
+  // make row t resident for this lane and return its slot
+  template <int NZ>
+  __device__ __forceinline__ const float4* next(const ProbCtx& c, const RowIdx& I, int lane,
+                                                int warp) {
+    while (issued <= t && issue<NZ>(c, I, lane, warp)) {
+    }
+    while (issued < t + RS && issue<NZ>(c, I, lane, warp)) {
+    }
+    const int64_t pend = issued - t - 1;
+    ucp_wait_pending(pend < 7 ? (int)pend : 7);
+    return reinterpret_cast<const float4*>(ring + (size_t)cslot * slot_bytes);
+  }
+
+  __device__ __forceinline__ void advance() {
+    ++t;
+    cslot = (cslot + 1 == RS) ? 0 : cslot + 1;
+  }
+};
+
+template <int NZ>
+__device__ __forceinline__ WarpRows make_rows(const UnrolledArgs& a, const ProbCtx& c,
+                                              unsigned char* ring, int count, int warp) {
+  WarpRows w;
+  w.ring = ring;
+  w.slot_bytes = (uint32_t)c.n4 * 16u;
+  w.RS = min(RW_RS_MAX, (int)(RW_RING / w.slot_bytes));
+  w.cw = (a.eta > warp) ? (a.eta - warp + UW - 1) / UW : 0;
+  w.count = count;
+  w.iq = w.ii = w.islot = w.cslot = 0;
+  w.allowed = 0;
+  w.issued = w.t = 0;
+  return w;
+}
+
+// `count` forward iterations k_begin .. k_begin+count-1 of problem p.  On
+// entry zsh/xsh hold z and x = S(z), dsh is zero and I buffer 0 holds the
+// entries of iteration k_begin (all visible to every thread).  After local
+// step j, z is stored at store_base + ((j+1)/store_every) x_stride when
+// store_every divides j+1.  On exit zsh/xsh hold the last iterate.
+template <int NZ>
+__device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, RowIdx& I,
+                             float4* zsh, float4* xsh, float4* dsh, unsigned char* ring,
+                             int k_begin, int count, float* store_base, int store_every) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n4 = (int)c.n4;
+  WarpRows W = make_rows<NZ>(a, c, ring, count, warp);
+  float4 xr[NZ], dl[NZ];
+#pragma unroll
+  for (int j = 0; j < NZ; ++j) {
+    const int col = lane + 32 * j;
+    xr[j] = (col < n4) ? xsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+    dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  while (W.issued < W.RS && W.issue<NZ>(c, I, lane, warp)) {
+  }
+  for (int q = 0; q < count; ++q) {
+    const int buf = q & 1;
+    int32_t nidx = 0;
+    float nb = 0.f, niv = 0.f;
+    if (q + 1 < count) fetch_entry(a, p, k_begin + q + 1, nidx, nb, niv);
+    for (int i = 0; i < W.cw; ++i) {
+      const float4* rowp = W.next<NZ>(c, I, lane, warp);
+      const int s = warp + UW * i;
+      float dp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        const int col = lane + 32 * j;
+        if (col < n4) {
+          float4 v = rowp[col];
+          if (col == n4 - 1) v = mask_tail(v, col, c.n);
+          dp[j & 3] = fmaf(v.x, xr[j].x, dp[j & 3]);
+          dp[j & 3] = fmaf(v.y, xr[j].y, dp[j & 3]);
+          dp[j & 3] = fmaf(v.z, xr[j].z, dp[j & 3]);
+          dp[j & 3] = fmaf(v.w, xr[j].w, dp[j & 3]);
+        }
+      }
+      float d = (dp[0] + dp[1]) + (dp[2] + dp[3]);
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      const float cval = c.coef * ((d - I.b[buf][s]) * I.iv[buf][s]);
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        const int col = lane + 32 * j;
+        if (col < n4) {
+          float4 v = rowp[col];
+          if (col == n4 - 1) v = mask_tail(v, col, c.n);
+          dl[j].x = fmaf(cval, v.x, dl[j].x);
+          dl[j].y = fmaf(cval, v.y, dl[j].y);
+          dl[j].z = fmaf(cval, v.z, dl[j].z);
+          dl[j].w = fmaf(cval, v.w, dl[j].w);
+        }
+      }
+      W.advance();
+    }
+    if (q + 1 < count) put_entry(a, I, buf ^ 1, nidx, nb, niv);
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+      const int col = lane + 32 * j;
+      if (col < n4) {
+        float* dp = reinterpret_cast<float*>(dsh + col);
+        atomicAdd(dp + 0, dl[j].x);
+        atomicAdd(dp + 1, dl[j].y);
+        atomicAdd(dp + 2, dl[j].z);
+        atomicAdd(dp + 3, dl[j].w);
+      }
+      dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    // the next iteration's entries are visible: start its first rows now
+    W.allowed = q + 1;
+    while (W.issued < W.t + W.RS && W.issue<NZ>(c, I, lane, warp)) {
+    }
+    const bool store = ((q + 1) % store_every) == 0;
+    float4* dst = reinterpret_cast<float4*>(store_base + (size_t)((q + 1) / store_every) * a.x_stride);
+    for (int c4 = tid; c4 < n4; c4 += UT) {
+      float4 zv = zsh[c4];
+      const float4 dv = dsh[c4];
+      zv.x -= dv.x;
+      zv.y -= dv.y;
+      zv.z -= dv.z;
+      zv.w -= dv.w;
+      zv = mask_tail(zv, c4, c.n);
+      zsh[c4] = zv;
+      xsh[c4] = soft_shrink4(zv, c.lam);
+      dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (store) dst[c4] = zv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+      const int col = lane + 32 * j;
+      xr[j] = (col < n4) ? xsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  ucp_wait_all();
+}
+
+template <int NZ>
+__global__ void __launch_bounds__(UT, 1) unrolled_fwd_rows_kernel(UnrolledArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ RowIdx I;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  float4* zsh = reinterpret_cast<float4*>(smem);
+  float4* xsh = zsh + RW_N4;
+  float4* dsh = xsh + RW_N4;
+  unsigned char* ring = smem + 4 * RW_VEC + (size_t)warp * RW_RING;
+  const int nck = a.K / a.ckpt;
+  for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
+    const ProbCtx c = prob_ctx(a, p);
+    const int n4 = (int)c.n4;
+    float* ck = a.ckpts + (size_t)p * (nck + 1) * a.x_stride;
+    for (int c4 = tid; c4 < n4; c4 += UT) {
+      zsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      xsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      reinterpret_cast<float4*>(ck)[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    {
+      int32_t idx = 0;
+      float bv = 0.f, iv = 0.f;
+      fetch_entry(a, p, 0, idx, bv, iv);
+      put_entry(a, I, 0, idx, bv, iv);
+    }
+    __syncthreads();
+    forward_rows<NZ>(a, c, p, I, zsh, xsh, dsh, ring, 0, a.K, ck, a.ckpt);
+    float4* xo = reinterpret_cast<float4*>(a.x_out + a.x_off[p]);
+    for (int c4 = tid; c4 < n4; c4 += UT) xo[c4] = xsh[c4];
+    __syncthreads();
+  }
+}
+
+// Reverse sweep over one checkpoint segment: iterations k = k0+cnt-1 down to
+// k0.  On entry zsh/xsh hold z_{k0+cnt-1} and its shrink, gsh holds
+// g = dL/dz_{k0+cnt}, dsh is zero, I buffer 0 holds iteration k0+cnt-1's
+// entries.  seg[j] holds z_{k0+j}.  On exit gsh holds dL/dz_{k0}.
+template <int NZ>
+__device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, RowIdx& I,
+                              float4* zsh, float4* xsh, float4* dsh, float4* gsh,
+                              unsigned char* ring, int k0, int cnt, const float* seg, float* gbp,
+                              float& glam, float& gt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n4 = (int)c.n4;
+  WarpRows W = make_rows<NZ>(a, c, ring, cnt, warp);
+  while (W.issued < W.RS && W.issue<NZ>(c, I, lane, warp)) {
+  }
+  for (int q = 0; q < cnt; ++q) {
+    const int k = k0 + cnt - 1 - q;
+    const int buf = q & 1;
+    float4 xr[NZ], gr[NZ], xb[NZ];
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+      const int col = lane + 32 * j;
+      xr[j] = (col < n4) ? xsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+      gr[j] = (col < n4) ? gsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+      xb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    int32_t nidx = 0;
+    float nb = 0.f, niv = 0.f;
+    if (q + 1 < cnt) fetch_entry(a, p, k - 1, nidx, nb, niv);
+    for (int i = 0; i < W.cw; ++i) {
+      const float4* rowp = W.next<NZ>(c, I, lane, warp);
+      const int s = warp + UW * i;
+      float d1 = 0.f, d2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        const int col = lane + 32 * j;
+        if (col < n4) {
+          float4 v = rowp[col];
+          if (col == n4 - 1) v = mask_tail(v, col, c.n);
+          d1 += dot4(v, xr[j]);
+          d2 += dot4(v, gr[j]);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      }
+      const float rs = d1 - I.b[buf][s];
+      const float ivs = I.iv[buf][s];
+      const float us = c.coef * d2 * ivs;
+      if (lane == 0) {
+        atomicAdd(gbp + I.idx[buf][s], us);
+        gt -= rs * ivs * d2 / (float)a.eta;
+      }
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        const int col = lane + 32 * j;
+        if (col < n4) {
+          float4 v = rowp[col];
+          if (col == n4 - 1) v = mask_tail(v, col, c.n);
+          xb[j].x = fmaf(-us, v.x, xb[j].x);
+          xb[j].y = fmaf(-us, v.y, xb[j].y);
+          xb[j].z = fmaf(-us, v.z, xb[j].z);
+          xb[j].w = fmaf(-us, v.w, xb[j].w);
+        }
+      }
+      W.advance();
+    }
+    if (q + 1 < cnt) put_entry(a, I, buf ^ 1, nidx, nb, niv);
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) {
+      const int col = lane + 32 * j;
+      if (col < n4) {
+        float* dp = reinterpret_cast<float*>(dsh + col);
+        atomicAdd(dp + 0, xb[j].x);
+        atomicAdd(dp + 1, xb[j].y);
+        atomicAdd(dp + 2, xb[j].z);
+        atomicAdd(dp + 3, xb[j].w);
+      }
+    }
+    __syncthreads();
+    W.allowed = q + 1;
+    while (W.issued < W.t + W.RS && W.issue<NZ>(c, I, lane, warp)) {
+    }
+    // dL/dlambda and dL/dz_k = g + mask_k xbar; then z_{k-1} for the next step
+    const float4* zprev = reinterpret_cast<const float4*>(seg + (size_t)(k - 1 - k0) * a.x_stride);
+    for (int c4 = tid; c4 < n4; c4 += UT) {
+      const float4 xv = mask_tail(dsh[c4], c4, c.n);
+      const float4 zv = zsh[c4];
+      const float sx = neg_sign_mask(zv.x, c.lam), sy = neg_sign_mask(zv.y, c.lam);
+      const float sz = neg_sign_mask(zv.z, c.lam), sw = neg_sign_mask(zv.w, c.lam);
+      glam += xv.x * sx + xv.y * sy + xv.z * sz + xv.w * sw;
+      float4 g = gsh[c4];
+      if (sx != 0.f) g.x += xv.x;
+      if (sy != 0.f) g.y += xv.y;
+      if (sz != 0.f) g.z += xv.z;
+      if (sw != 0.f) g.w += xv.w;
+      gsh[c4] = g;
+      dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q + 1 < cnt) {
+        const float4 zp = __ldcg(zprev + c4);
+        zsh[c4] = zp;
+        xsh[c4] = soft_shrink4(zp, c.lam);
+      }
+    }
+    __syncthreads();
+  }
+  ucp_wait_all();
+}
+
+template <int NZ>
+__global__ void __launch_bounds__(UT, 1) unrolled_bwd_rows_kernel(UnrolledArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ RowIdx I;
+  __shared__ float sfin[2][UW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4* zsh = reinterpret_cast<float4*>(smem);
+  float4* xsh = zsh + RW_N4;
+  float4* dsh = xsh + RW_N4;
+  float4* gsh = dsh + RW_N4;
+  unsigned char* ring = smem + 4 * RW_VEC + (size_t)warp * RW_RING;
+  const int nck = a.K / a.ckpt;
+  for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
+    const ProbCtx c = prob_ctx(a, p);
+    const int n4 = (int)c.n4;
+    const float* ck = a.ckpts + (size_t)p * (nck + 1) * a.x_stride;
+    float* seg = a.segbuf + (size_t)p * a.ckpt * a.x_stride;
+    float* gbp = a.gb + a.b_off[p];
+    const float4* gxp = reinterpret_cast<const float4*>(a.gx + a.x_off[p]);
+    float glam = 0.f, gt = 0.f;
+    // g = dL/dz_K = mask_K dL/dx_K
+    const float4* zK = reinterpret_cast<const float4*>(ck + (size_t)nck * a.x_stride);
+    for (int c4 = tid; c4 < n4; c4 += UT) {
+      const float4 zv = __ldcg(zK + c4);
+      const float4 gxv = mask_tail(__ldg(gxp + c4), c4, c.n);
+      const float sx = neg_sign_mask(zv.x, c.lam), sy = neg_sign_mask(zv.y, c.lam);
+      const float sz = neg_sign_mask(zv.z, c.lam), sw = neg_sign_mask(zv.w, c.lam);
+      glam += gxv.x * sx + gxv.y * sy + gxv.z * sz + gxv.w * sw;
+      gsh[c4] = make_float4(sx != 0.f ? gxv.x : 0.f, sy != 0.f ? gxv.y : 0.f,
+                            sz != 0.f ? gxv.z : 0.f, sw != 0.f ? gxv.w : 0.f);
+    }
+    for (int sgi = nck - 1; sgi >= 0; --sgi) {
+      const int k0 = sgi * a.ckpt;
+      // recompute z_{k0} .. z_{k0+ckpt-1} into seg
+      const float4* zk0 = reinterpret_cast<const float4*>(ck + (size_t)sgi * a.x_stride);
+      for (int c4 = tid; c4 < n4; c4 += UT) {
+        const float4 zv = __ldcg(zk0 + c4);
+        zsh[c4] = zv;
+        xsh[c4] = soft_shrink4(zv, c.lam);
+        dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4*>(seg)[c4] = zv;
+      }
+      {
+        int32_t idx = 0;
+        float bv = 0.f, iv = 0.f;
+        fetch_entry(a, p, k0, idx, bv, iv);
+        put_entry(a, I, 0, idx, bv, iv);
+      }
+      __syncthreads();
+      forward_rows<NZ>(a, c, p, I, zsh, xsh, dsh, ring, k0, a.ckpt - 1, seg, 1);
+      // reverse sweep (zsh/xsh hold z_{k0+ckpt-1})
+      {
+        int32_t idx = 0;
+        float bv = 0.f, iv = 0.f;
+        fetch_entry(a, p, k0 + a.ckpt - 1, idx, bv, iv);
+        put_entry(a, I, 0, idx, bv, iv);
+      }
+      __syncthreads();
+      backward_rows<NZ>(a, c, p, I, zsh, xsh, dsh, gsh, ring, k0, a.ckpt, seg, gbp, glam, gt);
+    }
+    // reduce dL/dlambda over the CTA and dL/dt over the warps
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) glam += __shfl_xor_sync(0xffffffffu, glam, o);
+    if (lane == 0) {
+      sfin[0][warp] = glam;
+      sfin[1][warp] = gt;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float sl = 0.f, st = 0.f;
+      for (int w = 0; w < UW; ++w) {
+        sl += sfin[0][w];
+        st += sfin[1][w];
+      }
+      a.glam[p] = sl;
+      a.gt[p] = st;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 }  // namespace rska
 
@@ -481,6 +986,9 @@ struct rska_unrolled {
   uint32_t* thr = nullptr;
   int32_t* alias = nullptr;
   float *ckpts = nullptr, *segbuf = nullptr;
+  int row_nz = 0;               // row form: float4 columns per lane (0: column form)
+  int32_t* tidx = nullptr;      // row form: tau for every problem and iteration [P][K][eta]
+  float *tiv = nullptr, *tb = nullptr;
   // inputs of the last forward, kept for the backward
   const float* b = nullptr;
   const float* lambda = nullptr;
@@ -491,8 +999,9 @@ struct rska_unrolled {
 namespace {
 
 void unrolled_free(rska_unrolled* u) {
-  void* ptrs[] = {u->a_off, u->lda,   u->b_off, u->row_off, u->x_off,  u->m,     u->n,
-                  u->nu,    u->inv_nu, u->thr,  u->alias,   u->ckpts, u->segbuf};
+  void* ptrs[] = {u->a_off, u->lda,    u->b_off, u->row_off, u->x_off,  u->m,   u->n,
+                  u->nu,    u->inv_nu, u->thr,   u->alias,   u->ckpts,  u->segbuf,
+                  u->tidx,  u->tiv,    u->tb};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -526,7 +1035,19 @@ UnrolledArgs uargs(rska_unrolled* u) {
   a.ckpts = u->ckpts;
   a.segbuf = u->segbuf;
   a.x_stride = u->x_stride;
+  a.tidx = u->tidx;
+  a.tiv = u->tiv;
+  a.tb = u->tb;
   return a;
+}
+
+// One CTA per problem with the row form's shared memory.
+template <typename K>
+cudaError_t launch_rows(K kernel, rska_unrolled* u, const UnrolledArgs& a, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kernel<<<u->P, rska::UT, smem, u->stream>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -577,6 +1098,11 @@ int rska_unrolled_setup(rska_unrolled** out, int32_t P, const float* A, const in
   {
     const int64_t zr = (maxn4 + rska::UT - 1) / rska::UT;
     u->zreg = zr <= 1 ? 1 : (zr <= 2 ? 2 : 4);
+    // row form for n <= 1024 and eta <= 256: float4 columns per lane
+    if (maxn4 <= rska::RW_N4 && eta <= rska::RW_ETA) {
+      const int64_t nz = (maxn4 + 31) / 32;
+      u->row_nz = nz <= 1 ? 1 : (nz <= 2 ? 2 : (nz <= 4 ? 4 : 8));
+    }
   }
   u->h_x_off = x_off;
   int dev = 0;
@@ -595,6 +1121,9 @@ int rska_unrolled_setup(rska_unrolled** out, int32_t P, const float* A, const in
        (e = dalloc(&u->alias, rows)) != cudaSuccess ||
        (e = dalloc(&u->ckpts, (size_t)P * (nck + 1) * u->x_stride)) != cudaSuccess ||
        (e = dalloc(&u->segbuf, (size_t)P * ckpt_every * u->x_stride)) != cudaSuccess ||
+       (u->row_nz && ((e = dalloc(&u->tidx, (size_t)P * K * eta)) != cudaSuccess ||
+                      (e = dalloc(&u->tiv, (size_t)P * K * eta)) != cudaSuccess ||
+                      (e = dalloc(&u->tb, (size_t)P * K * eta)) != cudaSuccess)) ||
        (e = dalloc(&q, rows)) != cudaSuccess || (e = dalloc(&stk, rows)) != cudaSuccess ||
        (e = dalloc(&pstat, P)) != cudaSuccess)) {
   }
@@ -615,6 +1144,10 @@ int rska_unrolled_setup(rska_unrolled** out, int32_t P, const float* A, const in
     if (e == cudaSuccess) {
       rska::unrolled_alias_kernel<<<(P + 63) / 64, 64, 0, s>>>(a, u->nu, q, stk, u->thr, u->alias,
                                                                pstat);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && u->row_nz) {
+      rska::unrolled_presample_kernel<<<u->num_sms * 8, 256, 0, s>>>(a);
       e = cudaGetLastError();
     }
   }
@@ -647,14 +1180,26 @@ int rska_unrolled_forward(rska_unrolled* u, const float* b, const float* lambda,
   u->t = t;
   UnrolledArgs a = uargs(u);
   a.x_out = x_out;
-  const int z = u->zreg;
-  if (z == 1)
-    rska::unrolled_forward_kernel<1><<<u->P, rska::UT, 0, u->stream>>>(a);
-  else if (z == 2)
-    rska::unrolled_forward_kernel<2><<<u->P, rska::UT, 0, u->stream>>>(a);
-  else
-    rska::unrolled_forward_kernel<4><<<u->P, rska::UT, 0, u->stream>>>(a);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (u->row_nz) {
+    rska::unrolled_gather_b_kernel<<<u->num_sms * 8, 256, 0, u->stream>>>(a);
+    const size_t sm = rska::RW_SMEM;
+    switch (u->row_nz) {
+      case 1: e = launch_rows(rska::unrolled_fwd_rows_kernel<1>, u, a, sm); break;
+      case 2: e = launch_rows(rska::unrolled_fwd_rows_kernel<2>, u, a, sm); break;
+      case 4: e = launch_rows(rska::unrolled_fwd_rows_kernel<4>, u, a, sm); break;
+      default: e = launch_rows(rska::unrolled_fwd_rows_kernel<8>, u, a, sm); break;
+    }
+  } else {
+    const int z = u->zreg;
+    if (z == 1)
+      rska::unrolled_forward_kernel<1><<<u->P, rska::UT, 0, u->stream>>>(a);
+    else if (z == 2)
+      rska::unrolled_forward_kernel<2><<<u->P, rska::UT, 0, u->stream>>>(a);
+    else
+      rska::unrolled_forward_kernel<4><<<u->P, rska::UT, 0, u->stream>>>(a);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return RSKA_ECUDA;
   u->have_forward = true;
   return RSKA_OK;
@@ -669,7 +1214,16 @@ int rska_unrolled_backward(rska_unrolled* u, const float* gx, float* gb, float* 
   a.glam = glam;
   a.gt = gt;
   cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(float) * u->b_total, u->stream);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && u->row_nz) {
+    const size_t sm = rska::RW_SMEM;
+    switch (u->row_nz) {
+      case 1: e = launch_rows(rska::unrolled_bwd_rows_kernel<1>, u, a, sm); break;
+      case 2: e = launch_rows(rska::unrolled_bwd_rows_kernel<2>, u, a, sm); break;
+      case 4: e = launch_rows(rska::unrolled_bwd_rows_kernel<4>, u, a, sm); break;
+      default: e = launch_rows(rska::unrolled_bwd_rows_kernel<8>, u, a, sm); break;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+  } else if (e == cudaSuccess) {
     const int z = u->zreg;
     if (z == 1)
       rska::unrolled_backward_kernel<1><<<u->P, rska::UT, 0, u->stream>>>(a);
