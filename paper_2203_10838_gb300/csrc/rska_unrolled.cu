@@ -515,7 +515,7 @@ constexpr int RW_ETA = 256;                              // largest eta of the r
 constexpr int RW_N4 = 256;                               // largest n/4 of the row form
 constexpr size_t RW_VEC = (size_t)RW_N4 * 16;            // bytes of one vector
 constexpr size_t RW_RING = 22 * 1024;                    // row slots of one warp
-constexpr size_t RW_SMEM = 4 * RW_VEC + UW * RW_RING;    // z, x, update, g, rings
+constexpr size_t RW_SMEM = 5 * RW_VEC + UW * RW_RING;    // z, x, two update buffers, g, rings
 constexpr int RW_RS_MAX = 8;
 
 struct RowIdx {
@@ -550,6 +550,38 @@ __device__ __forceinline__ void ucp_wait_pending(int pending) {
   }
 }
 
+// Barrier over the CTAs of the cluster (release/acquire: shared-memory writes
+// before it are visible to the peer CTA after it); a CTA barrier when CL = 1.
+template <int CL>
+__device__ __forceinline__ void cl_sync() {
+  if constexpr (CL == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+  }
+}
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// The same shared-memory float4 in CTA `peer` of the cluster.
+__device__ __forceinline__ float4 ld_peer(const float4* p, uint32_t peer) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(ra)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(peer));
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(ra)
+               : "memory");
+  return v;
+}
+
 // Entries (index, b, 1/||a||^2) of iteration k of problem p, one per thread.
 __device__ __forceinline__ void fetch_entry(const UnrolledArgs& a, int p, int k, int32_t& idx,
                                             float& bv, float& iv) {
@@ -577,6 +609,7 @@ struct WarpRows {
   unsigned char* ring;
   uint32_t slot_bytes;
   int RS, cw, count;
+  int s0, ss;                 // rows s0, s0 + ss, ... of every tau_k
   int iq, ii, islot, cslot;   // next row to issue (iteration position, row), slots
   int allowed;                // iterations whose entries are visible in I
   int64_t issued, t;          // rows issued / consumed by this lane
@@ -584,7 +617,7 @@ struct WarpRows {
   template <int NZ>
   __device__ __forceinline__ bool issue(const ProbCtx& c, const RowIdx& I, int lane, int warp) {
     if (cw == 0 || iq >= count || iq > allowed) return false;
-    const int32_t row = I.idx[iq & 1][warp + UW * ii];
+    const int32_t row = I.idx[iq & 1][s0 + ss * ii];
     const float4* src = reinterpret_cast<const float4*>(c.Ap + (int64_t)row * c.lda);
     float4* dst = reinterpret_cast<float4*>(ring + (size_t)islot * slot_bytes);
 #pragma unroll
@@ -621,14 +654,18 @@ struct WarpRows {
   }
 };
 
-template <int NZ>
+// Warp w of cluster rank r takes rows s = r UW + w + (UW CL) i.
+template <int NZ, int CL>
 __device__ __forceinline__ WarpRows make_rows(const UnrolledArgs& a, const ProbCtx& c,
-                                              unsigned char* ring, int count, int warp) {
+                                              unsigned char* ring, int count, int warp,
+                                              int rank) {
   WarpRows w;
   w.ring = ring;
   w.slot_bytes = (uint32_t)c.n4 * 16u;
   w.RS = min(RW_RS_MAX, (int)(RW_RING / w.slot_bytes));
-  w.cw = (a.eta > warp) ? (a.eta - warp + UW - 1) / UW : 0;
+  w.s0 = rank * UW + warp;
+  w.ss = UW * CL;
+  w.cw = (a.eta > w.s0) ? (a.eta - w.s0 + w.ss - 1) / w.ss : 0;
   w.count = count;
   w.iq = w.ii = w.islot = w.cslot = 0;
   w.allowed = 0;
@@ -637,17 +674,22 @@ __device__ __forceinline__ WarpRows make_rows(const UnrolledArgs& a, const ProbC
 }
 
 // `count` forward iterations k_begin .. k_begin+count-1 of problem p.  On
-// entry zsh/xsh hold z and x = S(z), dsh is zero and I buffer 0 holds the
-// entries of iteration k_begin (all visible to every thread).  After local
-// step j, z is stored at store_base + ((j+1)/store_every) x_stride when
-// store_every divides j+1.  On exit zsh/xsh hold the last iterate.
-template <int NZ>
+// entry zsh/xsh hold z and x = S(z), both update buffers (dsh, dsh + RW_N4)
+// are zero and I buffer 0 holds the entries of iteration k_begin, all visible
+// to every thread of the cluster.  With CL = 2 the two CTAs of a cluster take
+// alternate blocks of 8 rows and add their update shares through
+// distributed shared memory; both keep identical z and x.  After local step
+// j, z is stored (when `store`) at store_base + ((j+1)/store_every) x_stride
+// if store_every divides j+1.  On exit zsh/xsh hold the last iterate and the
+// update buffer of the last step is not zero.
+template <int NZ, int CL>
 __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, RowIdx& I,
                              float4* zsh, float4* xsh, float4* dsh, unsigned char* ring,
-                             int k_begin, int count, float* store_base, int store_every) {
+                             int k_begin, int count, float* store_base, int store_every,
+                             bool store, int rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n4 = (int)c.n4;
-  WarpRows W = make_rows<NZ>(a, c, ring, count, warp);
+  WarpRows W = make_rows<NZ, CL>(a, c, ring, count, warp, rank);
   float4 xr[NZ], dl[NZ];
 #pragma unroll
   for (int j = 0; j < NZ; ++j) {
@@ -664,7 +706,7 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
     if (q + 1 < count) fetch_entry(a, p, k_begin + q + 1, nidx, nb, niv);
     for (int i = 0; i < W.cw; ++i) {
       const float4* rowp = W.next<NZ>(c, I, lane, warp);
-      const int s = warp + UW * i;
+      const int s = W.s0 + W.ss * i;
       float dp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
@@ -697,11 +739,13 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       W.advance();
     }
     if (q + 1 < count) put_entry(a, I, buf ^ 1, nidx, nb, niv);
+    float4* dcur = dsh + (size_t)buf * RW_N4;   // this step's update buffer
+    float4* dnext = dsh + (size_t)(buf ^ 1) * RW_N4;
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
       const int col = lane + 32 * j;
       if (col < n4) {
-        float* dp = reinterpret_cast<float*>(dsh + col);
+        float* dp = reinterpret_cast<float*>(dcur + col);
         atomicAdd(dp + 0, dl[j].x);
         atomicAdd(dp + 1, dl[j].y);
         atomicAdd(dp + 2, dl[j].z);
@@ -709,16 +753,23 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       }
       dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
+    cl_sync<CL>();
     // the next iteration's entries are visible: start its first rows now
     W.allowed = q + 1;
     while (W.issued < W.t + W.RS && W.issue<NZ>(c, I, lane, warp)) {
     }
-    const bool store = ((q + 1) % store_every) == 0;
+    const bool st = store && ((q + 1) % store_every) == 0;
     float4* dst = reinterpret_cast<float4*>(store_base + (size_t)((q + 1) / store_every) * a.x_stride);
     for (int c4 = tid; c4 < n4; c4 += UT) {
       float4 zv = zsh[c4];
-      const float4 dv = dsh[c4];
+      float4 dv = dcur[c4];
+      if constexpr (CL == 2) {
+        const float4 pv = ld_peer(dcur + c4, (uint32_t)(rank ^ 1));
+        dv.x += pv.x;
+        dv.y += pv.y;
+        dv.z += pv.z;
+        dv.w += pv.w;
+      }
       zv.x -= dv.x;
       zv.y -= dv.y;
       zv.z -= dv.z;
@@ -726,10 +777,10 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       zv = mask_tail(zv, c4, c.n);
       zsh[c4] = zv;
       xsh[c4] = soft_shrink4(zv, c.lam);
-      dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (store) dst[c4] = zv;
+      dnext[c4] = make_float4(0.f, 0.f, 0.f, 0.f);  // read by the peer one step ago
+      if (st) dst[c4] = zv;
     }
-    __syncthreads();
+    cl_sync<CL>();
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
       const int col = lane + 32 * j;
@@ -739,17 +790,18 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
   ucp_wait_all();
 }
 
-template <int NZ>
+template <int NZ, int CL>
 __global__ void __launch_bounds__(UT, 1) unrolled_fwd_rows_kernel(UnrolledArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ RowIdx I;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int rank = (CL == 1) ? 0 : (int)cl_rank();
   float4* zsh = reinterpret_cast<float4*>(smem);
   float4* xsh = zsh + RW_N4;
-  float4* dsh = xsh + RW_N4;
-  unsigned char* ring = smem + 4 * RW_VEC + (size_t)warp * RW_RING;
+  float4* dsh = xsh + RW_N4;  // two buffers
+  unsigned char* ring = smem + 5 * RW_VEC + (size_t)warp * RW_RING;
   const int nck = a.K / a.ckpt;
-  for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
+  for (int p = blockIdx.x / CL; p < a.P; p += gridDim.x / CL) {
     const ProbCtx c = prob_ctx(a, p);
     const int n4 = (int)c.n4;
     float* ck = a.ckpts + (size_t)p * (nck + 1) * a.x_stride;
@@ -757,7 +809,8 @@ __global__ void __launch_bounds__(UT, 1) unrolled_fwd_rows_kernel(UnrolledArgs a
       zsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
       xsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
       dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
-      reinterpret_cast<float4*>(ck)[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      dsh[RW_N4 + c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rank == 0) reinterpret_cast<float4*>(ck)[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     {
       int32_t idx = 0;
@@ -765,11 +818,13 @@ __global__ void __launch_bounds__(UT, 1) unrolled_fwd_rows_kernel(UnrolledArgs a
       fetch_entry(a, p, 0, idx, bv, iv);
       put_entry(a, I, 0, idx, bv, iv);
     }
-    __syncthreads();
-    forward_rows<NZ>(a, c, p, I, zsh, xsh, dsh, ring, 0, a.K, ck, a.ckpt);
-    float4* xo = reinterpret_cast<float4*>(a.x_out + a.x_off[p]);
-    for (int c4 = tid; c4 < n4; c4 += UT) xo[c4] = xsh[c4];
-    __syncthreads();
+    cl_sync<CL>();
+    forward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, ring, 0, a.K, ck, a.ckpt, rank == 0, rank);
+    if (rank == 0) {
+      float4* xo = reinterpret_cast<float4*>(a.x_out + a.x_off[p]);
+      for (int c4 = tid; c4 < n4; c4 += UT) xo[c4] = xsh[c4];
+    }
+    cl_sync<CL>();
   }
 }
 
@@ -777,14 +832,14 @@ __global__ void __launch_bounds__(UT, 1) unrolled_fwd_rows_kernel(UnrolledArgs a
 // k0.  On entry zsh/xsh hold z_{k0+cnt-1} and its shrink, gsh holds
 // g = dL/dz_{k0+cnt}, dsh is zero, I buffer 0 holds iteration k0+cnt-1's
 // entries.  seg[j] holds z_{k0+j}.  On exit gsh holds dL/dz_{k0}.
-template <int NZ>
+template <int NZ, int CL>
 __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, RowIdx& I,
                               float4* zsh, float4* xsh, float4* dsh, float4* gsh,
                               unsigned char* ring, int k0, int cnt, const float* seg, float* gbp,
-                              float& glam, float& gt) {
+                              float& glam, float& gt, int rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n4 = (int)c.n4;
-  WarpRows W = make_rows<NZ>(a, c, ring, cnt, warp);
+  WarpRows W = make_rows<NZ, CL>(a, c, ring, cnt, warp, rank);
   while (W.issued < W.RS && W.issue<NZ>(c, I, lane, warp)) {
   }
   for (int q = 0; q < cnt; ++q) {
@@ -803,7 +858,7 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
     if (q + 1 < cnt) fetch_entry(a, p, k - 1, nidx, nb, niv);
     for (int i = 0; i < W.cw; ++i) {
       const float4* rowp = W.next<NZ>(c, I, lane, warp);
-      const int s = warp + UW * i;
+      const int s = W.s0 + W.ss * i;
       float d1 = 0.f, d2 = 0.f;
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
@@ -842,87 +897,100 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       W.advance();
     }
     if (q + 1 < cnt) put_entry(a, I, buf ^ 1, nidx, nb, niv);
+    float4* dcur = dsh + (size_t)buf * RW_N4;
+    float4* dnext = dsh + (size_t)(buf ^ 1) * RW_N4;
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
       const int col = lane + 32 * j;
       if (col < n4) {
-        float* dp = reinterpret_cast<float*>(dsh + col);
+        float* dp = reinterpret_cast<float*>(dcur + col);
         atomicAdd(dp + 0, xb[j].x);
         atomicAdd(dp + 1, xb[j].y);
         atomicAdd(dp + 2, xb[j].z);
         atomicAdd(dp + 3, xb[j].w);
       }
     }
-    __syncthreads();
+    cl_sync<CL>();
     W.allowed = q + 1;
     while (W.issued < W.t + W.RS && W.issue<NZ>(c, I, lane, warp)) {
     }
     // dL/dlambda and dL/dz_k = g + mask_k xbar; then z_{k-1} for the next step
     const float4* zprev = reinterpret_cast<const float4*>(seg + (size_t)(k - 1 - k0) * a.x_stride);
     for (int c4 = tid; c4 < n4; c4 += UT) {
-      const float4 xv = mask_tail(dsh[c4], c4, c.n);
+      float4 dv = dcur[c4];
+      if constexpr (CL == 2) {
+        const float4 pv = ld_peer(dcur + c4, (uint32_t)(rank ^ 1));
+        dv.x += pv.x;
+        dv.y += pv.y;
+        dv.z += pv.z;
+        dv.w += pv.w;
+      }
+      const float4 xv = mask_tail(dv, c4, c.n);
       const float4 zv = zsh[c4];
       const float sx = neg_sign_mask(zv.x, c.lam), sy = neg_sign_mask(zv.y, c.lam);
       const float sz = neg_sign_mask(zv.z, c.lam), sw = neg_sign_mask(zv.w, c.lam);
-      glam += xv.x * sx + xv.y * sy + xv.z * sz + xv.w * sw;
+      if (rank == 0) glam += xv.x * sx + xv.y * sy + xv.z * sz + xv.w * sw;
       float4 g = gsh[c4];
       if (sx != 0.f) g.x += xv.x;
       if (sy != 0.f) g.y += xv.y;
       if (sz != 0.f) g.z += xv.z;
       if (sw != 0.f) g.w += xv.w;
       gsh[c4] = g;
-      dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      dnext[c4] = make_float4(0.f, 0.f, 0.f, 0.f);  // read by the peer one step ago
       if (q + 1 < cnt) {
         const float4 zp = __ldcg(zprev + c4);
         zsh[c4] = zp;
         xsh[c4] = soft_shrink4(zp, c.lam);
       }
     }
-    __syncthreads();
+    cl_sync<CL>();
   }
   ucp_wait_all();
 }
 
-template <int NZ>
+template <int NZ, int CL>
 __global__ void __launch_bounds__(UT, 1) unrolled_bwd_rows_kernel(UnrolledArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ RowIdx I;
   __shared__ float sfin[2][UW];
+  __shared__ float4 s_gt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rank = (CL == 1) ? 0 : (int)cl_rank();
   float4* zsh = reinterpret_cast<float4*>(smem);
   float4* xsh = zsh + RW_N4;
-  float4* dsh = xsh + RW_N4;
-  float4* gsh = dsh + RW_N4;
-  unsigned char* ring = smem + 4 * RW_VEC + (size_t)warp * RW_RING;
+  float4* dsh = xsh + RW_N4;       // two buffers
+  float4* gsh = dsh + 2 * RW_N4;
+  unsigned char* ring = smem + 5 * RW_VEC + (size_t)warp * RW_RING;
   const int nck = a.K / a.ckpt;
-  for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
+  for (int p = blockIdx.x / CL; p < a.P; p += gridDim.x / CL) {
     const ProbCtx c = prob_ctx(a, p);
     const int n4 = (int)c.n4;
     const float* ck = a.ckpts + (size_t)p * (nck + 1) * a.x_stride;
-    float* seg = a.segbuf + (size_t)p * a.ckpt * a.x_stride;
+    float* seg = a.segbuf + ((size_t)p * CL + rank) * a.ckpt * a.x_stride;  // this CTA's own
     float* gbp = a.gb + a.b_off[p];
     const float4* gxp = reinterpret_cast<const float4*>(a.gx + a.x_off[p]);
     float glam = 0.f, gt = 0.f;
-    // g = dL/dz_K = mask_K dL/dx_K
+    // g = dL/dz_K = mask_K dL/dx_K (both CTAs; dL/dlambda counted by rank 0)
     const float4* zK = reinterpret_cast<const float4*>(ck + (size_t)nck * a.x_stride);
     for (int c4 = tid; c4 < n4; c4 += UT) {
       const float4 zv = __ldcg(zK + c4);
       const float4 gxv = mask_tail(__ldg(gxp + c4), c4, c.n);
       const float sx = neg_sign_mask(zv.x, c.lam), sy = neg_sign_mask(zv.y, c.lam);
       const float sz = neg_sign_mask(zv.z, c.lam), sw = neg_sign_mask(zv.w, c.lam);
-      glam += gxv.x * sx + gxv.y * sy + gxv.z * sz + gxv.w * sw;
+      if (rank == 0) glam += gxv.x * sx + gxv.y * sy + gxv.z * sz + gxv.w * sw;
       gsh[c4] = make_float4(sx != 0.f ? gxv.x : 0.f, sy != 0.f ? gxv.y : 0.f,
                             sz != 0.f ? gxv.z : 0.f, sw != 0.f ? gxv.w : 0.f);
     }
     for (int sgi = nck - 1; sgi >= 0; --sgi) {
       const int k0 = sgi * a.ckpt;
-      // recompute z_{k0} .. z_{k0+ckpt-1} into seg
+      // recompute z_{k0} .. z_{k0+ckpt-1} into this CTA's segment buffer
       const float4* zk0 = reinterpret_cast<const float4*>(ck + (size_t)sgi * a.x_stride);
       for (int c4 = tid; c4 < n4; c4 += UT) {
         const float4 zv = __ldcg(zk0 + c4);
         zsh[c4] = zv;
         xsh[c4] = soft_shrink4(zv, c.lam);
         dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dsh[RW_N4 + c4] = make_float4(0.f, 0.f, 0.f, 0.f);
         reinterpret_cast<float4*>(seg)[c4] = zv;
       }
       {
@@ -931,8 +999,8 @@ __global__ void __launch_bounds__(UT, 1) unrolled_bwd_rows_kernel(UnrolledArgs a
         fetch_entry(a, p, k0, idx, bv, iv);
         put_entry(a, I, 0, idx, bv, iv);
       }
-      __syncthreads();
-      forward_rows<NZ>(a, c, p, I, zsh, xsh, dsh, ring, k0, a.ckpt - 1, seg, 1);
+      cl_sync<CL>();
+      forward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, ring, k0, a.ckpt - 1, seg, 1, true, rank);
       // reverse sweep (zsh/xsh hold z_{k0+ckpt-1})
       {
         int32_t idx = 0;
@@ -940,10 +1008,15 @@ __global__ void __launch_bounds__(UT, 1) unrolled_bwd_rows_kernel(UnrolledArgs a
         fetch_entry(a, p, k0 + a.ckpt - 1, idx, bv, iv);
         put_entry(a, I, 0, idx, bv, iv);
       }
-      __syncthreads();
-      backward_rows<NZ>(a, c, p, I, zsh, xsh, dsh, gsh, ring, k0, a.ckpt, seg, gbp, glam, gt);
+      for (int c4 = tid; c4 < n4; c4 += UT) {
+        dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dsh[RW_N4 + c4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      cl_sync<CL>();
+      backward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, gsh, ring, k0, a.ckpt, seg, gbp, glam, gt,
+                            rank);
     }
-    // reduce dL/dlambda over the CTA and dL/dt over the warps
+    // reduce dL/dlambda over the CTA and dL/dt over the warps and the cluster
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) glam += __shfl_xor_sync(0xffffffffu, glam, o);
     if (lane == 0) {
@@ -951,16 +1024,21 @@ __global__ void __launch_bounds__(UT, 1) unrolled_bwd_rows_kernel(UnrolledArgs a
       sfin[1][warp] = gt;
     }
     __syncthreads();
+    float sl = 0.f, st = 0.f;
     if (tid == 0) {
-      float sl = 0.f, st = 0.f;
       for (int w = 0; w < UW; ++w) {
         sl += sfin[0][w];
         st += sfin[1][w];
       }
+      s_gt = make_float4(st, 0.f, 0.f, 0.f);
+    }
+    cl_sync<CL>();
+    if (tid == 0 && rank == 0) {
+      if constexpr (CL == 2) st += ld_peer(&s_gt, 1u).x;
       a.glam[p] = sl;
       a.gt[p] = st;
     }
-    __syncthreads();
+    cl_sync<CL>();
   }
 }
 
@@ -987,6 +1065,7 @@ struct rska_unrolled {
   int32_t* alias = nullptr;
   float *ckpts = nullptr, *segbuf = nullptr;
   int row_nz = 0;               // row form: float4 columns per lane (0: column form)
+  int row_cl = 1;               // row form: CTAs (a cluster) per problem
   int32_t* tidx = nullptr;      // row form: tau for every problem and iteration [P][K][eta]
   float *tiv = nullptr, *tb = nullptr;
   // inputs of the last forward, kept for the backward
@@ -1041,13 +1120,48 @@ UnrolledArgs uargs(rska_unrolled* u) {
   return a;
 }
 
-// One CTA per problem with the row form's shared memory.
+// CL CTAs (one cluster) per problem with the row form's shared memory.
 template <typename K>
-cudaError_t launch_rows(K kernel, rska_unrolled* u, const UnrolledArgs& a, size_t smem) {
+cudaError_t launch_rows(K kernel, rska_unrolled* u, const UnrolledArgs& a, size_t smem, int CL) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kernel<<<u->P, rska::UT, smem, u->stream>>>(a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(u->P * CL));
+  cfg.blockDim = dim3(rska::UT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = u->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kernel, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+template <int CL>
+cudaError_t launch_fwd_rows(rska_unrolled* u, const UnrolledArgs& a) {
+  const size_t sm = rska::RW_SMEM;
+  switch (u->row_nz) {
+    case 1: return launch_rows(rska::unrolled_fwd_rows_kernel<1, CL>, u, a, sm, CL);
+    case 2: return launch_rows(rska::unrolled_fwd_rows_kernel<2, CL>, u, a, sm, CL);
+    case 4: return launch_rows(rska::unrolled_fwd_rows_kernel<4, CL>, u, a, sm, CL);
+    default: return launch_rows(rska::unrolled_fwd_rows_kernel<8, CL>, u, a, sm, CL);
+  }
+}
+
+template <int CL>
+cudaError_t launch_bwd_rows(rska_unrolled* u, const UnrolledArgs& a) {
+  const size_t sm = rska::RW_SMEM;
+  switch (u->row_nz) {
+    case 1: return launch_rows(rska::unrolled_bwd_rows_kernel<1, CL>, u, a, sm, CL);
+    case 2: return launch_rows(rska::unrolled_bwd_rows_kernel<2, CL>, u, a, sm, CL);
+    case 4: return launch_rows(rska::unrolled_bwd_rows_kernel<4, CL>, u, a, sm, CL);
+    default: return launch_rows(rska::unrolled_bwd_rows_kernel<8, CL>, u, a, sm, CL);
+  }
 }
 
 }  // namespace
@@ -1108,6 +1222,8 @@ int rska_unrolled_setup(rska_unrolled** out, int32_t P, const float* A, const in
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&u->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  // two CTAs per problem when the problems fill at most half of the SMs
+  if (e == cudaSuccess && u->row_nz && 2 * (int64_t)P <= u->num_sms) u->row_cl = 2;
   const int64_t nck = K / ckpt_every;
   double* q = nullptr;
   int32_t* stk = nullptr;
@@ -1120,7 +1236,7 @@ int rska_unrolled_setup(rska_unrolled** out, int32_t P, const float* A, const in
        (e = dalloc(&u->inv_nu, rows)) != cudaSuccess || (e = dalloc(&u->thr, rows)) != cudaSuccess ||
        (e = dalloc(&u->alias, rows)) != cudaSuccess ||
        (e = dalloc(&u->ckpts, (size_t)P * (nck + 1) * u->x_stride)) != cudaSuccess ||
-       (e = dalloc(&u->segbuf, (size_t)P * ckpt_every * u->x_stride)) != cudaSuccess ||
+       (e = dalloc(&u->segbuf, (size_t)P * u->row_cl * ckpt_every * u->x_stride)) != cudaSuccess ||
        (u->row_nz && ((e = dalloc(&u->tidx, (size_t)P * K * eta)) != cudaSuccess ||
                       (e = dalloc(&u->tiv, (size_t)P * K * eta)) != cudaSuccess ||
                       (e = dalloc(&u->tb, (size_t)P * K * eta)) != cudaSuccess)) ||
@@ -1183,13 +1299,8 @@ int rska_unrolled_forward(rska_unrolled* u, const float* b, const float* lambda,
   cudaError_t e = cudaSuccess;
   if (u->row_nz) {
     rska::unrolled_gather_b_kernel<<<u->num_sms * 8, 256, 0, u->stream>>>(a);
-    const size_t sm = rska::RW_SMEM;
-    switch (u->row_nz) {
-      case 1: e = launch_rows(rska::unrolled_fwd_rows_kernel<1>, u, a, sm); break;
-      case 2: e = launch_rows(rska::unrolled_fwd_rows_kernel<2>, u, a, sm); break;
-      case 4: e = launch_rows(rska::unrolled_fwd_rows_kernel<4>, u, a, sm); break;
-      default: e = launch_rows(rska::unrolled_fwd_rows_kernel<8>, u, a, sm); break;
-    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = (u->row_cl == 2) ? launch_fwd_rows<2>(u, a) : launch_fwd_rows<1>(u, a);
   } else {
     const int z = u->zreg;
     if (z == 1)
@@ -1215,13 +1326,7 @@ int rska_unrolled_backward(rska_unrolled* u, const float* gx, float* gb, float* 
   a.gt = gt;
   cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(float) * u->b_total, u->stream);
   if (e == cudaSuccess && u->row_nz) {
-    const size_t sm = rska::RW_SMEM;
-    switch (u->row_nz) {
-      case 1: e = launch_rows(rska::unrolled_bwd_rows_kernel<1>, u, a, sm); break;
-      case 2: e = launch_rows(rska::unrolled_bwd_rows_kernel<2>, u, a, sm); break;
-      case 4: e = launch_rows(rska::unrolled_bwd_rows_kernel<4>, u, a, sm); break;
-      default: e = launch_rows(rska::unrolled_bwd_rows_kernel<8>, u, a, sm); break;
-    }
+    e = (u->row_cl == 2) ? launch_bwd_rows<2>(u, a) : launch_bwd_rows<1>(u, a);
     if (e == cudaSuccess) e = cudaGetLastError();
   } else if (e == cudaSuccess) {
     const int z = u->zreg;
