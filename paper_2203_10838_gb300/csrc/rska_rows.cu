@@ -187,6 +187,8 @@ __global__ void __launch_bounds__(NT, 1)
       }
     };
     fetch_meta(0);
+    int pslot = 0;      // slot of the next row to issue (kept incrementally:
+    int64_t puse = 0;   // no 64-bit division per row) and its use count
     for (int64_t g0 = 0; g0 < total_rows && !stop_now; g0 += 32) {
       const int32_t crow = row;
       const float cb = bv, civ = ivv;
@@ -199,8 +201,8 @@ __global__ void __launch_bounds__(NT, 1)
         int bad = 0;
         if (lane == 0) {
           const int64_t gi = g0 + i;
-          const int sl = (int)(gi % slots);
-          const int64_t use = gi / slots;
+          const int sl = pslot;
+          const int64_t use = puse;
           if (use > 0 && !mbar_wait_bounded(&empty[sl], (uint32_t)((use - 1) & 1), a.limit_ns,
                                             &s_abort))
             bad = 1;
@@ -212,6 +214,10 @@ __global__ void __launch_bounds__(NT, 1)
             tma_load_1d(ring + (size_t)sl * rowbytes_pad, a.A + (int64_t)r_i * a.lda, rowbytes,
                         &full[sl]);
             s_prod = gi + 1;
+            if (++pslot == slots) {
+              pslot = 0;
+              ++puse;
+            }
           }
         }
         if (__shfl_sync(0xffffffffu, bad, 0)) {
@@ -245,6 +251,8 @@ __global__ void __launch_bounds__(NT, 1)
   }
 
   int64_t cons = 0;  // rows consumed
+  int cslot = 0;     // slot of row `cons` and the parity of its current use,
+  uint32_t cpar = 0; // kept incrementally (no 64-bit division per row)
   int gcount = 0;    // groups consumed (selects the wpart buffer)
   // error exit: stop the producer, let every issued copy land, leave
   auto bail = [&]() {
@@ -274,12 +282,14 @@ __global__ void __launch_bounds__(NT, 1)
       bg[g] = 0.f;
       ivg[g] = 0.f;
       if (g < ng) {
-        const int64_t gi = cons + g;
-        const int sl = (int)(gi % slots);
+        int sl = cslot + g;
+        uint32_t par = cpar;
+        if (sl >= slots) {  // g < G <= 2 slots
+          sl -= slots;
+          par ^= 1u;
+        }
         // one lane per warp polls; __syncwarp orders the landed row for the others
-        if (lane == 0 &&
-            !mbar_wait_bounded(&full[sl], (uint32_t)((gi / slots) & 1), a.limit_ns, nullptr))
-          tmo = 1;
+        if (lane == 0 && !mbar_wait_bounded(&full[sl], par, a.limit_ns, nullptr)) tmo = 1;
         __syncwarp();
         const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
 #pragma unroll
@@ -331,6 +341,11 @@ __global__ void __launch_bounds__(NT, 1)
         return;
       }
       cons += ng;
+      cslot += ng;
+      while (cslot >= slots) {
+        cslot -= slots;
+        cpar ^= 1u;
+      }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         // lanes 0..NCW-1 hold the warp partials, the rest zero; a full xor
