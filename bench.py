@@ -651,7 +651,7 @@ def run_unrolled(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None,
                          "peak_kind": f"{peak_kind} (copy bandwidth)",
-                         "kernel": "unrolled_forward_kernel + unrolled_backward_kernel"},
+                         "kernel": "unrolled_fwd_rows_kernel + unrolled_bwd_rows_kernel"},
             "naive_torch_autograd_ms_extrapolated": naive_ms,
             "speedup_vs_naive_autograd": naive_ms / ms if naive_ms else None, "clocks": clk}
     if rank == 0:
