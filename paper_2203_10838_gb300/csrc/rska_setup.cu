@@ -44,9 +44,10 @@ __global__ void row_norms_kernel(const float* __restrict__ A, int64_t m, int64_t
 }
 
 // One block builds the table: all threads stage nu, thread 0 sums W in
-// ascending order, all threads form q_i = (nu_i m) / W, thread 0 runs Vose.
-// With use_smem the q and stack arrays live in shared memory (stack indices
-// as uint16, so m <= 65536); otherwise in the global scratch.
+// ascending order, all threads form q_i = (nu_i m) / W, then the block runs
+// the Vose construction (parallel partition and thresholds, the pairing loop
+// on thread 0).  With use_smem the q and stack arrays live in shared memory
+// (stack indices as uint16, so m <= 65536); otherwise in the global scratch.
 __global__ void alias_build_kernel(const double* __restrict__ nu, int64_t m, uint32_t* thr,
                                    int32_t* alias, double* gq, int32_t* gstk, const int* status,
                                    int use_smem) {
@@ -69,11 +70,10 @@ __global__ void alias_build_kernel(const double* __restrict__ nu, int64_t m, uin
   const double md = (double)m;
   for (int64_t i = threadIdx.x; i < m; i += blockDim.x) q[i] = __ddiv_rn(__dmul_rn(q[i], md), W);
   __syncthreads();
-  if (threadIdx.x != 0) return;
   if (use_smem)
-    vose_sequential<uint16_t>(q, reinterpret_cast<uint16_t*>(q + m), m, thr, alias);
+    vose_block<uint16_t>(q, reinterpret_cast<uint16_t*>(q + m), m, thr, alias);
   else
-    vose_sequential<int32_t>(q, gstk, m, thr, alias);
+    vose_block<int32_t>(q, gstk, m, thr, alias);
 }
 
 __global__ void indices_kernel(const uint32_t* __restrict__ thr, const int32_t* __restrict__ alias,
