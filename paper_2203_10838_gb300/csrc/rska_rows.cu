@@ -77,6 +77,14 @@ __device__ __forceinline__ void red_add_v4(float* p, float4 v) {
                : "memory");
 }
 
+// Arrival on the grid barrier: a release at GPU scope.  Issued by one thread
+// after a barrier over the consumer warps, it orders their reductions before
+// the count (the barrier makes them visible to this thread, and a release is
+// cumulative).
+__device__ __forceinline__ void red_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Barrier among the consumer warps only (named barrier 1).
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
@@ -129,7 +137,7 @@ __global__ void __launch_bounds__(NT, 1)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[SLOTS_MAX];
   __shared__ __align__(8) uint64_t empty[SLOTS_MAX];
-  __shared__ float wpart[2][NCW][G];
+  __shared__ __align__(16) float wpart[2][G][16];  // warp partials, entry 15 stays 0
   __shared__ float sb[SLOTS_MAX];
   __shared__ float siv[SLOTS_MAX];
   __shared__ int s_flag;
@@ -155,6 +163,7 @@ __global__ void __launch_bounds__(NT, 1)
   unsigned char* ring = smem;                                                     // slots x rowbytes_pad
   float4* zsh = reinterpret_cast<float4*>(smem + (size_t)slots * rowbytes_pad);  // ZREG x NC
 
+  if (tid < 2 * G * 16) (&wpart[0][0][0])[tid] = 0.f;
   if (tid == 0) {
     for (int i = 0; i < slots; ++i) {
       mbar_init(&full[i], 1);
@@ -270,6 +279,16 @@ __global__ void __launch_bounds__(NT, 1)
     consumer_sync();
   };
 
+  // this thread's columns t + NC r are valid for r < nvr; column t + NC tail_r
+  // is the last, partly valid float4 when 4 does not divide n
+  int nvr = 0;
+  if (n4 > tid) {
+    const int64_t q = (n4 - tid + NC - 1) / NC;
+    nvr = (q < ZREG) ? (int)q : ZREG;
+  }
+  const int tail_r = ((a.n & 3) != 0 && (n4 - 1 - tid) >= 0 && (n4 - 1 - tid) % NC == 0)
+                         ? (int)((n4 - 1 - tid) / NC)
+                         : -1;
   float4 av[G][ZREG];
   float bg[G], ivg[G];
   bool have_pre = false;
@@ -294,9 +313,8 @@ __global__ void __launch_bounds__(NT, 1)
         const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
 #pragma unroll
         for (int r = 0; r < ZREG; ++r) {
-          const int64_t col = tid + (int64_t)NC * r;
-          float4 v = (col < n4) ? rowp[col] : make_float4(0.f, 0.f, 0.f, 0.f);
-          if (col == n4 - 1) v = mask_tail(v, col, a.n);
+          float4 v = (r < nvr) ? rowp[tid + NC * r] : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (r == tail_r) v = mask_tail(v, tid + (int64_t)NC * r, a.n);
           av[g][r] = v;
         }
         bg[g] = sb[sl];
@@ -333,7 +351,7 @@ __global__ void __launch_bounds__(NT, 1)
       ++gcount;
       if (lane == 0) {
 #pragma unroll
-        for (int g = 0; g < G; ++g) wpart[wp][warp][g] = pd[g];
+        for (int g = 0; g < G; ++g) wpart[wp][g][warp] = pd[g];
       }
       if (consumer_sync_or(tmo)) {
         if (tid == 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
@@ -348,11 +366,12 @@ __global__ void __launch_bounds__(NT, 1)
       }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        // lanes 0..NCW-1 hold the warp partials, the rest zero; a full xor
-        // butterfly leaves the total in every lane
-        float d = (lane < NCW) ? wpart[wp][lane][g] : 0.f;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        // every thread sums the 15 warp partials (and a zero) from shared
+        // memory in one fixed pairwise order: the same value in all threads
+        const float4* wv = reinterpret_cast<const float4*>(&wpart[wp][g][0]);
+        const float4 w0 = wv[0], w1 = wv[1], w2 = wv[2], w3 = wv[3];
+        const float d = (((w0.x + w0.y) + (w0.z + w0.w)) + ((w1.x + w1.y) + (w1.z + w1.w))) +
+                        (((w2.x + w2.y) + (w2.z + w2.w)) + ((w3.x + w3.y) + (w3.z + w3.w)));
         if (g < ng) {
           const float cval = coef * ((d - bg[g]) * ivg[g]);
 #pragma unroll
@@ -401,10 +420,7 @@ __global__ void __launch_bounds__(NT, 1)
     // grid barrier (bounded): arrive, pull the next iteration's first rows
     // into registers (freeing their slots for the producer), then wait
     consumer_sync();
-    if (tid == 0) {
-      __threadfence();
-      atomicAdd(a.bar, 1ull);
-    }
+    if (tid == 0) red_release_u64(a.bar, 1ull);
     int pre_tmo = 0;
     if (j + 1 < a.K && rpi > 0) {
       pre_tmo = load_group(min(G, rpi));
@@ -428,7 +444,9 @@ __global__ void __launch_bounds__(NT, 1)
           }
         }
       }
-      __threadfence();
+      // the acquire load that saw the count orders this CTA's reads of the
+      // reduced update after every CTA's reductions (the consumer barrier
+      // below passes that order on to the other threads)
       s_flag = ok;
     }
     if (consumer_sync_or(pre_tmo) || !s_flag) {
