@@ -413,9 +413,15 @@ __global__ void __launch_bounds__(NT, 1)
       if (rpi > 0 && col < n4) red_add_v4(dacc + col * 4, dl[r]);
       dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (p == 0) {
+    {
+      // every CTA clears its 1/P slice of the accumulator of iteration j + 1
+      // (one CTA clearing all of it would arrive at the barrier last)
       float4* nxt = reinterpret_cast<float4*>(a.racc + (size_t)((j + 1) % 3) * n4 * 4);
-      for (int64_t col = tid; col < n4; col += NC) nxt[col] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int64_t chunk = (n4 + P - 1) / P;
+      for (int64_t c = tid; c < chunk; c += NC) {
+        const int64_t col = (int64_t)p * chunk + c;
+        if (col < n4) nxt[col] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
     // grid barrier (bounded): arrive, pull the next iteration's first rows
     // into registers (freeing their slots for the producer), then wait

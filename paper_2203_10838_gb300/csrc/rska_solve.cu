@@ -313,9 +313,11 @@ __global__ void __launch_bounds__(NT, 1)
         reduce_batch(ib);
       }
     }
-    if (!single && blockIdx.x == 0) {
+    if (!single) {
+      // every CTA clears its share of the accumulators of iteration j + 1
       float* nxt = a.racc + (size_t)((j + 1) % 3) * eta * kAccStride;
-      for (int s = tid; s < eta; s += NT) nxt[(size_t)s * kAccStride] = 0.f;
+      for (int s = blockIdx.x + (int)gridDim.x * tid; s < eta; s += (int)gridDim.x * NT)
+        nxt[(size_t)s * kAccStride] = 0.f;
     }
     cp_async_wait<0>();
 
