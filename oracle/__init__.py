@@ -69,6 +69,9 @@ def _load():
     lib.orc_sample.restype = None
     lib.orc_rska_fixed.argtypes = [P, i64, i64, i64, P, P, f64, f64, i32, P, i64, P]
     lib.orc_rska_fixed.restype = ctypes.c_int
+    lib.orc_rska_fixed_weighted.argtypes = [P, i64, i64, i64, P, P, P, f64, f64, i32, P, i64,
+                                            P]
+    lib.orc_rska_fixed_weighted.restype = ctypes.c_int
     lib.orc_rska_sampled.argtypes = [P, i64, i64, i64, P, P, P, P, f64, f64, i32, u64, u32,
                                      i64, i64, P]
     lib.orc_rska_sampled.restype = ctypes.c_int
@@ -130,10 +133,13 @@ def sample(thr, alias, seed: int, eta: int, k0: int, K: int, problem: int = 0) -
     return out.reshape(K, eta)
 
 
-def rska_fixed(A, b, lam: float, t: float, eta: int, tau, z0=None, nu=None) -> np.ndarray:
+def rska_fixed(A, b, lam: float, t: float, eta: int, tau, z0=None, nu=None,
+               w=None) -> np.ndarray:
     """K = len(tau) iterations of eq. (rska) with the given index sequence.
 
-    tau has shape (K, eta).  Returns the dual iterate z_K (x_K = S_lam(z_K)).
+    tau has shape (K, eta).  w (optional, m entries) is the diagonal of the
+    weight matrix W: row i's step is scaled by t * w_i (Sec. 5, v3/v4 with
+    t = 1).  Returns the dual iterate z_K (x_K = S_lam(z_K)).
     """
     A, lda = _as_A(A)
     m, n = A.shape
@@ -143,6 +149,15 @@ def rska_fixed(A, b, lam: float, t: float, eta: int, tau, z0=None, nu=None) -> n
     if tau.size and (tau.min() < 0 or tau.max() >= m):
         raise ValueError("index out of range")
     z = np.zeros(n, dtype=np.float64) if z0 is None else np.array(z0, dtype=np.float64)
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (m,):
+            raise ValueError("w must have one entry per row")
+        rc = _load().orc_rska_fixed_weighted(_ptr(A), m, n, lda, _ptr(b), _ptr(nu), _ptr(w),
+                                             lam, t, eta, _ptr(tau), tau.shape[0], _ptr(z))
+        if rc != 0:
+            raise ValueError(f"rska_fixed_weighted failed ({rc})")
+        return z
     rc = _load().orc_rska_fixed(_ptr(A), m, n, lda, _ptr(b), _ptr(nu), lam, t, eta, _ptr(tau),
                                 tau.shape[0], _ptr(z))
     if rc != 0:

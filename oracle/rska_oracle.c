@@ -24,6 +24,11 @@
  *                       (Lemma 1 / Lemma 2), Lemma lm:bd decrease, eta=1 RSK,
  *                       lambda=0 minimum-norm limit (pseudo-inverse), range
  *                       invariant, brute-force RBPP limit.
+ *   orc_rska_fixed_weighted  pinned: w = 1 and constant w reduce to
+ *                       orc_rska_fixed bit for bit; the exact mean of the step
+ *                       over all index tuples equals the closed forms of v3
+ *                       (A^T W (A x - b)/||A||_F^2) and v4 (A^T (A x - b) /
+ *                       sum_j ||a_j||^2/w_j).
  *   orc_unrolled_grad   pinned: central finite differences of orc_rska_fixed.
  *   orc_metrics         pinned: closed form on hand-made vectors.
  */
@@ -210,18 +215,19 @@ static double soft_shrink(double v, double lambda)
 }
 
 /* ------------------------------------------------------------------------ */
-/* One RSKA iteration, eq. (rska) / Algorithm 1 with uniform weights w_i = t */
-/* (variant v2 of Sec. 5 with alpha = t; t = 1 is v1):                       */
+/* One RSKA iteration, eq. (rska) / Algorithm 1 with weights t w_i (w = NULL: */
+/* uniform weights t, variant v2 of Sec. 5 with alpha = t, t = 1 is v1; a    */
+/* general diagonal W = diag(w) with t = 1 is v3 or v4):                     */
 /*   x_k      = S_lambda(z_k)                   (z = x^*, the dual iterate)  */
-/*   delta_k  = (1/eta) sum_{s} t (<a_{i_s}, x_k> - b_{i_s}) / ||a_{i_s}||^2 */
-/*              * a_{i_s}     (sum over the eta draws, duplicates included)  */
+/*   delta_k  = (1/eta) sum_{s} t w_{i_s} (<a_{i_s}, x_k> - b_{i_s})         */
+/*              / ||a_{i_s}||^2 * a_{i_s}  (the eta draws, duplicates count) */
 /*   z_{k+1}  = z_k - delta_k ;   x_{k+1} = S_lambda(z_{k+1}).               */
 /* Residuals are taken at the thresholded x_k, coefficient sums in draw     */
 /* order.  x and delta are caller-provided work vectors of length n.         */
 /* ------------------------------------------------------------------------ */
 static void rska_iteration(const float *A, int64_t n, int64_t lda, const double *b,
-                           const double *nu, double lambda, double t, int32_t eta,
-                           const int32_t *tau, double *z, double *x, double *delta)
+                           const double *nu, const double *w, double lambda, double t,
+                           int32_t eta, const int32_t *tau, double *z, double *x, double *delta)
 {
     for (int64_t j = 0; j < n; ++j) {
         x[j] = soft_shrink(z[j], lambda);
@@ -232,7 +238,8 @@ static void rska_iteration(const float *A, int64_t n, int64_t lda, const double 
         const float *row = A + i * lda;
         double dot = 0.0;
         for (int64_t j = 0; j < n; ++j) dot = dot + (double)row[j] * x[j];
-        double coeff = t * (dot - b[i]) / nu[i];
+        double weight = w ? t * w[i] : t;
+        double coeff = weight * (dot - b[i]) / nu[i];
         for (int64_t j = 0; j < n; ++j) delta[j] = delta[j] + coeff * (double)row[j];
     }
     for (int64_t j = 0; j < n; ++j) z[j] = z[j] - delta[j] / (double)eta;
@@ -252,7 +259,26 @@ int orc_rska_fixed(const float *A, int64_t m, int64_t n, int64_t lda, const doub
         return -2;
     }
     for (int64_t k = 0; k < K; ++k)
-        rska_iteration(A, n, lda, b, nu, lambda, t, eta, tau + k * eta, z, x, delta);
+        rska_iteration(A, n, lda, b, nu, NULL, lambda, t, eta, tau + k * eta, z, x, delta);
+    free(x); free(delta);
+    return 0;
+}
+
+/* As orc_rska_fixed with row weights w (m entries, the diagonal of W in     */
+/* eq. (rska)); the step of row i is scaled by t * w_i.                      */
+int orc_rska_fixed_weighted(const float *A, int64_t m, int64_t n, int64_t lda, const double *b,
+                            const double *nu, const double *w, double lambda, double t,
+                            int32_t eta, const int32_t *tau, int64_t K, double *z)
+{
+    if (m < 1 || n < 1 || lda < n || eta < 1 || K < 0 || !w) return -1;
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *delta = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!x || !delta) {
+        free(x); free(delta);
+        return -2;
+    }
+    for (int64_t k = 0; k < K; ++k)
+        rska_iteration(A, n, lda, b, nu, w, lambda, t, eta, tau + k * eta, z, x, delta);
     free(x); free(delta);
     return 0;
 }
@@ -273,7 +299,7 @@ int orc_rska_sampled(const float *A, int64_t m, int64_t n, int64_t lda, const do
     }
     for (int64_t k = k0; k < k0 + K; ++k) {
         draw_iteration(thr, alias, m, seed, problem, k, eta, tau);
-        rska_iteration(A, n, lda, b, nu, lambda, t, eta, tau, z, x, delta);
+        rska_iteration(A, n, lda, b, nu, NULL, lambda, t, eta, tau, z, x, delta);
     }
     free(x); free(delta); free(tau);
     return 0;
@@ -347,7 +373,7 @@ int orc_unrolled_grad(const float *A, int64_t m, int64_t n, int64_t lda, const d
     /* forward, keeping z_0 .. z_K */
     for (int64_t k = 0; k < K; ++k) {
         memcpy(zs + (k + 1) * n, zs + k * n, sizeof(double) * (size_t)n);
-        rska_iteration(A, n, lda, b, nu, lambda, t, eta, tau + k * eta, zs + (k + 1) * n, x,
+        rska_iteration(A, n, lda, b, nu, NULL, lambda, t, eta, tau + k * eta, zs + (k + 1) * n, x,
                        delta);
     }
     /* loss and its gradient at x_K */
