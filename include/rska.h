@@ -176,6 +176,29 @@ int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
  */
 int rska_set_option(rska_ctx *ctx, int what, int64_t value);
 
+/*
+ * rska_set_weights -- HOST: a general diagonal weight matrix W = diag(w) in
+ * eq. (rska) (Sec. 5, variants v3 and v4).  From the next solve, iteration k
+ * applies
+ *     z -= (t/eta) sum_{s} w_{i_s} (<a_{i_s}, x_k> - b_{i_s}) / ||a_{i_s}||^2 a_{i_s}
+ * (t = 1 gives the paper's v3/v4; the product w_i/||a_i||^2 is formed in FP64
+ * and rounded once to FP32).
+ *   w:      device pointer to m floats (read during the call, not kept), each
+ *           finite and > 0; NULL restores uniform weights (w_i = 1).
+ *   couple: 0 keeps p_i = ||a_i||^2/||A||_F^2 (v3); 1 samples p_i proportional
+ *           to ||a_i||^2/w_i (v4): the alias table is rebuilt over
+ *           rho_i = nu_i / w_i (one FP64 division per row) by the same
+ *           construction and Philox draws as the index contract above, so
+ *           rska_get_tables and rska_get_indices return the coupled table and
+ *           indices.  With w = NULL couple is ignored.
+ * The iteration count k and the iterate are kept.  Synchronous on the
+ * context's stream; allocates temporary device memory.  Returns RSKA_EINVAL
+ * for a null context, couple not 0 or 1, or a weight that is not finite and
+ * positive (then nothing is changed), RSKA_ENOMEM, RSKA_ECUDA, or the
+ * context's sticky error.
+ */
+int rska_set_weights(rska_ctx *ctx, const float *w, int couple);
+
 /* ------------------------------------------------------------------------ */
 /* Batched independent systems: eq. (rska) / Algorithm 1 run on P problems   */
 /* (A_p, b_p) in one persistent launch, each with its own index stream       */

@@ -383,6 +383,55 @@ int rska_reset(rska_ctx* h) {
   return RSKA_OK;
 }
 
+int rska_set_weights(rska_ctx* h, const float* w, int couple) {
+  if (!h || (couple != 0 && couple != 1)) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky != RSKA_OK) return c->sticky;
+  cudaStream_t s = c->stream;
+  const int64_t m = c->m;
+  // scratch: the new scales, rho, the alias build's q and stack, a flag
+  float* scale = nullptr;
+  double* rho = nullptr;
+  double* q = nullptr;
+  int32_t* stk = nullptr;
+  int* bad = nullptr;
+  cudaError_t e = dalloc(&scale, m);
+  if (e == cudaSuccess) e = dalloc(&rho, m);
+  if (e == cudaSuccess) e = dalloc(&q, m);
+  if (e == cudaSuccess) e = dalloc(&stk, m);
+  if (e == cudaSuccess) e = dalloc(&bad, 1);
+  auto release = [&]() {
+    cudaFree(scale);
+    cudaFree(rho);
+    cudaFree(q);
+    cudaFree(stk);
+    cudaFree(bad);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+  }
+  int hbad = 0;
+  e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = rska::launch_weights(c->nu, w, m, couple, scale, rho, bad, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e);
+  }
+  if (hbad) {  // nothing has changed
+    release();
+    return RSKA_EINVAL;
+  }
+  e = cudaMemcpyAsync(c->inv_nu, scale, sizeof(float) * (size_t)m, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = rska::launch_alias_build(rho, m, c->thr, c->alias, q, stk, c->status, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  return check_status(c);
+}
+
 int rska_destroy(rska_ctx* h) {
   if (!h) return RSKA_EINVAL;
   cudaStreamSynchronize(h->c.stream);

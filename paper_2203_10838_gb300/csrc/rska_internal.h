@@ -107,6 +107,8 @@ struct Ctx {
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_row_norms(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
                              double* nu, float* inv_nu, int* status, cudaStream_t s);
+cudaError_t launch_weights(const double* nu, const float* w, int64_t m, int couple, float* scale,
+                           double* rho, int* bad, cudaStream_t s);
 cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,
                                double* q_scratch, int32_t* stack_scratch, int* status,
                                cudaStream_t s);

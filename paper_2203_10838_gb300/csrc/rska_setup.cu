@@ -115,6 +115,39 @@ cudaError_t launch_row_norms(const float* A, int64_t m, int64_t n, int64_t lda, 
   return cudaGetLastError();
 }
 
+// Row weights w_i of eq. (rska) (the diagonal of W; Sec. 5, variants v3 and
+// v4).  scale_i = w_i / nu_i rounded once to FP32 (the factor the solver applies
+// to row i's residual; w = NULL gives 1/nu_i, the uniform-weight value), and
+// rho_i = nu_i / w_i in FP64 when the sampling is coupled to the weights (v4),
+// else nu_i.  A weight that is not finite and positive sets *bad.
+__global__ void weights_kernel(const double* __restrict__ nu, const float* __restrict__ w,
+                               int64_t m, int couple, float* __restrict__ scale,
+                               double* __restrict__ rho, int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double p = nu[i];
+    double wi = 1.0;
+    if (w != nullptr) {
+      const float wf = w[i];
+      if (!(isfinite(wf) && wf > 0.f)) {
+        atomicExch(bad, 1);
+      }
+      wi = (double)wf;
+    }
+    scale[i] = (float)__ddiv_rn(wi, p);
+    rho[i] = (couple && w != nullptr) ? __ddiv_rn(p, wi) : p;
+  }
+}
+
+cudaError_t launch_weights(const double* nu, const float* w, int64_t m, int couple, float* scale,
+                           double* rho, int* bad, cudaStream_t s) {
+  int64_t blocks = (m + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(nu, w, m, couple, scale, rho, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,
                                double* q_scratch, int32_t* stack_scratch, int* status,
                                cudaStream_t s) {

@@ -137,6 +137,19 @@ class Solver:
     def set_option(self, what: str, value: int):
         check(lib().rska_set_option(self._h, OPTION[what], int(value)), "rska_set_option")
 
+    def set_weights(self, w=None, couple: bool = False):
+        """Row weights w_i of eq. (rska) (Sec. 5, v3: couple=False keeps
+        p_i ~ ||a_i||^2; v4: couple=True samples p_i ~ ||a_i||^2 / w_i).
+        w: float32 CUDA tensor of m entries, finite and > 0, or None for
+        uniform weights."""
+        ptr = None
+        if w is not None:
+            if (not w.is_cuda or w.dtype != torch.float32 or w.dim() != 1
+                    or w.shape[0] != self.m or not w.is_contiguous()):
+                raise ValueError("w must be a contiguous float32 CUDA vector of m entries")
+            ptr = ctypes.c_void_p(w.data_ptr())
+        check(lib().rska_set_weights(self._h, ptr, 1 if couple else 0), "rska_set_weights")
+
 
 def rska_setup(A, b, lam, eta, t, seed, n=None, stream=None) -> Solver:
     return Solver(A, b, lam, eta, t, seed, n=n, stream=stream)

@@ -82,6 +82,8 @@ def test_null_context_is_rejected(L):
     assert L.rska_metrics(None, None, None, None) == 1
     k = ctypes.c_int64()
     assert L.rska_iteration(None, ctypes.byref(k)) == 1
+    assert L.rska_set_weights(None, None, 0) == 1
+    assert L.rska_set_weights(None, None, 2) == 1
 
 
 @pytest.mark.parametrize("args", [
