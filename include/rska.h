@@ -199,6 +199,25 @@ int rska_set_option(rska_ctx *ctx, int what, int64_t value);
  */
 int rska_set_weights(rska_ctx *ctx, const float *w, int couple);
 
+/*
+ * rska_sigma_max2 -- HOST: an estimate of sigma_max(A)^2, which Corollary 1
+ * needs for the step alpha^*(eta) and Theorem th:RSKA for the admissible range
+ * of t.  `iters` power iterations on A^T A from a start vector drawn from
+ * `seed` (splitmix64 per entry): u = A v, rq = ||u||^2 (FP64), w = A^T u,
+ * v = w / ||w|| (FP64 norm); products in FP32, reduced in a fixed order.
+ *   sigma2_out: the last Rayleigh quotient rq (a lower estimate that converges
+ *               to sigma_max^2 as iters grows; the rate depends on the gap
+ *               between the two largest singular values)
+ *   fro2_out:   nullable; ||A||_F^2 = sum_i nu_i (FP64)
+ *   alpha_out:  nullable; alpha^*(eta) = eta / (1 + (eta - 1) sigma2 / fro2)
+ *               (Corollary 1, uniform weights), usable as t in rska_setup
+ * Synchronous on the context's stream; allocates temporary device memory
+ * (m + 19 n floats).  Returns RSKA_EINVAL for a null context or sigma2_out or
+ * iters outside 1..100000, RSKA_ENOMEM, RSKA_ECUDA, or the sticky error.
+ */
+int rska_sigma_max2(rska_ctx *ctx, int32_t iters, uint64_t seed, double *sigma2_out,
+                    double *fro2_out, double *alpha_out);
+
 /* ------------------------------------------------------------------------ */
 /* Batched independent systems: eq. (rska) / Algorithm 1 run on P problems   */
 /* (A_p, b_p) in one persistent launch, each with its own index stream       */

@@ -15,7 +15,11 @@ What each function follows in the paper (Tondji & Lorenz, arXiv 2203.10838):
 * ``alias_build``   -- Walker/Vose table for p_i = ||a_i||^2 / ||A||_F^2
   (Sec. 5, variants v1/v2).
 * ``sample``        -- tau_k with replacement (eq. rska, Algorithm 1).
-* ``rska_fixed`` / ``rska`` -- eq. (rska) / Algorithm 1 with w_i = t.
+* ``rska_fixed`` / ``rska`` -- eq. (rska) / Algorithm 1 with w_i = t, or
+  t w_i for given row weights (Sec. 5, variants v3/v4).
+* ``sigma_max2`` / ``alpha_star`` -- sigma_max(A)^2 (the largest eigenvalue
+  of A^T A, a library eigensolver in FP64) and the step alpha^*(eta) of
+  Corollary 1 (uniform weights).
 * ``rska_mrhs``     -- eq. (rska) on every right-hand side b_j of a shared A
   with one index sequence (the matrix form A^T M_k (A x - b) of Sec. 3 per
   column).
@@ -196,6 +200,20 @@ def rska_mrhs(A, B, lam: float, t: float, eta: int, tau, nu=None, rows=None) -> 
     B = np.asarray(B)
     rows = range(B.shape[0]) if rows is None else rows
     return np.stack([rska_fixed(A, B[j], lam, t, eta, tau, nu=nu) for j in rows])
+
+
+def sigma_max2(A) -> float:
+    """sigma_max(A)^2: the largest eigenvalue of A^T A (or A A^T, the smaller
+    of the two) formed in FP64 from the FP32 values."""
+    A = np.asarray(A, dtype=np.float64)
+    G = A.T @ A if A.shape[1] <= A.shape[0] else A @ A.T
+    return float(np.linalg.eigvalsh(G)[-1])
+
+
+def alpha_star(eta: int, sigma2: float, fro2: float) -> float:
+    """alpha^* = eta / (1 + (eta - 1) sigma_max^2 / ||A||_F^2), the uniform
+    weight of Corollary 1 that maximises the rate bound L(alpha)."""
+    return eta / (1.0 + (eta - 1) * sigma2 / fro2)
 
 
 def soft_shrink(z, lam: float) -> np.ndarray:

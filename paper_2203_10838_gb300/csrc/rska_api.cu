@@ -432,6 +432,40 @@ int rska_set_weights(rska_ctx* h, const float* w, int couple) {
   return check_status(c);
 }
 
+int rska_sigma_max2(rska_ctx* h, int32_t iters, uint64_t seed, double* sigma2_out,
+                    double* fro2_out, double* alpha_out) {
+  if (!h || !sigma2_out || iters < 1 || iters > 100000) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky != RSKA_OK) return c->sticky;
+  cudaStream_t s = c->stream;
+  float* scratch = nullptr;
+  double* d = nullptr;
+  cudaError_t e = dalloc(&scratch, rska::sigma_scratch_floats(c->m, c->n));
+  if (e == cudaSuccess) e = dalloc(&d, 4);
+  if (e != cudaSuccess) {
+    cudaFree(scratch);
+    cudaFree(d);
+    return (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+  }
+  double host[2] = {0.0, 0.0};
+  e = rska::launch_sigma_max2(c->A, c->m, c->n, c->lda, c->nu, iters, seed, scratch, d, d + 2,
+                              d + 3, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host, d + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  const double sigma2 = host[0], fro2 = host[1];
+  *sigma2_out = sigma2;
+  if (fro2_out) *fro2_out = fro2;
+  if (alpha_out) {
+    const double eta = (double)c->eta;
+    *alpha_out = (fro2 > 0.0) ? eta / (1.0 + (eta - 1.0) * sigma2 / fro2) : 0.0;
+  }
+  return RSKA_OK;
+}
+
 int rska_destroy(rska_ctx* h) {
   if (!h) return RSKA_EINVAL;
   cudaStreamSynchronize(h->c.stream);

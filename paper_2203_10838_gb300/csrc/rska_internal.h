@@ -107,6 +107,13 @@ struct Ctx {
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_row_norms(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
                              double* nu, float* inv_nu, int* status, cudaStream_t s);
+// sigma_max(A)^2 by `iters` power iterations (rq_out: the last Rayleigh
+// quotient; fro2_out: sum of nu); scratch holds sigma_scratch_floats(m, n)
+// floats, d2 two doubles.
+size_t sigma_scratch_floats(int64_t m, int64_t n);
+cudaError_t launch_sigma_max2(const float* A, int64_t m, int64_t n, int64_t lda, const double* nu,
+                              int32_t iters, uint64_t seed, float* scratch, double* d2,
+                              double* rq_out, double* fro2_out, cudaStream_t s);
 cudaError_t launch_weights(const double* nu, const float* w, int64_t m, int couple, float* scale,
                            double* rho, int* bad, cudaStream_t s);
 cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,

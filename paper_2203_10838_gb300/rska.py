@@ -137,6 +137,14 @@ class Solver:
     def set_option(self, what: str, value: int):
         check(lib().rska_set_option(self._h, OPTION[what], int(value)), "rska_set_option")
 
+    def sigma_max2(self, iters: int = 50, seed: int = 0):
+        """(sigma_max(A)^2 estimate, ||A||_F^2, alpha^*(eta)) by power
+        iteration on A^T A (Corollary 1)."""
+        s2, f2, al = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().rska_sigma_max2(self._h, int(iters), int(seed), ctypes.byref(s2),
+                                    ctypes.byref(f2), ctypes.byref(al)), "rska_sigma_max2")
+        return s2.value, f2.value, al.value
+
     def set_weights(self, w=None, couple: bool = False):
         """Row weights w_i of eq. (rska) (Sec. 5, v3: couple=False keeps
         p_i ~ ||a_i||^2; v4: couple=True samples p_i ~ ||a_i||^2 / w_i).
