@@ -418,6 +418,14 @@ def run_gpu(args):
                "sample": f"{iters} iterations of this workload from z=0 ({el:.1f} s, FP64, "
                          "single thread)"}
 
+    # the step of Corollary 1 from a power-iteration estimate of sigma_max^2
+    # (outside the timed region), beside the Marchenko-Pastur value the
+    # workload uses
+    step = None
+    if not args.skip_plain:
+        s2, f2, al = sol.sigma_max2(30, 0)
+        step = {"t_used": T_STEP, "t_rule": "alpha*(eta) with sigma_max^2 ~ (sqrt m + sqrt n)^2",
+                "power_iteration": {"iters": 30, "sigma_max2": s2, "fro2": f2, "alpha_star": al}}
     sol.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -428,7 +436,8 @@ def run_gpu(args):
                 "clocks": clk, "gpu_launches": 2 * args.steps,
                 "accuracy": {"rel_residual": rel_res, "rel_error": rel_err,
                              "after_iterations": ITERS},
-                "plain_rska_gpu": plain, "time_to_accuracy": tta, "eta_sweep": sweep}
+                "plain_rska_gpu": plain, "time_to_accuracy": tta, "eta_sweep": sweep,
+                "step": step}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
