@@ -218,6 +218,22 @@ int rska_set_weights(rska_ctx *ctx, const float *w, int couple);
 int rska_sigma_max2(rska_ctx *ctx, int32_t iters, uint64_t seed, double *sigma2_out,
                     double *fro2_out, double *alpha_out);
 
+/*
+ * rska_linearized_bregman -- HOST: K iterations of the linearized Bregman
+ * method, the eta -> infinity limit of eq. (rska) (Sec. 4, the remark on the
+ * linearized Bregman rate and the mini-batch versus full-batch remark):
+ *     z -= step * A^T (A x - b),   x = S_lambda(z)
+ * (the paper's step is 1/sigma_max(A)^2; rska_sigma_max2 estimates it).  Runs
+ * as the row-split kernel over every row once per iteration (one pass over A)
+ * from the context's current z, and leaves z, x there; the RSKA iteration
+ * counter k and its index sequence are not touched.  Requires n <= 11520
+ * (else RSKA_EUNSUPPORTED).  Synchronous; allocates temporary device memory
+ * (3 m + 2 words).  Returns RSKA_EINVAL for a null context, K < 0 or a step
+ * that is not finite and positive, RSKA_ETIMEOUT, RSKA_ECUDA, or the sticky
+ * error.
+ */
+int rska_linearized_bregman(rska_ctx *ctx, int64_t K, double step);
+
 /* ------------------------------------------------------------------------ */
 /* Batched independent systems: eq. (rska) / Algorithm 1 run on P problems   */
 /* (A_p, b_p) in one persistent launch, each with its own index stream       */

@@ -17,6 +17,8 @@ What each function follows in the paper (Tondji & Lorenz, arXiv 2203.10838):
 * ``sample``        -- tau_k with replacement (eq. rska, Algorithm 1).
 * ``rska_fixed`` / ``rska`` -- eq. (rska) / Algorithm 1 with w_i = t, or
   t w_i for given row weights (Sec. 5, variants v3/v4).
+* ``linearized_bregman`` -- the full-gradient limit eta -> infinity of
+  eq. (rska) (Sec. 4 remarks), step by step.
 * ``sigma_max2`` / ``alpha_star`` -- sigma_max(A)^2 (the largest eigenvalue
   of A^T A, a library eigensolver in FP64) and the step alpha^*(eta) of
   Corollary 1 (uniform weights).
@@ -214,6 +216,19 @@ def alpha_star(eta: int, sigma2: float, fro2: float) -> float:
     """alpha^* = eta / (1 + (eta - 1) sigma_max^2 / ||A||_F^2), the uniform
     weight of Corollary 1 that maximises the rate bound L(alpha)."""
     return eta / (1.0 + (eta - 1) * sigma2 / fro2)
+
+
+def linearized_bregman(A, b, lam: float, step: float, K: int, z0=None) -> np.ndarray:
+    """K iterations of the linearized Bregman method (the remark on its rate
+    in Sec. 4): z <- z - step A^T (A x - b), x = S_lam(z), in FP64 on the
+    FP32 values of A.  Returns z_K."""
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    z = np.zeros(A.shape[1]) if z0 is None else np.array(z0, dtype=np.float64)
+    for _ in range(K):
+        x = soft_shrink(z, lam)
+        z = z - step * (A.T @ (A @ x - b))
+    return z
 
 
 def soft_shrink(z, lam: float) -> np.ndarray:

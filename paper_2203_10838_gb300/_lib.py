@@ -38,6 +38,7 @@ def _declare(lib):
         "rska_query": ([P, c_int, ctypes.POINTER(i64)], c_int),
         "rska_set_option": ([P, c_int, i64], c_int),
         "rska_set_weights": ([P, P, c_int], c_int),
+        "rska_linearized_bregman": ([P, i64, f64], c_int),
         "rska_sigma_max2": ([P, i32, u64, ctypes.POINTER(f64), ctypes.POINTER(f64),
                              ctypes.POINTER(f64)], c_int),
         "rska_batch_setup": ([PP, i32, P, P, P, P, P, P, P, f32, i32, f32, u64, P], c_int),

@@ -1,5 +1,6 @@
 // rska_api.cu -- the C ABI of librska (declared in include/rska.h).
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -121,6 +122,7 @@ rska::SolveArgs solve_args(Ctx* c, int64_t K, const int* stop) {
   a.tidx = c->tidx;
   a.tb = c->tb;
   a.tiv = c->tiv;
+  a.tstride = (c->eta + 3) / 4 * 4;
   a.K = K;
   a.limit_ns = c->limit_ns;
   return a;
@@ -464,6 +466,56 @@ int rska_sigma_max2(rska_ctx* h, int32_t iters, uint64_t seed, double* sigma2_ou
     *alpha_out = (fro2 > 0.0) ? eta / (1.0 + (eta - 1.0) * sigma2 / fro2) : 0.0;
   }
   return RSKA_OK;
+}
+
+int rska_linearized_bregman(rska_ctx* h, int64_t K, double step) {
+  if (!h || K < 0 || !(step > 0.0) || !(step < 3.0e38)) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->sticky != RSKA_OK) return c->sticky;
+  if (K == 0) return RSKA_OK;
+  if (c->m > INT32_MAX) return RSKA_EUNSUPPORTED;
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  // every row once per iteration: eta = m
+  rska::RowsGeometry rg;
+  if (!rska::plan_rows(c->n, (int32_t)c->m, c->num_sms, c->grid_override, (size_t)optin, &rg))
+    return RSKA_EUNSUPPORTED;
+  const int64_t m4 = (c->m + 3) / 4 * 4;
+  int32_t* idx = nullptr;
+  float* tb = nullptr;
+  float* tiv = nullptr;
+  int64_t* kscratch = nullptr;
+  e = dalloc(&idx, m4);
+  if (e == cudaSuccess) e = dalloc(&tb, m4);
+  if (e == cudaSuccess) e = dalloc(&tiv, m4);
+  if (e == cudaSuccess) e = dalloc(&kscratch, 1);
+  auto release = [&]() {
+    cudaFree(idx);
+    cudaFree(tb);
+    cudaFree(tiv);
+    cudaFree(kscratch);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+  }
+  cudaStream_t s = c->stream;
+  rska::SolveArgs a = solve_args(c, K, nullptr);
+  a.eta = (int32_t)c->m;
+  a.coef = (float)step;
+  a.tidx = idx;
+  a.tb = tb;
+  a.tiv = tiv;
+  a.tstride = 0;
+  a.kdev = kscratch;  // the index counter k of the RSKA iteration is not advanced
+  e = cudaMemsetAsync(kscratch, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = rska::launch_full_sweep(c->b, c->m, idx, tb, tiv, s);
+  if (e == cudaSuccess) e = rska::launch_rows(a, rg, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  return check_status(c);
 }
 
 int rska_destroy(rska_ctx* h) {

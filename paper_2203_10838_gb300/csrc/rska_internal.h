@@ -60,6 +60,9 @@ struct SolveArgs {
   const int32_t* tidx;         // pre-sampled tau (K rows of eta4)
   const float* tb;             // b at tau
   const float* tiv;            // 1/||a||^2 at tau
+  int64_t tstride;             // entries of tidx/tb/tiv per iteration (eta rounded up to 4);
+                               // 0: one fixed list for every iteration (row-split kernel
+                               // only, no pre-sampling)
   int64_t K;
   uint64_t limit_ns;
 };
@@ -114,6 +117,8 @@ size_t sigma_scratch_floats(int64_t m, int64_t n);
 cudaError_t launch_sigma_max2(const float* A, int64_t m, int64_t n, int64_t lda, const double* nu,
                               int32_t iters, uint64_t seed, float* scratch, double* d2,
                               double* rq_out, double* fro2_out, cudaStream_t s);
+cudaError_t launch_full_sweep(const float* b, int64_t m, int32_t* idx, float* tb, float* tiv,
+                              cudaStream_t s);
 cudaError_t launch_weights(const double* nu, const float* w, int64_t m, int couple, float* scale,
                            double* rho, int* bad, cudaStream_t s);
 cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,

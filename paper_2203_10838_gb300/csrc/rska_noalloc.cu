@@ -161,6 +161,7 @@ extern "C" int rska_solve_noalloc(const float* A, int64_t m, int64_t n, int64_t 
   a.tidx = reinterpret_cast<int32_t*>(base + L.tidx);
   a.tb = reinterpret_cast<float*>(base + L.tb);
   a.tiv = reinterpret_cast<float*>(base + L.tiv);
+  a.tstride = (eta + 3) / 4 * 4;
   a.limit_ns = 2000000000ull;
   for (int64_t done = 0; done < K && e == cudaSuccess; done += L.chunk) {
     a.K = (K - done < L.chunk) ? (K - done) : L.chunk;

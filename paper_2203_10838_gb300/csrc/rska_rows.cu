@@ -153,7 +153,6 @@ __global__ void __launch_bounds__(NT, 1)
   const int P = gridDim.x;
   const int p = blockIdx.x;
   const int eta = a.eta;
-  const int eta4 = (eta + 3) & ~3;
   const int64_t n4 = (a.n + 3) >> 2;
   const bool single = (P == 1);
   const int rpi = (p < eta) ? (eta - p + P - 1) / P : 0;  // rows of tau_k owned per iteration
@@ -189,7 +188,7 @@ __global__ void __launch_bounds__(NT, 1)
       if (gl < total_rows) {
         const int64_t jj = gl / rpi;
         const int q = (int)(gl - jj * rpi);
-        const int64_t o = jj * eta4 + p + (int64_t)P * q;
+        const int64_t o = jj * a.tstride + p + (int64_t)P * q;
         row = a.tidx[o];
         bv = a.tb[o];
         ivv = a.tiv[o];
@@ -545,7 +544,8 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
 }
 
 cudaError_t launch_rows(const SolveArgs& a, const RowsGeometry& g, cudaStream_t s) {
-  cudaError_t e = launch_presample(a, s);
+  cudaError_t e = cudaSuccess;
+  if (a.tstride != 0) e = launch_presample(a, s);
   if (e != cudaSuccess) return e;
   const int64_t n4 = (a.n + 3) / 4;
   e = cudaMemsetAsync(a.racc, 0, sizeof(float) * 3 * (size_t)n4 * 4, s);

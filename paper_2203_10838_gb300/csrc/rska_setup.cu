@@ -139,6 +139,28 @@ __global__ void weights_kernel(const double* __restrict__ nu, const float* __res
   }
 }
 
+// The index list of a full sweep (every row once, in order) with b at the
+// rows and a per-row factor of 1: the linearized Bregman step as one
+// iteration of the row-split kernel.
+__global__ void full_sweep_kernel(const float* __restrict__ b, int64_t m, int32_t* __restrict__ idx,
+                                  float* __restrict__ tb, float* __restrict__ tiv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    idx[i] = (int32_t)i;
+    tb[i] = b[i];
+    tiv[i] = 1.0f;
+  }
+}
+
+cudaError_t launch_full_sweep(const float* b, int64_t m, int32_t* idx, float* tb, float* tiv,
+                              cudaStream_t s) {
+  int64_t blocks = (m + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  full_sweep_kernel<<<(unsigned)blocks, 256, 0, s>>>(b, m, idx, tb, tiv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_weights(const double* nu, const float* w, int64_t m, int couple, float* scale,
                            double* rho, int* bad, cudaStream_t s) {
   int64_t blocks = (m + 255) / 256;

@@ -145,6 +145,12 @@ class Solver:
                                     ctypes.byref(f2), ctypes.byref(al)), "rska_sigma_max2")
         return s2.value, f2.value, al.value
 
+    def linearized_bregman(self, K: int, step: float):
+        """K iterations of z -= step A^T (A x - b), x = S_lam(z) (the eta ->
+        infinity limit of RSKA; the paper's step is 1/sigma_max(A)^2)."""
+        check(lib().rska_linearized_bregman(self._h, int(K), float(step)),
+              "rska_linearized_bregman")
+
     def set_weights(self, w=None, couple: bool = False):
         """Row weights w_i of eq. (rska) (Sec. 5, v3: couple=False keeps
         p_i ~ ||a_i||^2; v4: couple=True samples p_i ~ ||a_i||^2 / w_i).

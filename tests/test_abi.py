@@ -86,6 +86,7 @@ def test_null_context_is_rejected(L):
     assert L.rska_set_weights(None, None, 2) == 1
     s2 = ctypes.c_double()
     assert L.rska_sigma_max2(None, 10, 0, ctypes.byref(s2), None, None) == 1
+    assert L.rska_linearized_bregman(None, 1, 1.0) == 1
 
 
 @pytest.mark.parametrize("args", [
