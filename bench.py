@@ -421,11 +421,30 @@ def run_gpu(args):
     # the step of Corollary 1 from a power-iteration estimate of sigma_max^2
     # (outside the timed region), beside the Marchenko-Pastur value the
     # workload uses
-    step = None
+    step = lb = None
     if not args.skip_plain:
         s2, f2, al = sol.sigma_max2(30, 0)
         step = {"t_used": T_STEP, "t_rule": "alpha*(eta) with sigma_max^2 ~ (sqrt m + sqrt n)^2",
                 "power_iteration": {"iters": 30, "sigma_max2": s2, "fro2": f2, "alpha_star": al}}
+        # the eta -> infinity limit: linearized Bregman, one full sweep of A per
+        # iteration; per-iteration time from the difference of two runs (the
+        # call is synchronous and allocates its index list), and the iteration
+        # complexity factor H(eta) = 1/L(alpha^*) of the mini-batch remark
+        walls = []
+        for kk in (5, 15):
+            torch.cuda.synchronize(dev)
+            c0 = time.perf_counter()
+            sol.linearized_bregman(kk, 1.0 / s2)
+            walls.append(time.perf_counter() - c0)
+        lb_us = (walls[1] - walls[0]) / 10 * 1e6
+        srat = s2 / f2
+        H = lambda e: 2.0 / e + 2.0 * (1.0 - 1.0 / e) * srat
+        rska_us = total_ms / args.steps / ITERS * 1000.0
+        lb = {"us_per_iter": lb_us, "rows_per_iter": M,
+              "rska_us_per_iter": rska_us,
+              "H": {str(e): H(e) for e in (1, 16, 64, 256, 1024)} | {"inf": 2.0 * srat},
+              "predicted_time_ratio_rska_over_lb":
+                  (H(ETA) * rska_us) / (2.0 * srat * lb_us) if lb_us > 0 else None}
     sol.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -437,7 +456,7 @@ def run_gpu(args):
                 "accuracy": {"rel_residual": rel_res, "rel_error": rel_err,
                              "after_iterations": ITERS},
                 "plain_rska_gpu": plain, "time_to_accuracy": tta, "eta_sweep": sweep,
-                "step": step}
+                "step": step, "linearized_bregman": lb}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
