@@ -122,3 +122,50 @@ def test_batched_rejects_bad_problems(env):
         BatchSolver(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), a_off, m, n, lda,
                     b_off, 1.0, 8, 4.0, 1)
     assert e.value.code == 7
+
+
+def test_batched_limits(env):
+    """n = 2688 (the largest row a warp keeps in registers) and eta = 448 (the
+    most rows of one iteration the index ring holds), with small and ragged
+    problems in the same launch."""
+    torch, orc, BatchSolver = env
+    probs = make_batch([(3000, 2688), (500, 2688), (449, 17), (900, 450), (5, 3)], 6000)
+    A, a_off, m, n, lda, b, b_off = pack_batch(probs)
+    lam, eta, t, seed, K = 0.5, 448, 1.0, 3, 15  # t = 1 is admissible for every shape
+    with BatchSolver(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), a_off, m, n, lda,
+                     b_off, lam, eta, t, seed) as bs:
+        bs.solve(K, tol=0.0)
+        iters, rr = bs.results()
+        x, z = [v.cpu().numpy().astype(np.float64) for v in bs.get_x()]
+        xo = bs.x_off
+    assert np.all(iters == K)
+    for p, pr in enumerate(probs):
+        Ap = pr.A[:, :pr.n]
+        zr = orc.rska(Ap, pr.b.astype(np.float64), lam, eta, t, seed, K, problem=p)
+        assert rel(z[xo[p]:xo[p] + pr.n], zr) <= REL_TOL, (p, pr.m, pr.n)
+
+
+def test_batched_full_configuration_sampled(env):
+    """The benchmark's 4096 systems (m log-uniform in [200, 4000], n = m/2,
+    s = n/20, lambda = 1, eta = 32, t = 16) in one launch for a fixed 40
+    iterations; the four largest problems and four others checked against the
+    FP64 oracle."""
+    torch, orc, BatchSolver = env
+    from synth import batched_problem_set
+    A, a_off, m, n, lda, b, b_off, _ = batched_problem_set(4096, seed=2024)
+    lam, eta, t, seed, K = 1.0, 32, 16.0, 11, 40
+    with BatchSolver(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), a_off, m, n, lda,
+                     b_off, lam, eta, t, seed) as bs:
+        bs.solve(K, tol=0.0)
+        iters, rr = bs.results()
+        x, z = [v.cpu().numpy().astype(np.float64) for v in bs.get_x()]
+        xo = bs.x_off
+    assert np.all(iters == K)
+    order = np.argsort(np.asarray(m) * np.asarray(n))
+    check = list(order[-4:]) + [0, 1, 2047, 4095]
+    for p in check:
+        mp, np_, lp = int(m[p]), int(n[p]), int(lda[p])
+        Ap = A[int(a_off[p]):int(a_off[p]) + mp * lp].reshape(mp, lp)[:, :np_]
+        bp = b[int(b_off[p]):int(b_off[p]) + mp].astype(np.float64)
+        zr = orc.rska(np.ascontiguousarray(Ap), bp, lam, eta, t, seed, K, problem=int(p))
+        assert rel(z[xo[p]:xo[p] + np_], zr) <= REL_TOL, (p, mp, np_)

@@ -87,3 +87,32 @@ def test_unrolled_gradient_full_size_configuration(env):
     shapes = [(2048, 1024)] * 64
     run(env, shapes, nnz=50, noise=0.01, eta=64, K=200, ckpt=20, lams=[1.0] * 64,
         ts=[32.0] * 64, seed=11, check=[0, 1, 17, 31, 48, 63])
+
+
+def test_unrolled_column_form_wide_rows(env):
+    """n above the row form's 1024 (ragged widths): the column-split kernels."""
+    shapes = [(600, 1100), (300, 1501), (900, 1030)]
+    run(env, shapes, nnz=10, noise=0.01, eta=32, K=30, ckpt=10,
+        lams=[0.5, 0.3, 0.8], ts=[6.0, 3.0, 8.0], seed=21, check=range(3))
+
+
+def test_unrolled_column_form_large_eta(env):
+    """eta = 300, above the row form's 256."""
+    shapes = [(1200, 500), (900, 260)]
+    run(env, shapes, nnz=10, noise=0.0, eta=300, K=12, ckpt=4,
+        lams=[0.5, 0.2], ts=[40.0, 30.0], seed=22, check=range(2))
+
+
+def test_unrolled_row_form_limits(env):
+    """n = 1024 and eta = 256, the row form's limits."""
+    shapes = [(2048, 1024), (1500, 1024), (3000, 1000)]
+    run(env, shapes, nnz=20, noise=0.01, eta=256, K=24, ckpt=6,
+        lams=[1.0, 0.5, 1.5], ts=[60.0, 40.0, 80.0], seed=23, check=range(3))
+
+
+def test_unrolled_one_cta_per_problem(env):
+    """80 problems: more than half the SMs, so every problem runs on one CTA
+    instead of a CTA pair."""
+    shapes = [(256 + 8 * (i % 7), 128 + 4 * (i % 5)) for i in range(80)]
+    run(env, shapes, nnz=6, noise=0.01, eta=16, K=30, ckpt=10, lams=[0.2] * 80,
+        ts=[4.0] * 80, seed=24, check=[0, 13, 41, 79])
