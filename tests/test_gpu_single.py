@@ -99,6 +99,16 @@ def test_parity_against_oracle(env, name, kernel):
     assert rx <= REL_TOL and rz <= REL_TOL, (name, rx, rz, info)
 
 
+@pytest.mark.parametrize("n,kernel_expected", [(11520, 2), (11521, 1)])
+def test_row_split_width_limit(env, n, kernel_expected):
+    """n = 11520 fills every float4 column slot of the row-split kernel (6 per
+    consumer thread); one more column and the automatic choice is the
+    column-split kernel."""
+    rx, rz, info = run_case(env, 1500, n, 40, 300, 1.0, 60.0, 12, 20, noise=0.01)
+    assert info["kernel"] == kernel_expected, info
+    assert rx <= REL_TOL and rz <= REL_TOL, (n, rx, rz, info)
+
+
 @pytest.mark.parametrize("kernel", ["auto", "column"])
 def test_parity_full_size_bench_configuration(env, kernel):
     """A 20000 x 10000 Gaussian system, 200 nonzeros, 1% noise, lambda = 2,
