@@ -390,9 +390,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       bulk_wait_read();  // the grid's completion orders the global writes
     }
   } else {
-    // two rounds of 128 columns.  Round 0's z boxes (4 x 16 KB FP32) were
-    // loaded at kernel start into ZREG0; round 1's go into the freed stage
-    // buffers [0, 64 KB).  Each round updates z in place, splits x = S_lambda(z)
+    // two halves of 128 columns.  The first half's z boxes (4 x 16 KB FP32)
+    // were loaded at kernel start into ZREG0; the second half's go into the
+    // freed stage buffers [0, 64 KB).  Each half updates z in place, splits x = S_lambda(z)
     // into BF16 hi/lo boxes (2 x 16 KB each) staged in [64 KB, 128 KB), and
     // stores everything with TMA.
     unsigned char* xreg = epi + 65536;
