@@ -130,6 +130,12 @@ __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+// All but the most recent committed bulk group have finished reading their
+// shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_all_but_one() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
 // Programmatic dependent launch: wait until the preceding kernel in the
 // stream has completed and its writes are visible (returns at once for an
 // ordinary launch); let the next kernel start its prologue.
@@ -390,11 +396,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       bulk_wait_read();  // the grid's completion orders the global writes
     }
   } else {
-    // two halves of 128 columns.  The first half's z boxes (4 x 16 KB FP32)
-    // were loaded at kernel start into ZREG0; the second half's go into the
-    // freed stage buffers [0, 64 KB).  Each half updates z in place, splits x = S_lambda(z)
-    // into BF16 hi/lo boxes (2 x 16 KB each) staged in [64 KB, 128 KB), and
-    // stores everything with TMA.
+    // four quarters of 64 columns.  The z boxes of quarters 0 and 1 (FP32,
+    // 32 columns x 128 rows = 16 KB each) were loaded at kernel start into
+    // ZREG0; those of quarters 2 and 3 go into the freed stage buffers
+    // [0, 64 KB).  Each quarter updates its z in place and splits
+    // x = S_lambda(z) into one BF16 hi and one BF16 lo box (16 KB each) staged
+    // in buffer q % 2 of [64 KB, 128 KB); its TMA stores then drain while the
+    // next quarter computes, and a buffer is reused only after the stores of
+    // two quarters back have read it.
     unsigned char* xreg = epi + 65536;
     if (threadIdx.x == 0 && ok) {
       mb_expect_tx(&zbar[1], 65536u);
@@ -402,16 +411,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         tma_load_2d(epi + (size_t)b * 16384, &mapE0, n0 + 128 + 32 * b, m0, &zbar[1]);
     }
 #pragma unroll 1
-    for (int round = 0; round < 2 && ok; ++round) {
-      const int cbase = n0 + 128 * round;
-      unsigned char* zreg = (round == 0) ? smem + ZREG0 : epi;
-      const bool zok = mb_wait(&zbar[round], 0u, a.limit_ns);
-#pragma unroll 1
-      for (int cc = 0; cc < 2; ++cc) {
-        const int c = 2 * half + cc;  // 32-column chunk of this round
+    for (int q = 0; q < 4 && ok; ++q) {
+      if (q >= 2) {
+        if (threadIdx.x == 0) bulk_wait_read_all_but_one();  // quarter q - 2 has read buffer q % 2
+        __syncthreads();
+      }
+      const int cbase = n0 + 64 * q;
+      unsigned char* zq = (q < 2) ? smem + ZREG0 + (size_t)q * 32768 : epi + (size_t)(q - 2) * 32768;
+      unsigned char* xq = xreg + (size_t)(q & 1) * 32768;
+      const bool zok = mb_wait(&zbar[q >> 1], 0u, a.limit_ns);
+      {
+        const int c = half;  // this warp's 32-column chunk of the quarter
         float v[32];
-        tmem_ld32(trow + (uint32_t)(128 * round + 32 * c), v);
-        unsigned char* zb = zreg + (size_t)c * 16384;
+        tmem_ld32(trow + (uint32_t)(64 * q + 32 * c), v);
+        unsigned char* zb = zq + (size_t)c * 16384;
         uint32_t hw[16], lw[16];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -432,30 +445,30 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           lw[2 * j] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
           lw[2 * j + 1] = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
         }
-        // 32 BF16 = 4 chunks of 16 bytes at chunks 4 (c % 2) .. + 3 of box c / 2
-        unsigned char* hb = xreg + (size_t)(c >> 1) * 16384;
-        unsigned char* lb = xreg + 32768 + (size_t)(c >> 1) * 16384;
+        // 32 BF16 = 4 chunks of 16 bytes at chunks 4 c .. 4 c + 3 of the
+        // quarter's 64-column box
+        unsigned char* hb = xq;
+        unsigned char* lb = xq + 16384;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t off = sw128_off(r, 4 * (c & 1) + q);
-          *reinterpret_cast<uint4*>(hb + off) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-          *reinterpret_cast<uint4*>(lb + off) = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+        for (int qq = 0; qq < 4; ++qq) {
+          const uint32_t off = sw128_off(r, 4 * c + qq);
+          *reinterpret_cast<uint4*>(hb + off) = make_uint4(hw[4 * qq], hw[4 * qq + 1], hw[4 * qq + 2], hw[4 * qq + 3]);
+          *reinterpret_cast<uint4*>(lb + off) = make_uint4(lw[4 * qq], lw[4 * qq + 1], lw[4 * qq + 2], lw[4 * qq + 3]);
         }
       }
       if (!zok) s_err = 1;
       fence_proxy_async_smem();
       __syncthreads();
       if (threadIdx.x == 0 && s_err == 0) {
-        for (int b = 0; b < 4; ++b) tma_store_2d(&mapE0, zreg + (size_t)b * 16384, cbase + 32 * b, m0);
-        for (int b = 0; b < 2; ++b) {
-          tma_store_2d(&mapE1, xreg + (size_t)b * 16384, cbase + 64 * b, m0);
-          tma_store_2d(&mapE2, xreg + 32768 + (size_t)b * 16384, cbase + 64 * b, m0);
-        }
+        for (int b = 0; b < 2; ++b) tma_store_2d(&mapE0, zq + (size_t)b * 16384, cbase + 32 * b, m0);
+        tma_store_2d(&mapE1, xq, cbase, m0);
+        tma_store_2d(&mapE2, xq + 16384, cbase, m0);
         bulk_commit();
-        bulk_wait_read();  // the x staging boxes are reused by the next round
       }
-      __syncthreads();
     }
+    // every store has read its shared-memory source before the CTA ends
+    if (threadIdx.x == 0 && ok) bulk_wait_read();
+    __syncthreads();
   }
   if (threadIdx.x == 0 && (!ok || s_err) && nkb > 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
   // let every issued copy land before the shared memory goes away
