@@ -699,11 +699,21 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
   }
   while (W.issued < W.RS && W.issue<NZ>(c, I, lane, warp)) {
   }
+  // entries run one iteration ahead in registers: those of iteration q + 1
+  // are published at the start of iteration q (their buffer held iteration
+  // q - 1's, which every warp has left), so the rings stream iteration q + 1's
+  // rows during the whole of iteration q
+  int32_t nidx = 0;
+  float nb = 0.f, niv = 0.f;
+  if (1 < count) fetch_entry(a, p, k_begin + 1, nidx, nb, niv);
   for (int q = 0; q < count; ++q) {
     const int buf = q & 1;
-    int32_t nidx = 0;
-    float nb = 0.f, niv = 0.f;
-    if (q + 1 < count) fetch_entry(a, p, k_begin + q + 1, nidx, nb, niv);
+    if (q + 1 < count) {
+      put_entry(a, I, buf ^ 1, nidx, nb, niv);
+      if (q + 2 < count) fetch_entry(a, p, k_begin + q + 2, nidx, nb, niv);
+      __syncthreads();
+      W.allowed = q + 1;
+    }
     for (int i = 0; i < W.cw; ++i) {
       const float4* rowp = W.next<NZ>(c, I, lane, warp);
       const int s = W.s0 + W.ss * i;
@@ -738,7 +748,6 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       }
       W.advance();
     }
-    if (q + 1 < count) put_entry(a, I, buf ^ 1, nidx, nb, niv);
     float4* dcur = dsh + (size_t)buf * RW_N4;   // this step's update buffer
     float4* dnext = dsh + (size_t)(buf ^ 1) * RW_N4;
 #pragma unroll
@@ -754,8 +763,6 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     cl_sync<CL>();
-    // the next iteration's entries are visible: start its first rows now
-    W.allowed = q + 1;
     while (W.issued < W.t + W.RS && W.issue<NZ>(c, I, lane, warp)) {
     }
     const bool st = store && ((q + 1) % store_every) == 0;
@@ -842,9 +849,20 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
   WarpRows W = make_rows<NZ, CL>(a, c, ring, cnt, warp, rank);
   while (W.issued < W.RS && W.issue<NZ>(c, I, lane, warp)) {
   }
+  // entries one step ahead, published at the start of the step before (as in
+  // forward_rows)
+  int32_t nidx = 0;
+  float nb = 0.f, niv = 0.f;
+  if (1 < cnt) fetch_entry(a, p, k0 + cnt - 2, nidx, nb, niv);
   for (int q = 0; q < cnt; ++q) {
     const int k = k0 + cnt - 1 - q;
     const int buf = q & 1;
+    if (q + 1 < cnt) {
+      put_entry(a, I, buf ^ 1, nidx, nb, niv);
+      if (q + 2 < cnt) fetch_entry(a, p, k - 2, nidx, nb, niv);
+      __syncthreads();
+      W.allowed = q + 1;
+    }
     float4 xr[NZ], gr[NZ], xb[NZ];
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
@@ -853,9 +871,6 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       gr[j] = (col < n4) ? gsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
       xb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    int32_t nidx = 0;
-    float nb = 0.f, niv = 0.f;
-    if (q + 1 < cnt) fetch_entry(a, p, k - 1, nidx, nb, niv);
     for (int i = 0; i < W.cw; ++i) {
       const float4* rowp = W.next<NZ>(c, I, lane, warp);
       const int s = W.s0 + W.ss * i;
@@ -896,7 +911,6 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       }
       W.advance();
     }
-    if (q + 1 < cnt) put_entry(a, I, buf ^ 1, nidx, nb, niv);
     float4* dcur = dsh + (size_t)buf * RW_N4;
     float4* dnext = dsh + (size_t)(buf ^ 1) * RW_N4;
 #pragma unroll
@@ -911,7 +925,6 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       }
     }
     cl_sync<CL>();
-    W.allowed = q + 1;
     while (W.issued < W.t + W.RS && W.issue<NZ>(c, I, lane, warp)) {
     }
     // dL/dlambda and dL/dz_k = g + mask_k xbar; then z_{k-1} for the next step
