@@ -718,12 +718,15 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       const float4* rowp = W.next<NZ>(c, I, lane, warp);
       const int s = W.s0 + W.ss * i;
       float dp[4] = {0.f, 0.f, 0.f, 0.f};
+      float4 rv[NZ];  // the row, read once from the ring for both uses
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
+        rv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (col < n4) {
           float4 v = rowp[col];
           if (col == n4 - 1) v = mask_tail(v, col, c.n);
+          rv[j] = v;
           dp[j & 3] = fmaf(v.x, xr[j].x, dp[j & 3]);
           dp[j & 3] = fmaf(v.y, xr[j].y, dp[j & 3]);
           dp[j & 3] = fmaf(v.z, xr[j].z, dp[j & 3]);
@@ -738,8 +741,7 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
         if (col < n4) {
-          float4 v = rowp[col];
-          if (col == n4 - 1) v = mask_tail(v, col, c.n);
+          const float4 v = rv[j];
           dl[j].x = fmaf(cval, v.x, dl[j].x);
           dl[j].y = fmaf(cval, v.y, dl[j].y);
           dl[j].z = fmaf(cval, v.z, dl[j].z);
@@ -875,12 +877,15 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       const float4* rowp = W.next<NZ>(c, I, lane, warp);
       const int s = W.s0 + W.ss * i;
       float d1 = 0.f, d2 = 0.f;
+      float4 rv[NZ];  // the row, read once from the ring for both uses
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
+        rv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (col < n4) {
           float4 v = rowp[col];
           if (col == n4 - 1) v = mask_tail(v, col, c.n);
+          rv[j] = v;
           d1 += dot4(v, xr[j]);
           d2 += dot4(v, gr[j]);
         }
@@ -901,8 +906,7 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
         if (col < n4) {
-          float4 v = rowp[col];
-          if (col == n4 - 1) v = mask_tail(v, col, c.n);
+          const float4 v = rv[j];
           xb[j].x = fmaf(-us, v.x, xb[j].x);
           xb[j].y = fmaf(-us, v.y, xb[j].y);
           xb[j].z = fmaf(-us, v.z, xb[j].z);
