@@ -367,14 +367,20 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       { const int64_t pend = issued - t - 1; cp_async_wait_pending(pend < 30 ? (int)pend : 30); }
       const int64_t e = k * eta + warp + BCW * i;
       const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)slot_t * slot_bytes);
-      // four independent partial sums keep the FMA chain short
+      // four independent partial sums keep the FMA chain short; up to 16
+      // float4 per lane the row stays in registers for the update (the widest
+      // form reads it from the ring again: its registers hold x and the share)
+      constexpr bool kHold = NZ <= 16;
+      float4 rv[kHold ? NZ : 1];
       float dp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
+        if constexpr (kHold) rv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (col < n4) {
           float4 v = rowp[col];
           if (col == n4 - 1) v = mask_tail(v, col, n);
+          if constexpr (kHold) rv[j] = v;
           dp[j & 3] = fmaf(v.x, xr[j].x, dp[j & 3]);
           dp[j & 3] = fmaf(v.y, xr[j].y, dp[j & 3]);
           dp[j & 3] = fmaf(v.z, xr[j].z, dp[j & 3]);
@@ -393,8 +399,13 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
         if (col < n4) {
-          float4 v = rowp[col];
-          if (col == n4 - 1) v = mask_tail(v, col, n);
+          float4 v;
+          if constexpr (kHold) {
+            v = rv[j];
+          } else {
+            v = rowp[col];
+            if (col == n4 - 1) v = mask_tail(v, col, n);
+          }
           dl[j].x = fmaf(cval, v.x, dl[j].x);
           dl[j].y = fmaf(cval, v.y, dl[j].y);
           dl[j].z = fmaf(cval, v.z, dl[j].z);
