@@ -514,8 +514,10 @@ __global__ void unrolled_alias_kernel(UnrolledArgs a, const double* nu, double* 
 constexpr int RW_ETA = 256;                              // largest eta of the row form
 constexpr int RW_N4 = 256;                               // largest n/4 of the row form
 constexpr size_t RW_VEC = (size_t)RW_N4 * 16;            // bytes of one vector
-constexpr size_t RW_RING = 22 * 1024;                    // row slots of one warp
-constexpr size_t RW_SMEM = 5 * RW_VEC + UW * RW_RING;    // z, x, two update buffers, g, rings
+constexpr size_t RW_RING = 21 * 1024;                    // row slots of one warp
+constexpr int RW_NVEC = 5 + (UW - 1);                    // z, x, two update buffers, g, and
+                                                         // the update shares of warps 1..UW-1
+constexpr size_t RW_SMEM = RW_NVEC * RW_VEC + UW * RW_RING;
 constexpr int RW_RS_MAX = 8;
 
 struct RowIdx {
@@ -673,6 +675,36 @@ __device__ __forceinline__ WarpRows make_rows(const UnrolledArgs& a, const ProbC
   return w;
 }
 
+// The update of one step from the warps' shares, without shared-memory
+// atomics: warp 0 stores its share into `dcur`, warps 1.. into their own
+// buffers `wsh`; after a block barrier every thread sums its columns in warp
+// order into `dcur`.  The caller's cluster barrier then publishes `dcur` to
+// the peer CTA.
+template <int NZ>
+__device__ __forceinline__ void merge_shares(float4 (&dl)[NZ], float4* dcur, float4* wsh, int n4) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4* dst = (warp == 0) ? dcur : wsh + (size_t)(warp - 1) * RW_N4;
+#pragma unroll
+  for (int j = 0; j < NZ; ++j) {
+    const int col = lane + 32 * j;
+    if (col < n4) dst[col] = dl[j];
+    dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int c4 = tid; c4 < n4; c4 += UT) {
+    float4 s = dcur[c4];
+#pragma unroll
+    for (int w = 1; w < UW; ++w) {
+      const float4 v = wsh[(size_t)(w - 1) * RW_N4 + c4];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+    dcur[c4] = s;
+  }
+}
+
 // `count` forward iterations k_begin .. k_begin+count-1 of problem p.  On
 // entry zsh/xsh hold z and x = S(z), both update buffers (dsh, dsh + RW_N4)
 // are zero and I buffer 0 holds the entries of iteration k_begin, all visible
@@ -684,7 +716,7 @@ __device__ __forceinline__ WarpRows make_rows(const UnrolledArgs& a, const ProbC
 // update buffer of the last step is not zero.
 template <int NZ, int CL>
 __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, RowIdx& I,
-                             float4* zsh, float4* xsh, float4* dsh, unsigned char* ring,
+                             float4* zsh, float4* xsh, float4* dsh, float4* wsh, unsigned char* ring,
                              int k_begin, int count, float* store_base, int store_every,
                              bool store, int rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -752,18 +784,7 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
     }
     float4* dcur = dsh + (size_t)buf * RW_N4;   // this step's update buffer
     float4* dnext = dsh + (size_t)(buf ^ 1) * RW_N4;
-#pragma unroll
-    for (int j = 0; j < NZ; ++j) {
-      const int col = lane + 32 * j;
-      if (col < n4) {
-        float* dp = reinterpret_cast<float*>(dcur + col);
-        atomicAdd(dp + 0, dl[j].x);
-        atomicAdd(dp + 1, dl[j].y);
-        atomicAdd(dp + 2, dl[j].z);
-        atomicAdd(dp + 3, dl[j].w);
-      }
-      dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    merge_shares<NZ>(dl, dcur, wsh, n4);
     cl_sync<CL>();
     while (W.issued < W.t + W.RS && W.issue<NZ>(c, I, lane, warp)) {
     }
@@ -808,7 +829,8 @@ __global__ void __launch_bounds__(UT, 1) unrolled_fwd_rows_kernel(UnrolledArgs a
   float4* zsh = reinterpret_cast<float4*>(smem);
   float4* xsh = zsh + RW_N4;
   float4* dsh = xsh + RW_N4;  // two buffers
-  unsigned char* ring = smem + 5 * RW_VEC + (size_t)warp * RW_RING;
+  float4* wsh = zsh + 5 * RW_N4;  // update shares of warps 1..UW-1
+  unsigned char* ring = smem + RW_NVEC * RW_VEC + (size_t)warp * RW_RING;
   const int nck = a.K / a.ckpt;
   for (int p = blockIdx.x / CL; p < a.P; p += gridDim.x / CL) {
     const ProbCtx c = prob_ctx(a, p);
@@ -828,7 +850,7 @@ __global__ void __launch_bounds__(UT, 1) unrolled_fwd_rows_kernel(UnrolledArgs a
       put_entry(a, I, 0, idx, bv, iv);
     }
     cl_sync<CL>();
-    forward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, ring, 0, a.K, ck, a.ckpt, rank == 0, rank);
+    forward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, wsh, ring, 0, a.K, ck, a.ckpt, rank == 0, rank);
     if (rank == 0) {
       float4* xo = reinterpret_cast<float4*>(a.x_out + a.x_off[p]);
       for (int c4 = tid; c4 < n4; c4 += UT) xo[c4] = xsh[c4];
@@ -843,7 +865,7 @@ __global__ void __launch_bounds__(UT, 1) unrolled_fwd_rows_kernel(UnrolledArgs a
 // entries.  seg[j] holds z_{k0+j}.  On exit gsh holds dL/dz_{k0}.
 template <int NZ, int CL>
 __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, RowIdx& I,
-                              float4* zsh, float4* xsh, float4* dsh, float4* gsh,
+                              float4* zsh, float4* xsh, float4* dsh, float4* gsh, float4* wsh,
                               unsigned char* ring, int k0, int cnt, const float* seg, float* gbp,
                               float& glam, float& gt, int rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -917,17 +939,7 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
     }
     float4* dcur = dsh + (size_t)buf * RW_N4;
     float4* dnext = dsh + (size_t)(buf ^ 1) * RW_N4;
-#pragma unroll
-    for (int j = 0; j < NZ; ++j) {
-      const int col = lane + 32 * j;
-      if (col < n4) {
-        float* dp = reinterpret_cast<float*>(dcur + col);
-        atomicAdd(dp + 0, xb[j].x);
-        atomicAdd(dp + 1, xb[j].y);
-        atomicAdd(dp + 2, xb[j].z);
-        atomicAdd(dp + 3, xb[j].w);
-      }
-    }
+    merge_shares<NZ>(xb, dcur, wsh, n4);
     cl_sync<CL>();
     while (W.issued < W.t + W.RS && W.issue<NZ>(c, I, lane, warp)) {
     }
@@ -977,7 +989,8 @@ __global__ void __launch_bounds__(UT, 1) unrolled_bwd_rows_kernel(UnrolledArgs a
   float4* xsh = zsh + RW_N4;
   float4* dsh = xsh + RW_N4;       // two buffers
   float4* gsh = dsh + 2 * RW_N4;
-  unsigned char* ring = smem + 5 * RW_VEC + (size_t)warp * RW_RING;
+  float4* wsh = zsh + 5 * RW_N4;  // update shares of warps 1..UW-1
+  unsigned char* ring = smem + RW_NVEC * RW_VEC + (size_t)warp * RW_RING;
   const int nck = a.K / a.ckpt;
   for (int p = blockIdx.x / CL; p < a.P; p += gridDim.x / CL) {
     const ProbCtx c = prob_ctx(a, p);
@@ -1017,7 +1030,7 @@ __global__ void __launch_bounds__(UT, 1) unrolled_bwd_rows_kernel(UnrolledArgs a
         put_entry(a, I, 0, idx, bv, iv);
       }
       cl_sync<CL>();
-      forward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, ring, k0, a.ckpt - 1, seg, 1, true, rank);
+      forward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, wsh, ring, k0, a.ckpt - 1, seg, 1, true, rank);
       // reverse sweep (zsh/xsh hold z_{k0+ckpt-1})
       {
         int32_t idx = 0;
@@ -1030,7 +1043,7 @@ __global__ void __launch_bounds__(UT, 1) unrolled_bwd_rows_kernel(UnrolledArgs a
         dsh[RW_N4 + c4] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       cl_sync<CL>();
-      backward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, gsh, ring, k0, a.ckpt, seg, gbp, glam, gt,
+      backward_rows<NZ, CL>(a, c, p, I, zsh, xsh, dsh, gsh, wsh, ring, k0, a.ckpt, seg, gbp, glam, gt,
                             rank);
     }
     // reduce dL/dlambda over the CTA and dL/dt over the warps and the cluster
