@@ -810,13 +810,19 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       dnext[c4] = make_float4(0.f, 0.f, 0.f, 0.f);  // read by the peer one step ago
       if (st) dst[c4] = zv;
     }
-    cl_sync<CL>();
+    // only this CTA's warps must see the new z and x: the peer's reads of
+    // this step's update buffer are ordered before its next overwrite (two
+    // steps on) by the next step's cluster barrier
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
       const int col = lane + 32 * j;
       xr[j] = (col < n4) ? xsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+  // the peer has finished reading the last step's update buffer before the
+  // caller reuses the shared memory
+  cl_sync<CL>();
   ucp_wait_all();
 }
 
@@ -972,8 +978,9 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
         xsh[c4] = soft_shrink4(zp, c.lam);
       }
     }
-    cl_sync<CL>();
+    __syncthreads();  // as in forward_rows: the next step's cluster barrier orders the peer
   }
+  cl_sync<CL>();  // the peer has finished reading the last step's update buffer
   ucp_wait_all();
 }
 
