@@ -54,7 +54,9 @@ constexpr int BRS_MAX = 16;      // ring slots per warp
 constexpr size_t BVEC = (size_t)BMAXNZ * 32 * 16;       // bytes of z, x or the update
 constexpr size_t BRING_OFF = 3 * BVEC;                  // rows start after z, x, update
 constexpr size_t BRING_WARP = 24 * 1024;                // row slots of one consumer warp
-constexpr size_t BSMEM = BRING_OFF + BCW * BRING_WARP;  // dynamic shared memory per CTA
+constexpr int BHOLDNZ = 16;      // rows up to this many float4 per lane stay in registers
+constexpr size_t BEXT_OFF = BRING_OFF + BCW * BRING_WARP;  // two more update-share buffers
+constexpr size_t BSMEM = BEXT_OFF + 2 * (size_t)BHOLDNZ * 32 * 16;  // dynamic shared memory per CTA
 constexpr int BMAX_ETA = 448;    // rows of one iteration stay inside the index ring
 static_assert(BRING_WARP / BVEC >= 2, "every warp holds two of the widest rows");
 static_assert(BMAX_ETA + 32 <= BIR, "an iteration's rows fit the index ring");
@@ -98,6 +100,19 @@ __device__ __forceinline__ uint32_t su32(const void* p) {
 
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(BC) : "memory");
+}
+
+// Pair barriers between consumer warps w and w + 3 (w = 1..3; named barriers
+// 2..4, 64 threads): the writer (w) arrives, the reader (w + 3) waits.
+__device__ __forceinline__ void pair_arrive(int warp) {
+  if (warp == 1) asm volatile("bar.arrive 2, 64;" ::: "memory");
+  else if (warp == 2) asm volatile("bar.arrive 3, 64;" ::: "memory");
+  else asm volatile("bar.arrive 4, 64;" ::: "memory");
+}
+__device__ __forceinline__ void pair_wait(int warp) {
+  if (warp == 4) asm volatile("bar.sync 2, 64;" ::: "memory");
+  else if (warp == 5) asm volatile("bar.sync 3, 64;" ::: "memory");
+  else asm volatile("bar.sync 4, 64;" ::: "memory");
 }
 
 __device__ __forceinline__ int consumer_sync_or(int pred) {
@@ -289,6 +304,7 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
   float4* zsh = reinterpret_cast<float4*>(smem);
   float4* xsh = zsh + BMAXNZ * 32;
   float4* dsh = xsh + BMAXNZ * 32;
+  float4* ext = reinterpret_cast<float4*>(smem + BEXT_OFF);  // 2 x BHOLDNZ * 32 float4
   const uint32_t slot_bytes = (uint32_t)n4 * 16u;
   const int RS = min(BRS_MAX, (int)(BRING_WARP / slot_bytes));  // ring slots of this warp
   unsigned char* ring = smem + BRING_OFF + (size_t)warp * BRING_WARP;
@@ -370,7 +386,7 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       // four independent partial sums keep the FMA chain short; up to 16
       // float4 per lane the row stays in registers for the update (the widest
       // form reads it from the ring again: its registers hold x and the share)
-      constexpr bool kHold = NZ <= 16;
+      constexpr bool kHold = NZ <= BHOLDNZ;
       float4 rv[kHold ? NZ : 1];
       float dp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -415,17 +431,42 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
     }
     // every consumer thread reaches the barriers below whether it failed or not
     // ---- end of iteration k: update = sum of the warps' shares ----
+    if constexpr (NZ <= BHOLDNZ) {
+      // no shared-memory atomics: warps 0..3 store their shares into four
+      // buffers (the update buffer, the x buffer -- rewritten by the update
+      // below -- and two more); warps 4..6 then add theirs into buffers 1..3,
+      // each after a pair barrier with that buffer's writer; the update loop
+      // sums the four buffers in order
+      float4* dst = (warp == 0) ? dsh : (warp == 1 || warp == 4) ? xsh
+                    : (warp == 2 || warp == 5) ? ext : ext + BHOLDNZ * 32;
+      if (warp >= 4) pair_wait(warp);
 #pragma unroll
-    for (int j = 0; j < NZ; ++j) {
-      const int col = lane + 32 * j;
-      if (col < n4) {
-        float* dp = reinterpret_cast<float*>(dsh + col);
-        atomicAdd(dp + 0, dl[j].x);
-        atomicAdd(dp + 1, dl[j].y);
-        atomicAdd(dp + 2, dl[j].z);
-        atomicAdd(dp + 3, dl[j].w);
+      for (int j = 0; j < NZ; ++j) {
+        const int col = lane + 32 * j;
+        if (col < n4) {
+          if (warp >= 4) {
+            const float4 o = dst[col];
+            dst[col] = make_float4(o.x + dl[j].x, o.y + dl[j].y, o.z + dl[j].z, o.w + dl[j].w);
+          } else {
+            dst[col] = dl[j];
+          }
+        }
+        dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (warp >= 1 && warp <= 3) pair_arrive(warp);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        const int col = lane + 32 * j;
+        if (col < n4) {
+          float* dp = reinterpret_cast<float*>(dsh + col);
+          atomicAdd(dp + 0, dl[j].x);
+          atomicAdd(dp + 1, dl[j].y);
+          atomicAdd(dp + 2, dl[j].z);
+          atomicAdd(dp + 3, dl[j].w);
+        }
+        dl[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
     if (consumer_sync_or(fail ? 1 : 0)) {
       fail = true;
@@ -434,7 +475,12 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
     if (tid == 0) S.used = (k + 1) * (int64_t)eta;
     for (int c4 = tid; c4 < n4; c4 += BC) {
       float4 zv = zsh[c4];
-      const float4 dv = dsh[c4];
+      float4 dv = dsh[c4];
+      if constexpr (NZ <= BHOLDNZ) {
+        const float4 d1 = xsh[c4], d2 = ext[c4], d3 = ext[BHOLDNZ * 32 + c4];
+        dv = make_float4(((dv.x + d1.x) + d2.x) + d3.x, ((dv.y + d1.y) + d2.y) + d3.y,
+                         ((dv.z + d1.z) + d2.z) + d3.z, ((dv.w + d1.w) + d2.w) + d3.w);
+      }
       zv.x -= dv.x;
       zv.y -= dv.y;
       zv.z -= dv.z;
