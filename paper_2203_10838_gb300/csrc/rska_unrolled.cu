@@ -675,6 +675,23 @@ __device__ __forceinline__ WarpRows make_rows(const UnrolledArgs& a, const ProbC
   return w;
 }
 
+// One lane's columns of a landed row, copied to registers (its ring slot may
+// then be refilled).
+template <int NZ>
+__device__ __forceinline__ void load_row(const float4* rowp, float4 (&r)[NZ], int lane, int n4,
+                                         int64_t n) {
+#pragma unroll
+  for (int j = 0; j < NZ; ++j) {
+    const int col = lane + 32 * j;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (col < n4) {
+      v = rowp[col];
+      if (col == n4 - 1) v = mask_tail(v, col, n);
+    }
+    r[j] = v;
+  }
+}
+
 // The update of one step from the warps' shares, without shared-memory
 // atomics: warp 0 stores its share into `dcur`, warps 1.. into their own
 // buffers `wsh`; after a block barrier every thread sums its columns in warp
@@ -746,41 +763,62 @@ __device__ void forward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Row
       __syncthreads();
       W.allowed = q + 1;
     }
-    for (int i = 0; i < W.cw; ++i) {
-      const float4* rowp = W.next<NZ>(c, I, lane, warp);
-      const int s = W.s0 + W.ss * i;
-      float dp[4] = {0.f, 0.f, 0.f, 0.f};
-      float4 rv[NZ];  // the row, read once from the ring for both uses
-#pragma unroll
-      for (int j = 0; j < NZ; ++j) {
-        const int col = lane + 32 * j;
-        rv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (col < n4) {
-          float4 v = rowp[col];
-          if (col == n4 - 1) v = mask_tail(v, col, c.n);
-          rv[j] = v;
-          dp[j & 3] = fmaf(v.x, xr[j].x, dp[j & 3]);
-          dp[j & 3] = fmaf(v.y, xr[j].y, dp[j & 3]);
-          dp[j & 3] = fmaf(v.z, xr[j].z, dp[j & 3]);
-          dp[j & 3] = fmaf(v.w, xr[j].w, dp[j & 3]);
-        }
-      }
-      float d = (dp[0] + dp[1]) + (dp[2] + dp[3]);
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      const float cval = c.coef * ((d - I.b[buf][s]) * I.iv[buf][s]);
-#pragma unroll
-      for (int j = 0; j < NZ; ++j) {
-        const int col = lane + 32 * j;
-        if (col < n4) {
-          const float4 v = rv[j];
-          dl[j].x = fmaf(cval, v.x, dl[j].x);
-          dl[j].y = fmaf(cval, v.y, dl[j].y);
-          dl[j].z = fmaf(cval, v.z, dl[j].z);
-          dl[j].w = fmaf(cval, v.w, dl[j].w);
-        }
-      }
+    // rows in pairs: both are copied to registers as they land, then their
+    // dots, reductions and updates interleave (two independent chains)
+    for (int i = 0; i < W.cw; i += 2) {
+      const bool two = (i + 1 < W.cw);
+      float4 r0[NZ], r1[NZ];
+      load_row<NZ>(W.next<NZ>(c, I, lane, warp), r0, lane, n4, c.n);
       W.advance();
+      if (two) {
+        load_row<NZ>(W.next<NZ>(c, I, lane, warp), r1, lane, n4, c.n);
+        W.advance();
+      } else {
+#pragma unroll
+        for (int j = 0; j < NZ; ++j) r1[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        p0[j & 3] = fmaf(r0[j].x, xr[j].x, p0[j & 3]);
+        p1[j & 3] = fmaf(r1[j].x, xr[j].x, p1[j & 3]);
+        p0[j & 3] = fmaf(r0[j].y, xr[j].y, p0[j & 3]);
+        p1[j & 3] = fmaf(r1[j].y, xr[j].y, p1[j & 3]);
+        p0[j & 3] = fmaf(r0[j].z, xr[j].z, p0[j & 3]);
+        p1[j & 3] = fmaf(r1[j].z, xr[j].z, p1[j & 3]);
+        p0[j & 3] = fmaf(r0[j].w, xr[j].w, p0[j & 3]);
+        p1[j & 3] = fmaf(r1[j].w, xr[j].w, p1[j & 3]);
+      }
+      float d0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
+      float d1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      }
+      const int s0 = W.s0 + W.ss * i;
+      const float cv0 = c.coef * ((d0 - I.b[buf][s0]) * I.iv[buf][s0]);
+      float cv1 = 0.f;
+      if (two) {
+        const int s1 = s0 + W.ss;
+        cv1 = c.coef * ((d1 - I.b[buf][s1]) * I.iv[buf][s1]);
+      }
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) {
+        dl[j].x = fmaf(cv0, r0[j].x, dl[j].x);
+        dl[j].y = fmaf(cv0, r0[j].y, dl[j].y);
+        dl[j].z = fmaf(cv0, r0[j].z, dl[j].z);
+        dl[j].w = fmaf(cv0, r0[j].w, dl[j].w);
+      }
+      if (two) {
+#pragma unroll
+        for (int j = 0; j < NZ; ++j) {
+          dl[j].x = fmaf(cv1, r1[j].x, dl[j].x);
+          dl[j].y = fmaf(cv1, r1[j].y, dl[j].y);
+          dl[j].z = fmaf(cv1, r1[j].z, dl[j].z);
+          dl[j].w = fmaf(cv1, r1[j].w, dl[j].w);
+        }
+      }
     }
     float4* dcur = dsh + (size_t)buf * RW_N4;   // this step's update buffer
     float4* dnext = dsh + (size_t)(buf ^ 1) * RW_N4;
@@ -901,47 +939,71 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       gr[j] = (col < n4) ? gsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
       xb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int i = 0; i < W.cw; ++i) {
-      const float4* rowp = W.next<NZ>(c, I, lane, warp);
-      const int s = W.s0 + W.ss * i;
-      float d1 = 0.f, d2 = 0.f;
-      float4 rv[NZ];  // the row, read once from the ring for both uses
+    // rows in pairs, as in forward_rows
+    for (int i = 0; i < W.cw; i += 2) {
+      const bool two = (i + 1 < W.cw);
+      float4 r0[NZ], r1[NZ];
+      load_row<NZ>(W.next<NZ>(c, I, lane, warp), r0, lane, n4, c.n);
+      W.advance();
+      if (two) {
+        load_row<NZ>(W.next<NZ>(c, I, lane, warp), r1, lane, n4, c.n);
+        W.advance();
+      } else {
+#pragma unroll
+        for (int j = 0; j < NZ; ++j) r1[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;  // <a, x>, <a, g> of the two rows
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
-        const int col = lane + 32 * j;
-        rv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (col < n4) {
-          float4 v = rowp[col];
-          if (col == n4 - 1) v = mask_tail(v, col, c.n);
-          rv[j] = v;
-          d1 += dot4(v, xr[j]);
-          d2 += dot4(v, gr[j]);
-        }
+        a1 += dot4(r0[j], xr[j]);
+        b1 += dot4(r1[j], xr[j]);
+        a2 += dot4(r0[j], gr[j]);
+        b2 += dot4(r1[j], gr[j]);
       }
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
-        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
       }
-      const float rs = d1 - I.b[buf][s];
-      const float ivs = I.iv[buf][s];
-      const float us = c.coef * d2 * ivs;
-      if (lane == 0) {
-        atomicAdd(gbp + I.idx[buf][s], us);
-        gt -= rs * ivs * d2 / (float)a.eta;
+      const int s0 = W.s0 + W.ss * i;
+      const int s1 = s0 + W.ss;
+      float u0, u1 = 0.f;
+      {
+        const float rs = a1 - I.b[buf][s0];
+        const float ivs = I.iv[buf][s0];
+        u0 = c.coef * a2 * ivs;
+        if (lane == 0) {
+          atomicAdd(gbp + I.idx[buf][s0], u0);
+          gt -= rs * ivs * a2 / (float)a.eta;
+        }
+      }
+      if (two) {
+        const float rs = b1 - I.b[buf][s1];
+        const float ivs = I.iv[buf][s1];
+        u1 = c.coef * b2 * ivs;
+        if (lane == 0) {
+          atomicAdd(gbp + I.idx[buf][s1], u1);
+          gt -= rs * ivs * b2 / (float)a.eta;
+        }
       }
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
-        const int col = lane + 32 * j;
-        if (col < n4) {
-          const float4 v = rv[j];
-          xb[j].x = fmaf(-us, v.x, xb[j].x);
-          xb[j].y = fmaf(-us, v.y, xb[j].y);
-          xb[j].z = fmaf(-us, v.z, xb[j].z);
-          xb[j].w = fmaf(-us, v.w, xb[j].w);
+        xb[j].x = fmaf(-u0, r0[j].x, xb[j].x);
+        xb[j].y = fmaf(-u0, r0[j].y, xb[j].y);
+        xb[j].z = fmaf(-u0, r0[j].z, xb[j].z);
+        xb[j].w = fmaf(-u0, r0[j].w, xb[j].w);
+      }
+      if (two) {
+#pragma unroll
+        for (int j = 0; j < NZ; ++j) {
+          xb[j].x = fmaf(-u1, r1[j].x, xb[j].x);
+          xb[j].y = fmaf(-u1, r1[j].y, xb[j].y);
+          xb[j].z = fmaf(-u1, r1[j].z, xb[j].z);
+          xb[j].w = fmaf(-u1, r1[j].w, xb[j].w);
         }
       }
-      W.advance();
     }
     float4* dcur = dsh + (size_t)buf * RW_N4;
     float4* dnext = dsh + (size_t)(buf ^ 1) * RW_N4;
