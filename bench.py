@@ -320,34 +320,32 @@ def run_gpu(args):
     e2e_steps = 0 if args.skip_e2e else max(2, min(args.steps, 5))
     torch.cuda.synchronize(dev)
     x_host = torch.empty(N, dtype=torch.float32).pin_memory()
-    parts = {"h2d_ms": 0.0, "setup_ms": 0.0, "solve_ms": 0.0, "d2h_and_teardown_ms": 0.0}
+    # rska_setup_host takes the pinned host buffers: the library copies A in row
+    # chunks while the row norms and the sum of W run on the landed chunks
+    parts = {"setup_with_h2d_ms": 0.0, "solve_ms": 0.0, "d2h_and_teardown_ms": 0.0}
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(stream)
-        Ad = A_host.to(dev, non_blocking=True)
-        bd = b_host.to(dev, non_blocking=True)
-        ev[1].record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         c_setup = time.perf_counter()
-        with Solver(Ad, bd, LAM, ETA, T_STEP, SEED, n=N, stream=stream) as s2:
+        with Solver(A_host, b_host, LAM, ETA, T_STEP, SEED, n=N, stream=stream) as s2:
             setup_host = time.perf_counter() - c_setup
-            ev[2].record(stream)
+            ev[0].record(stream)
             s2.solve(ITERS)
-            ev[3].record(stream)
+            ev[1].record(stream)
             xd, _ = s2.get_x()
             x_host.copy_(xd, non_blocking=True)
         c_end = time.perf_counter()
         torch.cuda.synchronize(dev)
-        parts["h2d_ms"] += ev[0].elapsed_time(ev[1])
-        parts["setup_ms"] += setup_host * 1000.0
-        parts["solve_ms"] += ev[2].elapsed_time(ev[3])
+        parts["setup_with_h2d_ms"] += setup_host * 1000.0
+        parts["solve_ms"] += ev[0].elapsed_time(ev[1])
         parts["d2h_and_teardown_ms"] += (time.perf_counter() - c_end) * 1000.0
     if e2e_steps:
         e2e_s = (time.perf_counter() - e0) / e2e_steps
         e2e = {"value": ETA * ITERS * world / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(A_host.numel() * 4 + b_host.numel() * 4),
                "d2h_bytes_per_step": int(N * 4),
-               "includes": "H2D of A and b, setup (FP64 norms + alias table), solve, D2H of x",
+               "includes": "rska_setup_host from pinned host A and b (H2D overlapped with the "
+                           "FP64 norms and the sum of W, then the alias table), solve, D2H of x",
                "parts_ms_per_step": {k: v / e2e_steps for k, v in parts.items()}}
 
     # plain per-iteration PyTorch RSKA on the same GPU (comparator)

@@ -84,6 +84,22 @@ int rska_setup(rska_ctx **out, const float *A, int64_t m, int64_t n, int64_t lda
                void *stream);
 
 /*
+ * rska_setup_host -- HOST: rska_setup for host buffers.  A_host (m x lda
+ * floats, row-major) and b_host (m floats) are host memory, read during the
+ * call and not kept; the library allocates the device copies (freed by
+ * rska_destroy).  A is copied in row chunks on a second stream while the row
+ * norms of each landed chunk and the ascending FP64 sum W = sum_i ||a_i||^2 of
+ * the alias construction run on `cuda_stream`, so the copy, the norms and the
+ * sum overlap (with pinned host memory; pageable memory is copied without
+ * overlap).  Tables, indices and iterates are identical to rska_setup's for
+ * the same values.  Same argument rules and errors as rska_setup (no
+ * alignment rule on A_host); synchronous.
+ */
+int rska_setup_host(rska_ctx **out, const float *A_host, int64_t m, int64_t n, int64_t lda,
+                    const float *b_host, float lambda, int32_t eta, float t, uint64_t seed,
+                    void *cuda_stream);
+
+/*
  * rska_solve -- run K iterations of Algorithm 1 (k -> k + K) on the context's
  * stream: per chunk of up to 2^21/eta iterations, one pre-sampling kernel
  * (tau_k, b and 1/||a||^2 for the whole chunk) and one persistent kernel

@@ -35,6 +35,9 @@ void free_all(Ctx* c) {
   cudaFree(c->z);
   cudaFree(c->x);
   cudaFree(c->racc);
+  cudaFree(c->A_own);
+  cudaFree(c->b_own);
+  c->A_own = c->b_own = nullptr;
   cudaFree(c->bar);
   cudaFree(c->status);
   cudaFree(c->kdev);
@@ -130,36 +133,18 @@ rska::SolveArgs solve_args(Ctx* c, int64_t K, const int* stop) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-const char* rska_strerror(int code) {
-  switch (code) {
-    case RSKA_OK: return "ok";
-    case RSKA_EINVAL: return "invalid argument";
-    case RSKA_EZEROROW: return "matrix has a zero row";
-    case RSKA_ENONFINITE: return "matrix or right-hand side holds Inf or NaN";
-    case RSKA_ENOMEM: return "device allocation failed";
-    case RSKA_ECUDA: return "CUDA runtime error";
-    case RSKA_ETIMEOUT: return "device-side wait timed out";
-    case RSKA_EUNSUPPORTED: return "problem outside this build's limits";
-    default: return "unknown error";
-  }
-}
-
-int rska_setup(rska_ctx** out, const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
-               float lambda, int32_t eta, float t, uint64_t seed, void* stream) {
-  if (out == nullptr) return RSKA_EINVAL;
-  *out = nullptr;
-  if (A == nullptr || b == nullptr || m < 1 || n < 1 || lda < n || (lda % 4) != 0 ||
-      (reinterpret_cast<uintptr_t>(A) % 16) != 0 || m > 0x7fffffffLL || eta < 1 ||
-      eta > rska::kMaxEta || !(lambda >= 0.f) || !std::isfinite(lambda) || !(t > 0.f) ||
-      !std::isfinite(t))
-    return RSKA_EINVAL;
+// rska_setup and rska_setup_host: with A_host set, the library allocates the
+// device copies of A and b and overlaps their host-to-device copy (row
+// chunks on a second stream) with the row norms and the ascending sum of W
+// over the chunks that have landed.
+int setup_impl(rska_ctx** out, const float* A, const float* b, const float* A_host,
+               const float* b_host, int64_t m, int64_t n, int64_t lda, float lambda,
+               int32_t eta, float t, uint64_t seed, void* stream) {
   rska_ctx* h = new (std::nothrow) rska_ctx;
   if (!h) return RSKA_ENOMEM;
   Ctx* c = &h->c;
-  c->A = A;
-  c->b = b;
   c->m = m;
   c->n = n;
   c->lda = lda;
@@ -195,24 +180,69 @@ int rska_setup(rska_ctx** out, const float* A, int64_t m, int64_t n, int64_t lda
       (e = dalloc(&c->tidx, (size_t)c->chunk * eta4)) != cudaSuccess ||
       (e = dalloc(&c->tb, (size_t)c->chunk * eta4)) != cudaSuccess ||
       (e = dalloc(&c->tiv, (size_t)c->chunk * eta4)) != cudaSuccess ||
-      (e = cudaMalloc(&c->scratch, (size_t)m * (sizeof(double) + sizeof(int32_t)))) !=
-          cudaSuccess) {
+      (e = cudaMalloc(&c->scratch, (size_t)m * (sizeof(double) + sizeof(int32_t)) + 16)) !=
+          cudaSuccess ||
+      (A_host != nullptr && ((e = dalloc(&c->A_own, (size_t)m * (size_t)lda)) != cudaSuccess ||
+                             (e = dalloc(&c->b_own, m)) != cudaSuccess))) {
     free_all(c);
     delete h;
     return (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
   }
+  c->A = A_host ? c->A_own : A;
+  c->b = A_host ? c->b_own : b;
   cudaStream_t s = c->stream;
+  double* q = static_cast<double*>(c->scratch);
+  int32_t* stk = reinterpret_cast<int32_t*>(q + m);
+  double* Wdev = reinterpret_cast<double*>(stk + m + (m & 1));  // 8-byte aligned past the stack
   e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->kdev, 0, sizeof(int64_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stop, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->macc, 0, 8 * sizeof(double), s);
   if (e == cudaSuccess) e = rska::launch_fill_shrink(c->z, c->x, nullptr, n, np, lambda, s);
-  if (e == cudaSuccess)
-    e = rska::launch_row_norms(A, m, n, lda, b, c->nu, c->inv_nu, c->status, s);
-  double* q = static_cast<double*>(c->scratch);
-  int32_t* stk = reinterpret_cast<int32_t*>(q + m);
-  if (e == cudaSuccess)
-    e = rska::launch_alias_build(c->nu, m, c->thr, c->alias, q, stk, c->status, s);
+  if (A_host == nullptr) {
+    if (e == cudaSuccess)
+      e = rska::launch_row_norms(A, m, n, lda, b, c->nu, c->inv_nu, c->status, s);
+    if (e == cudaSuccess)
+      e = rska::launch_alias_build(c->nu, m, c->thr, c->alias, q, stk, c->status, s);
+  } else {
+    // b, then A in row chunks on a copy stream; each chunk's norms and its
+    // part of W follow on the context's stream as soon as it has landed
+    constexpr int kChunks = 16;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[kChunks] = {};
+    int nev = 0;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int k = 0; k < kChunks && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) ++nev;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(Wdev, 0, sizeof(double), s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->b_own, b_host, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, cs);
+    const int64_t rows = (m + kChunks - 1) / kChunks;
+    for (int k = 0; k < kChunks && e == cudaSuccess; ++k) {
+      const int64_t r0 = (int64_t)k * rows;
+      if (r0 >= m) break;
+      const int64_t r = std::min<int64_t>(rows, m - r0);
+      e = cudaMemcpyAsync(c->A_own + r0 * lda, A_host + r0 * lda,
+                          sizeof(float) * (size_t)r * (size_t)lda, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[k], cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[k], 0);
+      if (e == cudaSuccess)
+        e = rska::launch_row_norms(c->A_own + r0 * lda, r, n, lda, c->b_own + r0, c->nu + r0,
+                                   c->inv_nu + r0, c->status, s);
+      if (e == cudaSuccess) e = rska::launch_w_accumulate(c->nu + r0, r, Wdev, s);
+    }
+    if (e == cudaSuccess)
+      e = rska::launch_alias_build(c->nu, m, c->thr, c->alias, q, stk, c->status, s, Wdev);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (cs) {
+      const cudaError_t e2 = cudaStreamSynchronize(cs);
+      if (e == cudaSuccess) e = e2;
+      cudaStreamDestroy(cs);
+    }
+    for (int k = 0; k < nev; ++k) cudaEventDestroy(ev[k]);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     free_all(c);
@@ -229,6 +259,52 @@ int rska_setup(rska_ctx** out, const float* A, int64_t m, int64_t n, int64_t lda
   c->scratch = nullptr;
   *out = h;
   return RSKA_OK;
+}
+
+bool setup_args_ok(int64_t m, int64_t n, int64_t lda, int32_t eta, float lambda, float t) {
+  return m >= 1 && n >= 1 && lda >= n && (lda % 4) == 0 && m <= 0x7fffffffLL && eta >= 1 &&
+         eta <= rska::kMaxEta && lambda >= 0.f && std::isfinite(lambda) && t > 0.f &&
+         std::isfinite(t);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rska_strerror(int code) {
+  switch (code) {
+    case RSKA_OK: return "ok";
+    case RSKA_EINVAL: return "invalid argument";
+    case RSKA_EZEROROW: return "matrix has a zero row";
+    case RSKA_ENONFINITE: return "matrix or right-hand side holds Inf or NaN";
+    case RSKA_ENOMEM: return "device allocation failed";
+    case RSKA_ECUDA: return "CUDA runtime error";
+    case RSKA_ETIMEOUT: return "device-side wait timed out";
+    case RSKA_EUNSUPPORTED: return "problem outside this build's limits";
+    default: return "unknown error";
+  }
+}
+
+
+int rska_setup(rska_ctx** out, const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
+               float lambda, int32_t eta, float t, uint64_t seed, void* stream) {
+  if (out == nullptr) return RSKA_EINVAL;
+  *out = nullptr;
+  if (A == nullptr || b == nullptr || (reinterpret_cast<uintptr_t>(A) % 16) != 0 ||
+      !setup_args_ok(m, n, lda, eta, lambda, t))
+    return RSKA_EINVAL;
+  return setup_impl(out, A, b, nullptr, nullptr, m, n, lda, lambda, eta, t, seed, stream);
+}
+
+int rska_setup_host(rska_ctx** out, const float* A_host, int64_t m, int64_t n, int64_t lda,
+                    const float* b_host, float lambda, int32_t eta, float t, uint64_t seed,
+                    void* stream) {
+  if (out == nullptr) return RSKA_EINVAL;
+  *out = nullptr;
+  if (A_host == nullptr || b_host == nullptr || !setup_args_ok(m, n, lda, eta, lambda, t))
+    return RSKA_EINVAL;
+  return setup_impl(out, nullptr, nullptr, A_host, b_host, m, n, lda, lambda, eta, t, seed,
+                    stream);
 }
 
 int rska_solve(rska_ctx* h, int64_t K) {

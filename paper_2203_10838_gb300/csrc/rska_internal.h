@@ -96,6 +96,8 @@ struct Ctx {
   float* tiv = nullptr;
   int64_t chunk = 1;           // iterations per persistent launch (pre-sample capacity)
   void* scratch = nullptr;     // alias-build scratch (freed after setup)
+  float* A_own = nullptr;      // device copies made by rska_setup_host (else null)
+  float* b_own = nullptr;
   // host mirrors
   int64_t k_host = 0;
   int sticky = RSKA_OK;
@@ -117,13 +119,15 @@ size_t sigma_scratch_floats(int64_t m, int64_t n);
 cudaError_t launch_sigma_max2(const float* A, int64_t m, int64_t n, int64_t lda, const double* nu,
                               int32_t iters, uint64_t seed, float* scratch, double* d2,
                               double* rq_out, double* fro2_out, cudaStream_t s);
+cudaError_t launch_w_accumulate(const double* nu, int64_t rows, double* W, cudaStream_t s);
 cudaError_t launch_full_sweep(const float* b, int64_t m, int32_t* idx, float* tb, float* tiv,
                               cudaStream_t s);
 cudaError_t launch_weights(const double* nu, const float* w, int64_t m, int couple, float* scale,
                            double* rho, int* bad, cudaStream_t s);
 cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,
                                double* q_scratch, int32_t* stack_scratch, int* status,
-                               cudaStream_t s);
+                               cudaStream_t s,
+                               const double* Wpre = nullptr);
 cudaError_t launch_indices(const uint32_t* thr, const int32_t* alias, int64_t m, uint64_t seed,
                            uint32_t problem, int64_t k0, int64_t K, int32_t eta, int32_t* out,
                            cudaStream_t s);

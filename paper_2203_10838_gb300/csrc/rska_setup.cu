@@ -50,7 +50,7 @@ __global__ void row_norms_kernel(const float* __restrict__ A, int64_t m, int64_t
 // (stack indices as uint16, so m <= 65536); otherwise in the global scratch.
 __global__ void alias_build_kernel(const double* __restrict__ nu, int64_t m, uint32_t* thr,
                                    int32_t* alias, double* gq, int32_t* gstk, const int* status,
-                                   int use_smem) {
+                                   int use_smem, const double* Wpre) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sW;
   __shared__ int sbad;
@@ -62,7 +62,11 @@ __global__ void alias_build_kernel(const double* __restrict__ nu, int64_t m, uin
   __syncthreads();
   if (threadIdx.x == 0) {
     double W = 0.0;
-    for (int64_t i = 0; i < m; ++i) W = __dadd_rn(W, q[i]);
+    if (Wpre != nullptr) {
+      W = *Wpre;  // the same ascending sum, taken chunk by chunk while A arrived
+    } else {
+      for (int64_t i = 0; i < m; ++i) W = __dadd_rn(W, q[i]);
+    }
     sW = W;
   }
   __syncthreads();
@@ -170,9 +174,22 @@ cudaError_t launch_weights(const double* nu, const float* w, int64_t m, int coup
   return cudaGetLastError();
 }
 
+// W += nu[0] + nu[1] + ... in ascending order, one thread (the canonical
+// sum of the alias construction, continued over consecutive row chunks)
+__global__ void w_accumulate_kernel(const double* __restrict__ nu, int64_t rows, double* W) {
+  double w = *W;
+  for (int64_t i = 0; i < rows; ++i) w = __dadd_rn(w, nu[i]);
+  *W = w;
+}
+
+cudaError_t launch_w_accumulate(const double* nu, int64_t rows, double* W, cudaStream_t s) {
+  w_accumulate_kernel<<<1, 1, 0, s>>>(nu, rows, W);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32_t* alias,
                                double* q_scratch, int32_t* stack_scratch, int* status,
-                               cudaStream_t s) {
+                               cudaStream_t s, const double* Wpre) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess)
@@ -187,7 +204,7 @@ cudaError_t launch_alias_build(const double* nu, int64_t m, uint32_t* thr, int32
     if (e != cudaSuccess) return e;
   }
   alias_build_kernel<<<1, 256, smem, s>>>(nu, m, thr, alias, q_scratch, stack_scratch, status,
-                                          use_smem);
+                                          use_smem, Wpre);
   return cudaGetLastError();
 }
 

@@ -37,9 +37,11 @@ def _dptr(t: torch.Tensor | None):
 class Solver:
     """One RSKA problem: rska_setup on construction, rska_destroy on close().
 
-    A: (m, lda) float32 CUDA tensor, row-major, lda a multiple of 4; the first
-    n columns are the matrix (n defaults to lda).  b: (m,) float32 CUDA tensor.
-    A and b are borrowed by the library and kept alive here.
+    A: (m, lda) float32 tensor, row-major, lda a multiple of 4; the first n
+    columns are the matrix (n defaults to lda).  b: (m,) float32 tensor.  CUDA
+    tensors are borrowed by the library and kept alive here; CPU tensors are
+    copied by the library (rska_setup_host, overlapped with the setup when
+    pinned).
     """
 
     def __init__(self, A: torch.Tensor, b: torch.Tensor, lam: float, eta: int, t: float,
@@ -53,11 +55,22 @@ class Solver:
         self.n = self.lda if n is None else int(n)
         self.eta, self.lam, self.t, self.seed = int(eta), float(lam), float(t), int(seed)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.device = A.device
         h = ctypes.c_void_p()
-        check(lib().rska_setup(ctypes.byref(h), _dptr(A), self.m, self.n, self.lda, _dptr(b),
-                               self.lam, self.eta, self.t, self.seed, _stream_ptr(self.stream)),
-              "rska_setup")
+        if A.is_cuda:
+            self.device = A.device
+            check(lib().rska_setup(ctypes.byref(h), _dptr(A), self.m, self.n, self.lda,
+                                   _dptr(b), self.lam, self.eta, self.t, self.seed,
+                                   _stream_ptr(self.stream)), "rska_setup")
+        else:
+            # host tensors: rska_setup_host copies them (overlapped with the
+            # row norms when they are pinned); the library owns the copies
+            if b.is_cuda or not A.is_contiguous() or not b.is_contiguous():
+                raise ValueError("host A and b must both be contiguous CPU tensors")
+            self.device = self.stream.device
+            check(lib().rska_setup_host(ctypes.byref(h), ctypes.c_void_p(A.data_ptr()), self.m,
+                                        self.n, self.lda, ctypes.c_void_p(b.data_ptr()),
+                                        self.lam, self.eta, self.t, self.seed,
+                                        _stream_ptr(self.stream)), "rska_setup_host")
         self._h = h
 
     # -- lifetime ---------------------------------------------------------

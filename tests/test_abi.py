@@ -87,6 +87,8 @@ def test_null_context_is_rejected(L):
     s2 = ctypes.c_double()
     assert L.rska_sigma_max2(None, 10, 0, ctypes.byref(s2), None, None) == 1
     assert L.rska_linearized_bregman(None, 1, 1.0) == 1
+    h = ctypes.c_void_p()
+    assert L.rska_setup_host(ctypes.byref(h), None, 10, 10, 12, None, 1.0, 4, 1.0, 0, None) == 1
 
 
 @pytest.mark.parametrize("args", [

@@ -1,0 +1,74 @@
+"""GPU setup from host buffers (rska_setup_host): the chunked, overlapped copy
+of A, the per-chunk row norms and the chunk-by-chunk FP64 sum of W must give
+exactly what the oracle gives (norms, alias table and indices bit for bit,
+iterates within 1e-4), from pinned and from pageable memory, for odd and even
+m, and reject zero rows and non-finite data as rska_setup does.
+"""
+import numpy as np
+import pytest
+
+from synth import gaussian_problem
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_10838_gb300 import build
+    build.build()
+    import oracle
+    oracle.build()
+    from paper_2203_10838_gb300.rska import Solver
+    return torch, oracle, Solver
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.parametrize("m,n,eta,pinned", [(2001, 1003, 64, True), (5000, 3000, 256, False),
+                                            (17, 9, 4, True)])
+def test_host_setup_matches_oracle(env, m, n, eta, pinned):
+    torch, orc, Solver = env
+    p = gaussian_problem(m, n, max(1, n // 40), seed=m + 7, noise=0.01)
+    A = torch.from_numpy(p.A)
+    b = torch.from_numpy(p.b)
+    if pinned:
+        A, b = A.pin_memory(), b.pin_memory()
+    K, lam, t, seed = 40, 0.5, 4.0, 13
+    with Solver(A, b, lam, eta, t, seed, n=n) as sol:
+        nu_g, thr_g, al_g = [v.cpu().numpy() for v in sol.get_tables()]
+        sol.solve(K)
+        x = sol.get_x()[0].cpu().numpy().astype(np.float64)
+        idx = sol.get_indices(0, K).cpu().numpy()
+    An = p.A[:, :n]
+    nu = orc.row_norms(An)
+    thr, alias = orc.alias_build(nu)
+    np.testing.assert_array_equal(nu_g, nu)
+    np.testing.assert_array_equal(thr_g.view(np.uint32), thr)
+    np.testing.assert_array_equal(al_g, alias)
+    tau = orc.sample(thr, alias, seed=seed, eta=eta, k0=0, K=K)
+    np.testing.assert_array_equal(idx, tau)
+    z = orc.rska_fixed(An, p.b.astype(np.float64), lam, t, eta, tau, nu=nu)
+    assert rel(x, orc.soft_shrink(z, lam)) <= REL_TOL
+
+
+def test_host_setup_rejects_bad_data(env):
+    torch, orc, Solver = env
+    from paper_2203_10838_gb300._lib import RSKAError
+    p = gaussian_problem(300, 64, 4, seed=3)
+    p.A[250] = 0.0  # a zero row in the last chunk
+    with pytest.raises(RSKAError) as e:
+        Solver(torch.from_numpy(p.A).pin_memory(), torch.from_numpy(p.b).pin_memory(), 0.1, 8,
+               1.0, 0, n=64)
+    assert e.value.code == 2
+    p = gaussian_problem(300, 64, 4, seed=3)
+    p.b[7] = np.nan
+    with pytest.raises(RSKAError) as e:
+        Solver(torch.from_numpy(p.A), torch.from_numpy(p.b), 0.1, 8, 1.0, 0, n=64)
+    assert e.value.code == 3
