@@ -86,7 +86,8 @@ def load_peaks():
 
 
 KERNEL_SOURCES = {"rska_rows_kernel": ["rska_rows.cu", "rska_device.cuh"],
-                  "rska_persistent_kernel": ["rska_solve.cu", "rska_device.cuh"]}
+                  "rska_persistent_kernel": ["rska_solve.cu", "rska_device.cuh"],
+                  "unrolled_bwd_rows_kernel": ["rska_unrolled.cu", "rska_device.cuh"]}
 
 
 def kernel_source_hash(kernel):
@@ -97,14 +98,15 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel):
+def committed_traffic(kernel, iters=ITERS):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the kernel's source changed since the counters were taken."""
+    when the kernel's source or the iterations of one launch changed since the
+    counters were taken."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_hash") != kernel_source_hash(kernel) or d.get("iters_per_launch") != ITERS:
+    if d.get("source_hash") != kernel_source_hash(kernel) or d.get("iters_per_launch") != iters:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -583,7 +585,8 @@ def run_batched(args):
                                               f"subset scaled to {P}",
                                       "speedup_of_batched": loop_all_s / (ms_step / 1000.0)},
             "prep": {"generate_s": gen_s, "h2d_s": h2d_s, "setup_s": setup_s},
-            "cpu_baseline": cpu, "clocks": clk}
+            "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": args.steps}   # one rska_batched_kernel per solve
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -638,6 +641,26 @@ def run_unrolled(args):
         loss.backward()
         return loss
 
+    # events on the solver's stream around each forward (b gather + forward
+    # kernel) and each adjoint launch (one backward kernel) of the timed steps
+    spans = {"fwd": [], "bwd": []}
+    timing = [False]
+
+    def timed(raw, key):
+        def call(*xs):
+            if not timing[0]:
+                return raw(*xs)
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(stream)
+            out = raw(*xs)
+            ev[1].record(stream)
+            spans[key].append(ev)
+            return out
+        return call
+
+    un.forward_raw = timed(un.forward_raw, "fwd")
+    un.backward_raw = timed(un.backward_raw, "bwd")
+
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
@@ -645,20 +668,30 @@ def run_unrolled(args):
     clocks = ClockSampler(local)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    timing[0] = True
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    timing[0] = False
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    fwd_ms = sum(a.elapsed_time(b) for a, b in spans["fwd"]) / len(spans["fwd"])
+    bwd_ms = sum(a.elapsed_time(b) for a, b in spans["bwd"]) / len(spans["bwd"])
     from paper_2203_10838_gb300.shard import max_over_ranks
     ms = max_over_ranks(ms, dev)
+    fwd_ms = max_over_ranks(fwd_ms, dev)
+    bwd_ms = max_over_ranks(bwd_ms, dev)
     # rows read: K forward, K - K/c recompute, K adjoint steps of eta rows each
-    row_reads = U_P * U_ETA * (U_K + (U_K - U_K // U_CK) + U_K)
+    bwd_rows = U_P * U_ETA * ((U_K - U_K // U_CK) + U_K)
+    row_reads = U_P * U_ETA * U_K + bwd_rows
     value = row_reads / (ms / 1000.0) * world
     hbm_peak, peak_kind = load_peaks()
-    achieved = row_reads * (4.0 * U_N) / (ms / 1000.0) / 1e9
+    # the dominant kernel is the adjoint launch (recompute + adjoint steps)
+    achieved = bwd_rows * (4.0 * U_N) / (bwd_ms / 1000.0) / 1e9
+    fwd_gbs = U_P * U_ETA * U_K * (4.0 * U_N) / (fwd_ms / 1000.0) / 1e9
+    step_gbs = row_reads * (4.0 * U_N) / (ms / 1000.0) / 1e9
     # naive torch autograd comparator on 4 problems, scaled to 64
     sub = 4 if args.mode != "kernel" else 0
     t_naive = 0.0
@@ -689,11 +722,19 @@ def run_unrolled(args):
             "config": {"workload": "rska_unrolled_64x2048x1024", "P": U_P, "m": U_M, "n": U_N,
                        "K": U_K, "eta": U_ETA, "ckpt": U_CK, "lambda": U_LAM, "t": U_T},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak,
+                         "traffic": committed_traffic("unrolled_bwd_rows_kernel", U_K),
                          "peak_kind": f"{peak_kind} (copy bandwidth)",
-                         "kernel": "unrolled_fwd_rows_kernel + unrolled_bwd_rows_kernel"},
+                         "kernel": "unrolled_bwd_rows_kernel", "launch_ms": bwd_ms,
+                         "algorithmic_bytes": bwd_rows * 4.0 * U_N},
+            "forward": {"launch_ms": fwd_ms, "achieved_gbs": fwd_gbs,
+                        "frac": fwd_gbs / hbm_peak,
+                        "kernels": "unrolled_gather_b_kernel + unrolled_fwd_rows_kernel"},
+            "step_row_bytes_gbs": step_gbs,
             "naive_torch_autograd_ms_extrapolated": naive_ms,
-            "speedup_vs_naive_autograd": naive_ms / ms if naive_ms else None, "clocks": clk}
+            "speedup_vs_naive_autograd": naive_ms / ms if naive_ms else None, "clocks": clk,
+            # per step: unrolled_gather_b_kernel, unrolled_fwd_rows_kernel, unrolled_bwd_rows_kernel
+            "gpu_launches": 3 * args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
