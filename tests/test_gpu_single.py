@@ -81,6 +81,14 @@ CASES = {
     "cpl8_partial_residency": (300, 9000, 50, 256, 2.0, 100.0, 5, 50, 16, 0.0),
     "eta_above_m": (1500, 3000, 30, 2048, 1.0, 400.0, 6, 20, None, 0.0),
     "single_cta_lambda0": (64, 96, 5, 4, 0.0, 2.0, 7, 500, None, 0.0),
+    # degenerate shapes: a 1 x 1 system (RK reaches b/a), one row drawn eta times
+    # per iteration, one column (n = 1: a single float4 column, three of it padding)
+    "one_by_one_rk": (1, 1, 1, 1, 0.0, 1.0, 8, 50, None, 0.0),
+    "single_row_eta3": (1, 7, 2, 3, 0.2, 1.5, 9, 100, None, 0.0),
+    "single_column": (9, 1, 1, 2, 0.1, 1.0, 10, 200, None, 0.0),
+    # a grid larger than eta: the row-split kernel has CTAs that own no rows
+    # and only take part in the exchange
+    "idle_ctas_grid8_eta3": (200, 300, 8, 3, 0.5, 2.0, 11, 100, 8, 0.0),
 }
 
 
@@ -215,3 +223,55 @@ def test_rejects_zero_row_and_nonfinite(env):
         sol.solve(10)
         x, _ = sol.get_x()
         assert torch.isfinite(x).all()
+
+
+def test_zero_iterations_leave_the_state(env):
+    """K = 0 launches nothing: x = z = 0 from z_0 = 0, the counter stays, an
+    empty index range is valid, and K = 0 after some iterations changes
+    nothing."""
+    torch, orc, Solver = env
+    prob = gaussian_problem(80, 40, 4, seed=13)
+    with Solver(torch.from_numpy(prob.A).cuda(), torch.from_numpy(prob.b).cuda(), 0.3, 5, 2.0,
+                1, n=40) as sol:
+        sol.solve(0)
+        x, z = sol.get_x()
+        assert sol.iteration == 0
+        assert not x.any() and not z.any()
+        assert tuple(sol.get_indices(0, 0).shape) == (0, 5)
+        sol.solve(30)
+        x30, z30 = [v.clone() for v in sol.get_x()]
+        sol.solve(0)
+        x, z = sol.get_x()
+        assert sol.iteration == 30
+        assert torch.equal(x, x30) and torch.equal(z, z30)
+
+
+@pytest.mark.parametrize("kernel", ["column", "rows"])
+def test_skewed_row_norms(env, kernel):
+    """Row norms spread over twelve decades (rows scaled by 10^u, u uniform in
+    [-3, 3], b scaled with them so the system stays consistent): alias tables
+    and indices bit-exact with the oracle's, iterates within the bar."""
+    torch, orc, Solver = env
+    from paper_2203_10838_gb300.rska import KERNEL
+    m, n, eta, lam, t, seed, K = 600, 250, 12, 0.5, 4.0, 21, 300
+    prob = gaussian_problem(m, n, 10, seed=77)
+    c = 10.0 ** np.random.default_rng(5).uniform(-3.0, 3.0, m)
+    A = (prob.A * c[:, None]).astype(np.float32)
+    b = (prob.b64 * c).astype(np.float32)
+    with Solver(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), lam, eta, t, seed,
+                n=n) as sol:
+        sol.set_option("kernel", KERNEL[kernel])
+        nu_g, thr_g, alias_g = [v.cpu().numpy() for v in sol.get_tables()]
+        sol.solve(K)
+        x = sol.get_x()[0].cpu().numpy().astype(np.float64)
+        idx = sol.get_indices(0, K).cpu().numpy()
+    An = A[:, :n]
+    nu = orc.row_norms(An)
+    thr, alias = orc.alias_build(nu)
+    np.testing.assert_array_equal(nu_g, nu)
+    np.testing.assert_array_equal(thr_g.view(np.uint32), thr)
+    np.testing.assert_array_equal(alias_g, alias)
+    tau = orc.sample(thr, alias, seed=seed, eta=eta, k0=0, K=K)
+    np.testing.assert_array_equal(idx, tau)
+    zr = orc.rska_fixed(An, b.astype(np.float64), lam, t, eta, tau, nu=nu)
+    assert rel(x, orc.soft_shrink(zr, lam)) <= REL_TOL
