@@ -169,3 +169,24 @@ def test_batched_full_configuration_sampled(env):
         bp = b[int(b_off[p]):int(b_off[p]) + mp].astype(np.float64)
         zr = orc.rska(np.ascontiguousarray(Ap), bp, lam, eta, t, seed, K, problem=int(p))
         assert rel(z[xo[p]:xo[p] + np_], zr) <= REL_TOL, (p, mp, np_)
+
+
+@pytest.mark.parametrize("shapes", [
+    [(1, 1), (1, 9), (7, 1), (3, 2), (50, 30)],   # 1 x 1, one row, one column, tiny, ragged
+    [(300, 150)],                                  # a batch of one problem
+])
+def test_batched_degenerate_shapes(env, shapes):
+    torch, orc, BatchSolver = env
+    probs = make_batch(shapes, 7000)
+    A, a_off, m, n, lda, b, b_off = pack_batch(probs)
+    lam, eta, t, seed, K = 0.1, 5, 1.0, 23, 30
+    with BatchSolver(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), a_off, m, n, lda,
+                     b_off, lam, eta, t, seed) as bs:
+        bs.solve(K, tol=0.0)
+        iters, rr = bs.results()
+        z = bs.get_x()[1].cpu().numpy().astype(np.float64)
+        xo = bs.x_off
+    assert np.all(iters == K)
+    for p, pr in enumerate(probs):
+        zr = orc.rska(pr.A[:, :pr.n], pr.b.astype(np.float64), lam, eta, t, seed, K, problem=p)
+        assert rel(z[xo[p]:xo[p] + pr.n], zr) <= REL_TOL, (p, pr.m, pr.n)

@@ -78,6 +78,15 @@ def test_mrhs_small_ragged(env):
              check_rows=range(40), tol=1e-4)
 
 
+@pytest.mark.parametrize("m,n,R,eta", [(5, 3, 1, 1), (1, 7, 3, 3)])
+def test_mrhs_degenerate_shapes(env, m, n, R, eta):
+    """One right-hand side with eta = 1 on a 5 x 3 system (every operand a
+    sliver of its padded tile), and a single row drawn eta times per iteration
+    for three right-hand sides."""
+    run_case(env, m, n, R, 1, eta=eta, lam=0.001, t=1.0, K=40, seed=3,
+             check_rows=range(R), tol=1e-4)
+
+
 def test_mrhs_single_term_within_spec(env):
     run_case(env, 700, 300, 40, 10, eta=100, lam=0.3, t=1.0, K=30, seed=7,
              check_rows=range(40), tol=SPEC_TOL, terms=1)

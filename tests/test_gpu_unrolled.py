@@ -116,3 +116,15 @@ def test_unrolled_one_cta_per_problem(env):
     shapes = [(256 + 8 * (i % 7), 128 + 4 * (i % 5)) for i in range(80)]
     run(env, shapes, nnz=6, noise=0.01, eta=16, K=30, ckpt=10, lams=[0.2] * 80,
         ts=[4.0] * 80, seed=24, check=[0, 13, 41, 79])
+
+
+@pytest.mark.parametrize("K,ckpt", [(12, 1), (12, 12), (1, 1)])
+def test_unrolled_checkpoint_extremes_and_degenerate_shapes(env, K, ckpt):
+    """Checkpoints after every iteration (the adjoint recomputes nothing), one
+    segment spanning all K iterations, and K = 1; the batch holds a single-row
+    problem (its row drawn eta times per iteration) and a single-column one
+    beside ragged shapes.  With K = 1 two problems end with x_1 = 0 (every mask
+    zero) and their exact gradients are zero."""
+    shapes = [(40, 24), (1, 5), (6, 1), (33, 17), (64, 64)]
+    run(env, shapes, nnz=3, noise=0.01, eta=8, K=K, ckpt=ckpt, lams=[0.05] * 5, ts=[2.0] * 5,
+        seed=17, check=range(5))
