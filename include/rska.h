@@ -61,7 +61,7 @@ extern "C" {
 #define RSKA_ENOMEM 4        /* device allocation failed */
 #define RSKA_ECUDA 5         /* a CUDA runtime call failed */
 #define RSKA_ETIMEOUT 6      /* a device-side wait exceeded its limit; kernel returned early */
-#define RSKA_EUNSUPPORTED 7  /* valid but outside this build's limits (e.g. n too large) */
+#define RSKA_EUNSUPPORTED 7  /* valid but outside the library's limits (e.g. n too large) */
 
 typedef struct rska_ctx rska_ctx;
 

@@ -280,7 +280,7 @@ const char* rska_strerror(int code) {
     case RSKA_ENOMEM: return "device allocation failed";
     case RSKA_ECUDA: return "CUDA runtime error";
     case RSKA_ETIMEOUT: return "device-side wait timed out";
-    case RSKA_EUNSUPPORTED: return "problem outside this build's limits";
+    case RSKA_EUNSUPPORTED: return "problem outside the library's limits";
     default: return "unknown error";
   }
 }
