@@ -721,6 +721,32 @@ def run_unrolled(args):
         t_naive += time.perf_counter() - c0
     naive_ms = 1000.0 * t_naive * U_P / sub if sub else None
     un.close()
+    # the FP64 oracle (forward, then the reverse sweep over all stored z_k) on
+    # one host core, problem by problem, expressed in this line's unit: the
+    # row reads the GPU's checkpointed schedule makes per problem
+    cpu = None
+    if rank == 0 and args.mode != "kernel" and not args.skip_cpu:
+        import oracle
+        oracle.build()
+        c0 = time.perf_counter()
+        done = 0
+        for p in range(U_P):
+            pr = probs[p]
+            Ap = np.ascontiguousarray(pr.A[:, :pr.n])
+            nu = oracle.row_norms(Ap)
+            thr, alias = oracle.alias_build(nu)
+            tau = oracle.sample(thr, alias, seed=U_SEED, eta=U_ETA, k0=0, K=U_K, problem=p)
+            oracle.unrolled_grad(Ap, pr.b.astype(np.float64), U_LAM, U_T, U_ETA, tau,
+                                 pr.xhat.astype(np.float32).astype(np.float64), nu=nu)
+            done += 1
+            if time.perf_counter() - c0 > args.ref_seconds:
+                break
+        el = time.perf_counter() - c0
+        cpu = {"value": row_reads / U_P * done / el, "unit": "row-reads/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"loss and gradient of {done} of the {U_P} problems (K = {U_K}, FP64, "
+                         f"single thread, {el:.1f} s), counted in the GPU schedule's row reads "
+                         f"per problem"}
     line = {"metric": "unrolled RSKA forward + adjoint (64 x 2048x1024, K=200, eta=64)",
             "value": value, "unit": "row-reads/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
@@ -738,7 +764,8 @@ def run_unrolled(args):
                         "kernels": "unrolled_gather_b_kernel + unrolled_fwd_rows_kernel"},
             "step_row_bytes_gbs": step_gbs,
             "naive_torch_autograd_ms_extrapolated": naive_ms,
-            "speedup_vs_naive_autograd": naive_ms / ms if naive_ms else None, "clocks": clk,
+            "speedup_vs_naive_autograd": naive_ms / ms if naive_ms else None,
+            "cpu_baseline": cpu, "clocks": clk,
             # per step: unrolled_gather_b_kernel, unrolled_fwd_rows_kernel, unrolled_bwd_rows_kernel
             "gpu_launches": 3 * args.steps}
     if rank == 0:
