@@ -4,8 +4,9 @@ The paper (Algorithm 1; Sec. 5 variants v1/v2) fixes only the distribution
 p_i = ||a_i||^2 / ||A||_F^2 with replacement; the counter/key layout and the
 alias construction are this library's index contract.  These tests tie the
 oracle's implementation to things outside itself: an independent Philox4x32-10
-(Triton's, run in its CPU interpreter), exact probability bookkeeping of the
-alias table, closed-form norms and chi-square frequency tests.
+(Triton's, run in its CPU interpreter), uniformity of the raw words, exact
+probability bookkeeping of the alias table, closed-form norms and chi-square
+frequency tests.
 """
 import json
 import os
@@ -80,6 +81,29 @@ def test_philox_changes_with_every_word(orc):
         k = [5, 6]
         k[pos] ^= 1
         assert not np.array_equal(orc.philox4x32_10([1, 2, 3, 4], k), base)
+
+
+def test_philox_words_are_uniform(orc):
+    """2^20 words from 2^18 consecutive counters under one key: the high and
+    the low 16 bits each pass a chi-square test on 2^16 bins, every bit
+    position is balanced (|z| < 5), and the pairs (u0, u1), (u2, u3) the
+    sampler uses as (column, accept) words pass a chi-square test on a
+    256 x 256 grid of their high bytes."""
+    n = 1 << 18
+    out = np.empty((n, 4), dtype=np.uint32)
+    key = [0x9E3779B9, 0x12345678]
+    for k in range(n):
+        out[k] = orc.philox4x32_10([k, 0, 7, 3], key)
+    w = out.ravel()
+    for v in (w >> 16, w & 0xFFFF):
+        counts = np.bincount(v.astype(np.int64), minlength=1 << 16)
+        assert stats.chisquare(counts).pvalue > 1e-4
+    ones = ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).sum(0)
+    z = (ones - w.size / 2) / np.sqrt(w.size / 4)
+    assert np.abs(z).max() < 5.0, z
+    pairs = out.reshape(-1, 2)
+    cell = (pairs[:, 0] >> 24).astype(np.int64) * 256 + (pairs[:, 1] >> 24).astype(np.int64)
+    assert stats.chisquare(np.bincount(cell, minlength=1 << 16)).pvalue > 1e-4
 
 
 def _bucket_probs(thr, alias):
