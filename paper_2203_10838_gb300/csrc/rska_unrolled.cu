@@ -931,6 +931,12 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       __syncthreads();
       W.allowed = q + 1;
     }
+    // z_{k-1}, which this thread stored during the recompute, is read now so
+    // its L2 latency overlaps the rows (n/4 <= UT: column tid is the thread's
+    // only one in the update loop below)
+    float4 zpre = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q + 1 < cnt && tid < n4)
+      zpre = __ldcg(reinterpret_cast<const float4*>(seg + (size_t)(k - 1 - k0) * a.x_stride) + tid);
     float4 xr[NZ], gr[NZ], xb[NZ];
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
@@ -1035,7 +1041,7 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
       gsh[c4] = g;
       dnext[c4] = make_float4(0.f, 0.f, 0.f, 0.f);  // read by the peer one step ago
       if (q + 1 < cnt) {
-        const float4 zp = __ldcg(zprev + c4);
+        const float4 zp = (c4 == tid) ? zpre : __ldcg(zprev + c4);
         zsh[c4] = zp;
         xsh[c4] = soft_shrink4(zp, c.lam);
       }
