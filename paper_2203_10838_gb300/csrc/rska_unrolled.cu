@@ -914,6 +914,9 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
                               float& glam, float& gt, int rank) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n4 = (int)c.n4;
+  // lane 0 adds each row's share of dL/dt; a product with 1/eta keeps a
+  // division out of the warp's path (exact when eta is a power of two)
+  const float inv_eta = 1.0f / (float)a.eta;
   WarpRows W = make_rows<NZ, CL>(a, c, ring, cnt, warp, rank);
   while (W.issued < W.RS && W.issue<NZ>(c, I, lane, warp)) {
   }
@@ -982,7 +985,7 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
         u0 = c.coef * a2 * ivs;
         if (lane == 0) {
           atomicAdd(gbp + I.idx[buf][s0], u0);
-          gt -= rs * ivs * a2 / (float)a.eta;
+          gt -= rs * ivs * a2 * inv_eta;
         }
       }
       if (two) {
@@ -991,7 +994,7 @@ __device__ void backward_rows(const UnrolledArgs& a, const ProbCtx& c, int p, Ro
         u1 = c.coef * b2 * ivs;
         if (lane == 0) {
           atomicAdd(gbp + I.idx[buf][s1], u1);
-          gt -= rs * ivs * b2 / (float)a.eta;
+          gt -= rs * ivs * b2 * inv_eta;
         }
       }
 #pragma unroll
