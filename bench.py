@@ -452,7 +452,8 @@ def run_gpu(args):
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk, "gpu_launches": 2 * args.steps,
+                # per step: fill_shrink_kernel (reset), presample_kernel, the solve kernel
+                "clocks": clk, "gpu_launches": 3 * args.steps,
                 "accuracy": {"rel_residual": rel_res, "rel_error": rel_err,
                              "after_iterations": ITERS},
                 "plain_rska_gpu": plain, "time_to_accuracy": tta, "eta_sweep": sweep,
