@@ -87,6 +87,16 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   return t;
 }
 
+// Limit of a wait for work this CTA has already issued (a TMA copy into its
+// shared memory, an MMA reading it): such work always completes, and the CTA
+// must not end before it has, so these waits use at least one second even
+// when the watchdog limit of the other waits is set much shorter.
+constexpr uint64_t kDrainLimitNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t drain_limit(uint64_t limit_ns) {
+  return limit_ns > kDrainLimitNs ? limit_ns : kDrainLimitNs;
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");

@@ -471,11 +471,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     __syncthreads();
   }
   if (threadIdx.x == 0 && (!ok || s_err) && nkb > 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
-  // let every issued copy land before the shared memory goes away
-  if (MODE == kUpdate && threadIdx.x == 64 && nkb > 0 && !ok) mb_wait(&zbar[0], 0u, a.limit_ns);
+  // let every issued copy land and every issued MMA finish before the shared
+  // and tensor memory go away (drain limit: these always complete, however
+  // short the watchdog limit of the waits above)
+  const uint64_t dl = drain_limit(a.limit_ns);
+  if (MODE == kUpdate && threadIdx.x == 64 && nkb > 0) mb_wait(&zbar[0], 0u, dl);
   if (threadIdx.x == 0) {
+    if (MODE == kUpdate && ok) mb_wait(&zbar[1], 0u, dl);
     for (int it = s_consumed; it < s_issued; ++it)
-      mb_wait(&full[it % GEMM_STAGES], (uint32_t)((it / GEMM_STAGES) & 1), a.limit_ns);
+      mb_wait(&full[it % GEMM_STAGES], (uint32_t)((it / GEMM_STAGES) & 1), dl);
+    mb_wait(&done, 0u, dl);
   }
   tc_fence_before();
   __syncthreads();
@@ -686,6 +691,7 @@ struct rska_mrhs {
   uint64_t limit_ns = 2000000000ull;
   cudaGraphExec_t graph = nullptr;   // one chunk of idx_cap iterations
   int graph_nsplit = -1, graph_ksplit = -1, graph_pdl = -1;
+  uint64_t graph_limit_ns = 0;       // the wait limit baked into the graph's kernel arguments
 };
 
 namespace {
@@ -1040,7 +1046,7 @@ int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
     if (e != cudaSuccess) break;
     if (cnt == h->idx_cap && h->use_graph) {
       if (!h->graph || h->graph_nsplit != h->nsplit || h->graph_ksplit != h->ksplit ||
-          h->graph_pdl != h->use_pdl) {
+          h->graph_pdl != h->use_pdl || h->graph_limit_ns != h->limit_ns) {
         if (h->graph) {
           cudaGraphExecDestroy(h->graph);
           h->graph = nullptr;
@@ -1061,6 +1067,7 @@ int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
         h->graph_nsplit = h->nsplit;
         h->graph_ksplit = h->ksplit;
         h->graph_pdl = h->use_pdl;
+        h->graph_limit_ns = h->limit_ns;
       }
       e = cudaGraphLaunch(h->graph, s);
     } else {

@@ -267,12 +267,15 @@ __global__ void __launch_bounds__(NT, 1)
     if (tid == 0) {
       s_abort = 1;
       const uint64_t t0 = global_timer_ns();
-      while (!s_pdone && global_timer_ns() - t0 < a.limit_ns) {
+      // the producer stops within one of its own bounded waits; every copy
+      // it issued lands before the CTA may end (drain limit, not the watchdog)
+      const uint64_t dl = drain_limit(a.limit_ns);
+      while (!s_pdone && global_timer_ns() - t0 < dl) {
       }
       const int64_t issued = s_prod;
       for (int64_t g = cons; g < issued; ++g) {
         const int sl = (int)(g % slots);
-        mbar_wait_bounded(&full[sl], (uint32_t)((g / slots) & 1), a.limit_ns, nullptr);
+        mbar_wait_bounded(&full[sl], (uint32_t)((g / slots) & 1), dl, nullptr);
       }
     }
     consumer_sync();

@@ -388,6 +388,7 @@ class Unrolled:
                                         int(seed), int(K), int(ckpt_every),
                                         _stream_ptr(self.stream)), "rska_unrolled_setup")
         self._h = h
+        self.generation = 0
         self.x_off = np.zeros(self.P + 1, dtype=np.int64)
         check(lib().rska_unrolled_offsets(self._h, ctypes.c_void_p(self.x_off.ctypes.data)),
               "rska_unrolled_offsets")
@@ -408,9 +409,18 @@ class Unrolled:
         check(lib().rska_unrolled_forward(self._h, _dptr(b), _dptr(lam), _dptr(t), _dptr(x)),
               "rska_unrolled_forward")
         self._keep = (b, lam, t)
+        self.generation += 1
         return x
 
-    def backward_raw(self, gx):
+    def backward_raw(self, gx, generation=None):
+        # the library differentiates its most recent forward (its checkpoints
+        # and the b, lambda, t it borrowed); a backward of an older forward
+        # would silently differentiate at the wrong point
+        if generation is not None and generation != self.generation:
+            raise RuntimeError(
+                f"rska_unrolled_backward: this output comes from forward {generation}, but "
+                f"forward {self.generation} ran since; the adjoint only differentiates the most "
+                "recent forward of an Unrolled context (run backward before the next forward)")
         b = self._keep[0]
         gb = torch.empty_like(b)
         glam = torch.empty(self.P, dtype=torch.float32, device=self.device)
@@ -430,10 +440,12 @@ class RSKAUnrolled(torch.autograd.Function):
     @staticmethod
     def forward(ctx, b, lam, t, unrolled):
         ctx.unrolled = unrolled
-        return unrolled.forward_raw(b.detach().contiguous(), lam.detach().contiguous(),
-                                    t.detach().contiguous())
+        x = unrolled.forward_raw(b.detach().contiguous(), lam.detach().contiguous(),
+                                 t.detach().contiguous())
+        ctx.generation = unrolled.generation
+        return x
 
     @staticmethod
     def backward(ctx, gx):
-        gb, glam, gt = ctx.unrolled.backward_raw(gx)
+        gb, glam, gt = ctx.unrolled.backward_raw(gx, ctx.generation)
         return gb, glam, gt, None

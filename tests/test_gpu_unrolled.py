@@ -128,3 +128,122 @@ def test_unrolled_checkpoint_extremes_and_degenerate_shapes(env, K, ckpt):
     shapes = [(40, 24), (1, 5), (6, 1), (33, 17), (64, 64)]
     run(env, shapes, nnz=3, noise=0.01, eta=8, K=K, ckpt=ckpt, lams=[0.05] * 5, ts=[2.0] * 5,
         seed=17, check=range(5))
+
+
+def test_backward_of_an_older_forward_raises(env):
+    """The adjoint differentiates the most recent forward of a context (its
+    checkpoints and the b, lambda, t it borrowed).  A backward of an output
+    from an earlier forward must raise instead of returning the gradient at
+    the later point."""
+    torch, orc, Unrolled = env
+    probs = [gaussian_problem(64, 32, 3, seed=800 + i, noise=0.01) for i in range(2)]
+    A, a_off, m, n, lda, b, b_off = pack_batch(probs)
+    un = Unrolled(torch.from_numpy(A).cuda(), a_off, m, n, lda, b_off, 8, 3, 10, 5)
+    b1 = torch.from_numpy(b).cuda().requires_grad_(True)
+    b2 = (1.5 * torch.from_numpy(b).cuda()).requires_grad_(True)
+    lam = torch.full((2,), 0.1, device="cuda", requires_grad=True)
+    t = torch.full((2,), 2.0, device="cuda", requires_grad=True)
+    x1 = un(b1, lam, t)
+    x2 = un(b2, lam, t)
+    with pytest.raises(RuntimeError, match="most recent forward"):
+        x1.sum().backward()
+    assert b1.grad is None
+    x2.sum().backward()
+    assert b2.grad is not None and torch.isfinite(b2.grad).all()
+    un.close()
+
+
+def _masks(orc, A, b, lam, t, eta, tau):
+    z = np.zeros(A.shape[1])
+    out = [np.abs(z) > lam]
+    for k in range(tau.shape[0]):
+        z = orc.rska_fixed(A, b, lam, t, eta, tau[k:k + 1], z0=z)
+        out.append(np.abs(z) > lam)
+    return np.array(out)
+
+
+def test_adjoint_against_central_differences_of_the_gpu_forward(env):
+    """dL/db (along a random unit direction per problem), dL/dlambda and
+    dL/dt from the hand-written adjoint against FP32 central differences of
+    the GPU forward itself with h = 1e-3, at 1e-2 relative.  Directions whose
+    +h or -h run changes a mask |z_j| > lambda anywhere along the trajectory
+    (decided by the FP64 oracle) are skipped: the loss is not differentiable
+    across those.  With the masks fixed, x_K is affine in b and lambda (so the
+    central difference of the quadratic loss is exact up to rounding) and a
+    polynomial in t."""
+    torch, orc, Unrolled = env
+    P, mm, nn, s, eta, K, ck, lam0, t0, seed, h = 12, 64, 24, 3, 8, 8, 4, 0.3, 2.0, 41, 1e-3
+    probs = [gaussian_problem(mm, nn, s, seed=1300 + i, noise=0.01) for i in range(P)]
+    A, a_off, m, n, lda, b, b_off = pack_batch(probs)
+    un = Unrolled(torch.from_numpy(A).cuda(), a_off, m, n, lda, b_off, eta, seed, K, ck)
+    xo = un.x_off
+    xhat = torch.zeros(int(xo[-1]), device="cuda")
+    for p, pr in enumerate(probs):
+        xhat[int(xo[p]):int(xo[p]) + pr.n] = torch.from_numpy(pr.xhat.astype(np.float32))
+    b0 = torch.from_numpy(b).cuda()
+    bd = b0.clone().requires_grad_(True)
+    lam = torch.full((P,), lam0, device="cuda", requires_grad=True)
+    t = torch.full((P,), t0, device="cuda", requires_grad=True)
+    x = un(bd, lam, t)
+    (0.5 * ((x - xhat) ** 2).sum()).backward()
+    gb = bd.grad.cpu().numpy().astype(np.float64)
+    glam = lam.grad.cpu().numpy().astype(np.float64)
+    gt = t.grad.cpu().numpy().astype(np.float64)
+
+    def losses(bv, lv, tv):
+        with torch.no_grad():
+            xx = un.forward_raw(bv.contiguous(), lv.contiguous(), tv.contiguous())
+        xx = xx.cpu().numpy().astype(np.float64)
+        xh = xhat.cpu().numpy().astype(np.float64)
+        return np.array([0.5 * np.sum((xx[int(xo[p]):int(xo[p]) + nn]
+                                       - xh[int(xo[p]):int(xo[p]) + nn]) ** 2)
+                         for p in range(P)])
+
+    rng = np.random.default_rng(5)
+    d = np.zeros_like(b)
+    for p in range(P):
+        v = rng.standard_normal(mm)
+        d[int(b_off[p]):int(b_off[p]) + mm] = v / np.linalg.norm(v)
+    dd = torch.from_numpy(d.astype(np.float32)).cuda()
+    lv = torch.full((P,), lam0, device="cuda")
+    tv = torch.full((P,), t0, device="cuda")
+    # b +- h d as the GPU holds them (FP32): the loss difference is compared
+    # with the gradient times the exact difference of the two FP32 vectors
+    b_plus, b_minus = b0 + h * dd, b0 - h * dd
+    db = (b_plus.double() - b_minus.double()).cpu().numpy()
+    bpl, bmi = b_plus.double().cpu().numpy(), b_minus.double().cpu().numpy()
+    dl_b = losses(b_plus, lv, tv) - losses(b_minus, lv, tv)
+    # lambda +- h and t +- h as FP32 values: divide by their exact difference
+    lv_p, lv_m, tv_p, tv_m = lv + h, lv - h, tv + h, tv - h
+    lp, lm = float(lv_p[0].item()), float(lv_m[0].item())
+    tp, tm = float(tv_p[0].item()), float(tv_m[0].item())
+    fd_l = (losses(b0, lv_p, tv) - losses(b0, lv_m, tv)) / (lp - lm)
+    fd_t = (losses(b0, lv, tv_p) - losses(b0, lv, tv_m)) / (tp - tm)
+    un.close()
+
+    checked = {"b": [], "lambda": [], "t": []}
+    for p, pr in enumerate(probs):
+        Ap = pr.A[:, :nn]
+        nu = orc.row_norms(Ap)
+        thr, alias = orc.alias_build(nu)
+        tau = orc.sample(thr, alias, seed=seed, eta=eta, k0=0, K=K, problem=p)
+        bp = pr.b.astype(np.float64)
+        seg = slice(int(b_off[p]), int(b_off[p]) + mm)
+        lf, tf = float(np.float32(lam0)), float(np.float32(t0))
+        base = _masks(orc, Ap, bp, lf, tf, eta, tau)
+        same = lambda *a: np.array_equal(_masks(orc, Ap, *a, eta, tau), base)  # noqa: E731
+        if same(bpl[seg], lf, tf) and same(bmi[seg], lf, tf):
+            checked["b"].append((gb[seg] @ db[seg], dl_b[p]))
+        if same(bp, lp, tf) and same(bp, lm, tf):
+            checked["lambda"].append((glam[p], fd_l[p]))
+        if same(bp, lf, tp) and same(bp, lf, tm):
+            checked["t"].append((gt[p], fd_t[p]))
+    worst = {}
+    for kind, pairs in checked.items():
+        assert len(pairs) >= 3, (kind, len(pairs))
+        scale = max(abs(f) for _, f in pairs)
+        errs = [abs(g - f) / max(abs(f), 1e-3 * scale) for g, f in pairs]
+        worst[kind] = max(errs)
+        assert worst[kind] <= 1e-2, (kind, pairs)
+    print(f"adjoint vs FP32 central differences (h = {h}): worst relative error {worst}, "
+          f"directions checked {({k: len(v) for k, v in checked.items()})}")

@@ -89,3 +89,21 @@ def test_noalloc_rejects_sizes_beyond_its_array(env):
                                 None) == 7
     assert L.rska_solve_noalloc(p(A), 4, 8, 8, p(b), 1.0, 2048, 1.0, 0, 1, p(x), None,
                                 None) == 7
+
+
+def test_noalloc_runs_several_launches_like_the_regular_path(env):
+    """eta = 1024 gives 64 iterations per launch of the allocation-free path
+    (its pre-sampled index buffer holds 65536 draws), so K = 200 takes four
+    launches; from the second on, each continues the index sequence from the
+    iteration counter the previous launch left on the device.  The result
+    must still match the regular entry points."""
+    torch, L, Solver = env
+    m, n, s, eta, lam, t, seed, K = 6000, 3000, 50, 1024, 1.0, 400.0, 13, 200
+    prob = gaussian_problem(m, n, s, seed=513, noise=0.01)
+    A = torch.from_numpy(prob.A).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    x_na, z_na = _noalloc(torch, L, A, b, n, lam, eta, t, seed, K)
+    x_rg, z_rg = _regular(torch, Solver, A, b, n, lam, eta, t, seed, K)
+    assert np.linalg.norm(x_rg) > 0
+    assert rel(x_na, x_rg) <= REL_TOL, rel(x_na, x_rg)
+    assert rel(z_na, z_rg) <= REL_TOL, rel(z_na, z_rg)
