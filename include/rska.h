@@ -100,6 +100,20 @@ int rska_setup_host(rska_ctx **out, const float *A_host, int64_t m, int64_t n, i
                     void *cuda_stream);
 
 /*
+ * rska_load_host -- HOST: load a new problem of the same shape into a context
+ * made by rska_setup_host, reusing its device memory (no allocation): A_host
+ * (m x lda floats) and b_host (m floats) with the m, n, lda of that setup are
+ * copied, row norms and alias table rebuilt exactly as rska_setup_host does
+ * (same overlap of copy, norms and W), and z = 0, k = 0.  lambda, eta, t,
+ * seed and the options are kept; row weights return to uniform.  For callers
+ * that solve many systems of one shape (the allocation of the device copy of
+ * A then happens once).  Synchronous.  Errors: EINVAL (null pointers, or a
+ * context not made by rska_setup_host), EZEROROW, ENONFINITE, ECUDA; clears
+ * a sticky ETIMEOUT.
+ */
+int rska_load_host(rska_ctx *ctx, const float *A_host, const float *b_host);
+
+/*
  * rska_solve -- run K iterations of Algorithm 1 (k -> k + K) on the context's
  * stream: per chunk of up to 2^21/eta iterations, one pre-sampling kernel
  * (tau_k, b and 1/||a||^2 for the whole chunk) and one persistent kernel
@@ -175,6 +189,12 @@ int rska_destroy(rska_ctx *ctx);
  *          5: row steps per thread held in registers (0 when the shared
  *             memory tile holds all of tau_k)
  *          6: solver kernel in use: 1 column-split, 2 row-split
+ *          7: microseconds the last setup spent allocating device memory
+ *             (host clock; 0 after rska_load_host)
+ *          8: microseconds of the copy (host buffers only), FP64 row norms
+ *             and the sum W of the last setup or load (device events)
+ *          9: microseconds of the alias construction (device events)
+ *         10: microseconds of the whole last setup or load call (host clock)
  * Items 2, 3 and 5 describe the column-split kernel.
  */
 int rska_query(rska_ctx *ctx, int what, int64_t *value_out);

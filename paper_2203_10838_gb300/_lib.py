@@ -25,6 +25,7 @@ def _declare(lib):
     sigs = {
         "rska_setup": ([PP, P, i64, i64, i64, P, f32, i32, f32, u64, P], c_int),
         "rska_setup_host": ([PP, P, i64, i64, i64, P, f32, i32, f32, u64, P], c_int),
+        "rska_load_host": ([P, P, P], c_int),
         "rska_solve": ([P, i64], c_int),
         "rska_solve_until": ([P, i64, i64, f64, P, ctypes.POINTER(i64), ctypes.POINTER(f64)],
                              c_int),

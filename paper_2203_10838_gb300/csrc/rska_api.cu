@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
 #include <new>
 
 #include "rska_internal.h"
@@ -44,6 +45,16 @@ void free_all(Ctx* c) {
   cudaFree(c->stop);
   cudaFree(c->macc);
   cudaFree(c->scratch);
+  for (cudaEvent_t& ev : c->chunk_ev) {
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+  }
+  for (cudaEvent_t& ev : c->phase_ev) {
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  c->copy_stream = nullptr;
   cudaFree(c->tidx);
   cudaFree(c->tb);
   cudaFree(c->tiv);
@@ -135,6 +146,83 @@ rska::SolveArgs solve_args(Ctx* c, int64_t K, const int* stop) {
 
 namespace {
 
+constexpr int kLoadChunks = 16;  // row chunks of a host-buffer load
+
+double host_us_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Row norms and the alias table of the context's problem (Definition 1,
+// Sec. 5 v1/v2), z = 0, k = 0, status cleared.  With A_host set, A and b are
+// first copied from host buffers into the context's own device copies: b,
+// then A in row chunks on the copy stream, each chunk's norms and its part of
+// W following on the context's stream as soon as it has landed.  Records the
+// device time of the copy + norms + W phase and of the alias construction.
+int load_impl(Ctx* c, const float* A_host, const float* b_host) {
+  const int64_t m = c->m, n = c->n, lda = c->lda;
+  const int64_t np = n_padded(n);
+  cudaStream_t s = c->stream;
+  double* q = static_cast<double*>(c->scratch);
+  int32_t* stk = reinterpret_cast<int32_t*>(q + m);
+  double* Wdev = reinterpret_cast<double*>(stk + m + (m & 1));  // 8-byte aligned past the stack
+  cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->kdev, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stop, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->macc, 0, 8 * sizeof(double), s);
+  if (e == cudaSuccess) e = rska::launch_fill_shrink(c->z, c->x, nullptr, n, np, c->lambda, s);
+  if (A_host == nullptr) {
+    if (e == cudaSuccess) e = cudaEventRecord(c->phase_ev[0], s);
+    if (e == cudaSuccess)
+      e = rska::launch_row_norms(c->A, m, n, lda, c->b, c->nu, c->inv_nu, c->status, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->phase_ev[1], s);
+    if (e == cudaSuccess)
+      e = rska::launch_alias_build(c->nu, m, c->thr, c->alias, q, stk, c->status, s);
+  } else {
+    cudaStream_t cs = c->copy_stream;
+    if (e == cudaSuccess) e = cudaMemsetAsync(Wdev, 0, sizeof(double), s);
+    // the copy stream starts after the context's stream has reached this point
+    // (a previous solve may still read the device copies)
+    if (e == cudaSuccess) e = cudaEventRecord(c->phase_ev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, c->phase_ev[0], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->b_own, b_host, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, cs);
+    const int64_t rows = (m + kLoadChunks - 1) / kLoadChunks;
+    for (int k = 0; k < kLoadChunks && e == cudaSuccess; ++k) {
+      const int64_t r0 = (int64_t)k * rows;
+      if (r0 >= m) break;
+      const int64_t r = std::min<int64_t>(rows, m - r0);
+      e = cudaMemcpyAsync(c->A_own + r0 * lda, A_host + r0 * lda,
+                          sizeof(float) * (size_t)r * (size_t)lda, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) e = cudaEventRecord(c->chunk_ev[k], cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->chunk_ev[k], 0);
+      if (e == cudaSuccess)
+        e = rska::launch_row_norms(c->A_own + r0 * lda, r, n, lda, c->b_own + r0, c->nu + r0,
+                                   c->inv_nu + r0, c->status, s);
+      if (e == cudaSuccess) e = rska::launch_w_accumulate(c->nu + r0, r, Wdev, s);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->phase_ev[1], s);
+    if (e == cudaSuccess)
+      e = rska::launch_alias_build(c->nu, m, c->thr, c->alias, q, stk, c->status, s, Wdev);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(c->phase_ev[2], s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && c->copy_stream) e = cudaStreamSynchronize(c->copy_stream);
+  if (e != cudaSuccess) return (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
+  float ms01 = 0.f, ms12 = 0.f;
+  if (cudaEventElapsedTime(&ms01, c->phase_ev[0], c->phase_ev[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms12, c->phase_ev[1], c->phase_ev[2]) == cudaSuccess) {
+    c->setup_us[1] = 1000.0 * ms01;
+    c->setup_us[2] = 1000.0 * ms12;
+  }
+  c->k_host = 0;
+  c->sticky = RSKA_OK;
+  return check_status(c);
+}
+
+}  // namespace
+
+namespace {
+
 // rska_setup and rska_setup_host: with A_host set, the library allocates the
 // device copies of A and b and overlaps their host-to-device copy (row
 // chunks on a second stream) with the row norms and the ascending sum of W
@@ -142,6 +230,7 @@ namespace {
 int setup_impl(rska_ctx** out, const float* A, const float* b, const float* A_host,
                const float* b_host, int64_t m, int64_t n, int64_t lda, float lambda,
                int32_t eta, float t, uint64_t seed, void* stream) {
+  const auto t_call = std::chrono::steady_clock::now();
   rska_ctx* h = new (std::nothrow) rska_ctx;
   if (!h) return RSKA_ENOMEM;
   Ctx* c = &h->c;
@@ -190,73 +279,25 @@ int setup_impl(rska_ctx** out, const float* A, const float* b, const float* A_ho
   }
   c->A = A_host ? c->A_own : A;
   c->b = A_host ? c->b_own : b;
-  cudaStream_t s = c->stream;
-  double* q = static_cast<double*>(c->scratch);
-  int32_t* stk = reinterpret_cast<int32_t*>(q + m);
-  double* Wdev = reinterpret_cast<double*>(stk + m + (m & 1));  // 8-byte aligned past the stack
-  e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->kdev, 0, sizeof(int64_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->stop, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->macc, 0, 8 * sizeof(double), s);
-  if (e == cudaSuccess) e = rska::launch_fill_shrink(c->z, c->x, nullptr, n, np, lambda, s);
-  if (A_host == nullptr) {
-    if (e == cudaSuccess)
-      e = rska::launch_row_norms(A, m, n, lda, b, c->nu, c->inv_nu, c->status, s);
-    if (e == cudaSuccess)
-      e = rska::launch_alias_build(c->nu, m, c->thr, c->alias, q, stk, c->status, s);
-  } else {
-    // b, then A in row chunks on a copy stream; each chunk's norms and its
-    // part of W follow on the context's stream as soon as it has landed
-    constexpr int kChunks = 16;
-    cudaStream_t cs = nullptr;
-    cudaEvent_t ev[kChunks] = {};
-    int nev = 0;
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    for (int k = 0; k < kChunks && e == cudaSuccess; ++k) {
-      e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
-      if (e == cudaSuccess) ++nev;
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(Wdev, 0, sizeof(double), s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->b_own, b_host, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, cs);
-    const int64_t rows = (m + kChunks - 1) / kChunks;
-    for (int k = 0; k < kChunks && e == cudaSuccess; ++k) {
-      const int64_t r0 = (int64_t)k * rows;
-      if (r0 >= m) break;
-      const int64_t r = std::min<int64_t>(rows, m - r0);
-      e = cudaMemcpyAsync(c->A_own + r0 * lda, A_host + r0 * lda,
-                          sizeof(float) * (size_t)r * (size_t)lda, cudaMemcpyHostToDevice, cs);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[k], cs);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[k], 0);
-      if (e == cudaSuccess)
-        e = rska::launch_row_norms(c->A_own + r0 * lda, r, n, lda, c->b_own + r0, c->nu + r0,
-                                   c->inv_nu + r0, c->status, s);
-      if (e == cudaSuccess) e = rska::launch_w_accumulate(c->nu + r0, r, Wdev, s);
-    }
-    if (e == cudaSuccess)
-      e = rska::launch_alias_build(c->nu, m, c->thr, c->alias, q, stk, c->status, s, Wdev);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (cs) {
-      const cudaError_t e2 = cudaStreamSynchronize(cs);
-      if (e == cudaSuccess) e = e2;
-      cudaStreamDestroy(cs);
-    }
-    for (int k = 0; k < nev; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->phase_ev[k]);
+  if (A_host != nullptr) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < kLoadChunks && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&c->chunk_ev[k], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     free_all(c);
     delete h;
     return RSKA_ECUDA;
   }
-  rc = check_status(c);
+  c->setup_us[0] = host_us_since(t_call);
+  rc = load_impl(c, A_host, b_host);
   if (rc != RSKA_OK) {
     free_all(c);
     delete h;
     return rc;
   }
-  cudaFree(c->scratch);
-  c->scratch = nullptr;
+  c->setup_us[3] = host_us_since(t_call);
   *out = h;
   return RSKA_OK;
 }
@@ -594,6 +635,18 @@ int rska_linearized_bregman(rska_ctx* h, int64_t K, double step) {
   return check_status(c);
 }
 
+int rska_load_host(rska_ctx* h, const float* A_host, const float* b_host) {
+  if (!h || !A_host || !b_host) return RSKA_EINVAL;
+  Ctx* c = &h->c;
+  if (c->A_own == nullptr) return RSKA_EINVAL;  // not created by rska_setup_host
+  if (c->sticky == RSKA_ECUDA) return RSKA_ECUDA;
+  const auto t_call = std::chrono::steady_clock::now();
+  c->setup_us[0] = 0.0;
+  const int rc = load_impl(c, A_host, b_host);
+  c->setup_us[3] = host_us_since(t_call);
+  return rc;
+}
+
 int rska_destroy(rska_ctx* h) {
   if (!h) return RSKA_EINVAL;
   cudaStreamSynchronize(h->c.stream);
@@ -613,6 +666,10 @@ int rska_query(rska_ctx* h, int what, int64_t* value_out) {
     case 4: *value_out = (int64_t)g.smem; return RSKA_OK;
     case 5: *value_out = g.rreg; return RSKA_OK;
     case 6: *value_out = h->c.use_rows ? 2 : 1; return RSKA_OK;
+    case 7:
+    case 8:
+    case 9:
+    case 10: *value_out = (int64_t)std::llround(h->c.setup_us[what - 7]); return RSKA_OK;
     default: return RSKA_EINVAL;
   }
 }

@@ -95,9 +95,15 @@ struct Ctx {
   float* tb = nullptr;
   float* tiv = nullptr;
   int64_t chunk = 1;           // iterations per persistent launch (pre-sample capacity)
-  void* scratch = nullptr;     // alias-build scratch (freed after setup)
+  void* scratch = nullptr;     // alias-build scratch (q, stack, W), kept for rska_load_host
   float* A_own = nullptr;      // device copies made by rska_setup_host (else null)
   float* b_own = nullptr;
+  // host-buffer loads: the copy stream, one event per row chunk, and the
+  // timing events of the last setup or load (start, norms done, table done)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t chunk_ev[16] = {};
+  cudaEvent_t phase_ev[3] = {};
+  double setup_us[4] = {0, 0, 0, 0};  // allocation, copy + norms + W, alias table, whole call
   // host mirrors
   int64_t k_host = 0;
   int sticky = RSKA_OK;

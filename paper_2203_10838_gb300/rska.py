@@ -13,7 +13,8 @@ import torch
 from ._lib import check, lib
 
 QUERY = {"grid": 0, "threads": 1, "rows_resident": 2, "w4max": 3, "smem": 4, "rreg": 5,
-         "kernel": 6}
+         "kernel": 6, "setup_alloc_us": 7, "setup_norms_us": 8, "setup_alias_us": 9,
+         "setup_total_us": 10}
 OPTION = {"grid": 0, "watchdog_us": 1, "kernel": 2}
 KERNEL = {"auto": 0, "column": 1, "rows": 2}
 
@@ -92,6 +93,20 @@ class Solver:
         self.close()
 
     # -- entry points -----------------------------------------------------
+    def load_host(self, A: torch.Tensor, b: torch.Tensor):
+        """rska_load_host: a new problem of this context's shape from host
+        tensors (float32, contiguous; pinned memory overlaps the copy with the
+        row norms), reusing the context's device memory; z = 0, k = 0."""
+        if A.is_cuda or b.is_cuda or A.dtype != torch.float32 or b.dtype != torch.float32:
+            raise ValueError("load_host takes float32 CPU tensors")
+        if tuple(A.shape) != (self.m, self.lda) or tuple(b.shape) != (self.m,):
+            raise ValueError("A and b must have the shape of the context's problem")
+        if not A.is_contiguous() or not b.is_contiguous():
+            raise ValueError("A and b must be contiguous")
+        self.A, self.b = A, b
+        check(lib().rska_load_host(self._h, ctypes.c_void_p(A.data_ptr()),
+                                   ctypes.c_void_p(b.data_ptr())), "rska_load_host")
+
     def solve(self, K: int):
         check(lib().rska_solve(self._h, int(K)), "rska_solve")
 

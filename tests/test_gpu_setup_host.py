@@ -72,3 +72,50 @@ def test_host_setup_rejects_bad_data(env):
     with pytest.raises(RSKAError) as e:
         Solver(torch.from_numpy(p.A), torch.from_numpy(p.b), 0.1, 8, 1.0, 0, n=64)
     assert e.value.code == 3
+
+
+def test_load_host_reuses_the_context_for_a_new_problem(env):
+    """rska_load_host: a second problem of the same shape loaded into a
+    context made by rska_setup_host (no new allocation) gives the oracle's
+    norms, table, indices and iterates for that problem, after the first
+    problem was solved, after a watchdog timeout (cleared by the load), and
+    after a zero row was rejected (the context stays usable); row weights set
+    before the load return to uniform."""
+    torch, orc, Solver = env
+    from paper_2203_10838_gb300._lib import RSKAError
+    m, n, eta, K, lam, t, seed = 3001, 1500, 128, 30, 0.5, 40.0, 21
+    p1 = gaussian_problem(m, n, 30, seed=71, noise=0.01)
+    p2 = gaussian_problem(m, n, 30, seed=72, noise=0.01)
+    A1, b1 = torch.from_numpy(p1.A).pin_memory(), torch.from_numpy(p1.b).pin_memory()
+    A2, b2 = torch.from_numpy(p2.A).pin_memory(), torch.from_numpy(p2.b).pin_memory()
+    with Solver(A1, b1, lam, eta, t, seed, n=n) as sol:
+        assert sol.query("setup_total_us") > 0 and sol.query("setup_alias_us") > 0
+        sol.solve(K)
+        sol.set_weights(torch.full((m,), 2.0, device="cuda"), couple=True)
+        sol.set_option("watchdog_us", 1)
+        sol.solve(50)
+        with pytest.raises(RSKAError):
+            sol.get_x()
+        sol.set_option("watchdog_us", 2_000_000)
+        bad = gaussian_problem(m, n, 30, seed=73)
+        bad.A[5] = 0.0
+        with pytest.raises(RSKAError) as e:
+            sol.load_host(torch.from_numpy(bad.A), torch.from_numpy(bad.b))
+        assert e.value.code == 2
+        sol.load_host(A2, b2)
+        assert sol.iteration == 0
+        assert sol.query("setup_alloc_us") == 0
+        nu_g, thr_g, al_g = [v.cpu().numpy() for v in sol.get_tables()]
+        sol.solve(K)
+        x = sol.get_x()[0].cpu().numpy().astype(np.float64)
+        idx = sol.get_indices(0, K).cpu().numpy()
+    An = p2.A[:, :n]
+    nu = orc.row_norms(An)
+    thr, alias = orc.alias_build(nu)
+    np.testing.assert_array_equal(nu_g, nu)
+    np.testing.assert_array_equal(thr_g.view(np.uint32), thr)
+    np.testing.assert_array_equal(al_g, alias)
+    tau = orc.sample(thr, alias, seed=seed, eta=eta, k0=0, K=K)
+    np.testing.assert_array_equal(idx, tau)
+    z = orc.rska_fixed(An, p2.b.astype(np.float64), lam, t, eta, tau, nu=nu)
+    assert rel(x, orc.soft_shrink(z, lam)) <= REL_TOL
