@@ -487,9 +487,25 @@ def run_batched(args):
     dev = torch.device("cuda", local)
     build.build()
     from paper_2203_10838_gb300.rska import BatchSolver, Solver
+    from paper_2203_10838_gb300.shard import gather_by_unit, problem_shards
+    from synth import batched_sizes
     t0 = time.perf_counter()
-    P = args.batch_p
-    A, a_off, m, n, lda, b, b_off, xhats = batched_problem_set(P, BATCH_SEED + rank)
+    P_all = args.batch_p
+    if args.shard:
+        # one fixed problem set split across the ranks (strong scaling): this
+        # rank generates and solves only its share, each problem with its
+        # index stream id in the whole set
+        ms_all, ns_all = batched_sizes(P_all, BATCH_SEED)
+        shards = problem_shards(ms_all, ns_all, BATCH_ETA, world)
+        units = shards[rank]
+        A, a_off, m, n, lda, b, b_off, xhats = batched_problem_set(P_all, BATCH_SEED,
+                                                                   subset=units)
+    else:
+        # replicas (weak scaling): every rank solves its own full problem set
+        shards = None
+        units = list(range(P_all))
+        A, a_off, m, n, lda, b, b_off, xhats = batched_problem_set(P_all, BATCH_SEED + rank)
+    P = len(units)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     Ad = torch.from_numpy(A).to(dev)
@@ -500,6 +516,8 @@ def run_batched(args):
     t0 = time.perf_counter()
     bs = BatchSolver(Ad, bd, a_off, m, n, lda, b_off, BATCH_LAM, BATCH_ETA, BATCH_T, BATCH_SEED,
                      stream=stream)
+    if args.shard:
+        bs.set_stream_ids(units)
     setup_s = time.perf_counter() - t0
     # --iters K: every problem runs exactly K iterations (no stopping test)
     max_iters = args.iters if args.iters is not None else BATCH_MAX_ITERS
@@ -522,13 +540,27 @@ def run_batched(args):
     ms_step = max_over_ranks(ms_step, dev)
     iters, rr = bs.results()
     bs.close()
-    updates = float(iters.sum()) * BATCH_ETA
-    value = updates / (ms_step / 1000.0) * world
     hbm_peak, peak_kind = load_peaks()
     row_bytes = float((iters * BATCH_ETA * (4.0 * n + 12.0)).sum())
-    achieved = row_bytes / (ms_step / 1000.0) / 1e9
+    achieved = row_bytes / (ms_step / 1000.0) / 1e9   # this rank's own rows
+    if args.shard:
+        # per-problem results of every rank (after the timed region)
+        by_p = gather_by_unit(units, list(zip(iters.tolist(), rr.tolist())), world)
+        iters_all = np.array([by_p[p][0] for p in range(P_all)], dtype=np.int64)
+        rr_all = np.array([by_p[p][1] for p in range(P_all)])
+        ms_all_, ns_all_ = batched_sizes(P_all, BATCH_SEED)
+        updates = float(iters_all.sum()) * BATCH_ETA
+        value = updates / (ms_step / 1000.0)
+        row_bytes_all = float((iters_all * BATCH_ETA * (4.0 * ns_all_ + 12.0)).sum())
+        achieved = row_bytes_all / (ms_step / 1000.0) / 1e9 / world   # per GPU
+        iters, rr = iters_all, rr_all
+    else:
+        updates = float(iters.sum()) * BATCH_ETA
+        value = updates / (ms_step / 1000.0) * world
     # per-problem comparator: the single-system solver looped over a subset
     sub = list(range(0, P, max(1, P // 32)))
+    if args.shard:
+        sub = []   # the sharded run reports the split, not the comparators
     t_loop = 0.0
     for p in (sub if args.mode != "kernel" else []):
         mp, np_, lp = int(m[p]), int(n[p]), int(lda[p])
@@ -539,9 +571,9 @@ def run_batched(args):
         with Solver(Ap, bp, BATCH_LAM, BATCH_ETA, BATCH_T, BATCH_SEED, n=np_, stream=stream) as sp:
             sp.solve_until(max_iters, -(-mp // BATCH_ETA), tol) if tol > 0 else sp.solve(max_iters)
         t_loop += time.perf_counter() - c0
-    loop_all_s = t_loop * P / len(sub) if args.mode != "kernel" else None
+    loop_all_s = t_loop * P / len(sub) if (args.mode != "kernel" and sub) else None
     cpu = None
-    if not args.skip_cpu:
+    if not args.skip_cpu and sub:
         # one problem per host thread: the C oracle is reentrant and ctypes
         # releases the GIL for the length of each call
         from concurrent.futures import ThreadPoolExecutor
@@ -566,15 +598,22 @@ def run_batched(args):
                "sample": f"the {len(sub)}-problem subset (every {max(1, P // 32)}th problem), one "
                          f"problem per thread on {cores} threads, each run for the iterations "
                          f"the GPU needed: {done_updates // BATCH_ETA} iterations in {el:.1f} s"}
-    line = {"metric": (f"batched RSKA: {P} Gaussian systems to 1e-6 relative residual" if tol > 0
-                       else f"batched RSKA: {P} Gaussian systems, {max_iters} iterations each"),
+    line = {"metric": (f"batched RSKA: {P_all} Gaussian systems to 1e-6 relative residual"
+                       if tol > 0
+                       else f"batched RSKA: {P_all} Gaussian systems, {max_iters} iterations each"),
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(1, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"rska_batched_{P}", "P": P,
+            "scaling": "strong" if args.shard else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"rska_batched_{P_all}", "P": P_all,
                        "m": "log-uniform [200, 4000]", "n": "m/2 rounded to 8", "eta": BATCH_ETA,
                        "t": BATCH_T, "lambda": BATCH_LAM, "tol": tol,
-                       "A_bytes": int(A.nbytes)},
+                       "A_bytes_this_rank": int(A.nbytes),
+                       "parallelism": "sharded" if args.shard else "replicas"},
+            "partition": ({"problems_per_rank": [len(sh) for sh in shards],
+                           "rule": "longest estimated work first (n^2 + m n / eta) to the least "
+                                   "loaded rank", "slowest_rank_ms": ms_step}
+                          if args.shard else None),
             "time_to_all_stopped_ms": ms_step,
             "converged": int((rr <= BATCH_TOL).sum()), "max_iters": max_iters,
             "stalled_at_cap": int((rr > BATCH_TOL).sum()) if tol > 0 else None,
@@ -792,11 +831,21 @@ def run_mrhs(args):
     dev = torch.device("cuda", local)
     build.build()
     from paper_2203_10838_gb300.rska import MultiRHS, Solver
+    from paper_2203_10838_gb300.shard import gather_by_unit, rhs_shards
     t0 = time.perf_counter()
-    p = multi_rhs_problem(MR_M, MR_N, MR_R, MR_S, seed=MR_PSEED + rank)
+    if args.shard:
+        # one A with R right-hand sides split across the ranks (strong
+        # scaling): A is replicated, each rank takes a contiguous block of
+        # right-hand sides, every rank draws the same tau from the same seed
+        p = multi_rhs_problem(MR_M, MR_N, MR_R, MR_S, seed=MR_PSEED)
+        r0, r1 = rhs_shards(MR_R, world)[rank]
+    else:
+        p = multi_rhs_problem(MR_M, MR_N, MR_R, MR_S, seed=MR_PSEED + rank)
+        r0, r1 = 0, MR_R
+    R_loc = r1 - r0
     gen_s = time.perf_counter() - t0
     A16_host = torch.from_numpy(p.A16.view(np.int16)).pin_memory()
-    B_host = torch.from_numpy(p.B).pin_memory()
+    B_host = torch.from_numpy(np.ascontiguousarray(p.B[r0:r1])).pin_memory()
     A = A16_host.to(dev).view(torch.bfloat16)
     B = B_host.to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -822,9 +871,10 @@ def run_mrhs(args):
     ms = e0.elapsed_time(e1) / args.steps
     from paper_2203_10838_gb300.shard import max_over_ranks
     ms = max_over_ranks(ms, dev)
-    updates = MR_ETA * MR_R * MR_K
-    value = updates / (ms / 1000.0) * world
-    flops = 4.0 * MR_ETA * MR_N * MR_R * MR_K   # the two products, multiply-add = 2 flops
+    updates = MR_ETA * R_loc * MR_K   # this rank's row-updates per step
+    # whole job: sharded ranks split the 512 right-hand sides, replicas each run all of them
+    value = (MR_ETA * MR_R * MR_K if args.shard else updates * world) / (ms / 1000.0)
+    flops = 4.0 * MR_ETA * MR_N * R_loc * MR_K   # the two products, multiply-add = 2 flops
     achieved = flops / (ms / 1000.0) / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -839,11 +889,16 @@ def run_mrhs(args):
     # accuracy of the timed solve: relative residual and error per right-hand side (FP64)
     x, _ = h.get_x()
     A64 = A.double()
-    res = (x.double() @ A64[:, :MR_N].t()) - torch.from_numpy(p.B64).to(dev)
-    rr = (res.norm(dim=1) / torch.from_numpy(p.B64).to(dev).norm(dim=1)).cpu().numpy()
-    xh = torch.from_numpy(p.Xhat).to(dev)
+    B64 = torch.from_numpy(np.ascontiguousarray(p.B64[r0:r1])).to(dev)
+    res = (x.double() @ A64[:, :MR_N].t()) - B64
+    rr = (res.norm(dim=1) / B64.norm(dim=1)).cpu().numpy()
+    xh = torch.from_numpy(np.ascontiguousarray(p.Xhat[r0:r1])).to(dev)
     re = ((x.double() - xh).norm(dim=1) / xh.norm(dim=1)).cpu().numpy()
-    del A64, res
+    del A64, res, B64
+    if args.shard:
+        by_j = gather_by_unit(range(r0, r1), list(zip(rr.tolist(), re.tolist())), world)
+        rr = np.array([by_j[j][0] for j in range(MR_R)])
+        re = np.array([by_j[j][1] for j in range(MR_R)])
     terms = h.query("terms")
     ksplit = h.query("ksplit")
     # end to end through the public API: H2D of A and B, setup, K iterations, D2H of X
@@ -895,12 +950,17 @@ def run_mrhs(args):
                       "eta=256)",
             "value": value, "unit": "row-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands, f32 accumulate",
-            "data": "synthetic",
+            "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
+            "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
             "config": {"workload": "rska_mrhs_16384x8192_R512", "m": MR_M, "n": MR_N, "R": MR_R,
                        "nnz": MR_S, "eta": MR_ETA, "t": MR_T, "lambda": MR_LAM,
                        "iters_per_step": MR_K, "terms": terms, "ksplit": ksplit,
-                       "l2": "A is 256 MB (> L2); rows of A are sampled at random"},
+                       "l2": "A is 256 MB (> L2); rows of A are sampled at random",
+                       "parallelism": "sharded" if args.shard else "replicas"},
+            "partition": ({"rhs_per_rank": [b - a for a, b in rhs_shards(MR_R, world)],
+                           "rule": "contiguous blocks of right-hand sides; A replicated, one "
+                                   "index stream", "slowest_rank_ms": ms}
+                          if args.shard else None),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_kind": "measured cuBLAS bf16, sustained",
@@ -912,7 +972,7 @@ def run_mrhs(args):
                          "rel_error_median": float(np.median(re)),
                          "after_iterations": MR_K},
             "e2e": {"value": updates / e2e_s, "unit": "row-updates/s",
-                    "h2d_bytes_per_step": int(p.A16.nbytes + p.B.nbytes),
+                    "h2d_bytes_per_step": int(p.A16.nbytes + B_host.numel() * 4),
                     "d2h_bytes_per_step": int(xe.numel() * 4),
                     "includes": "H2D of A (BF16) and B, setup (FP64 norms + alias table), "
                                 "K iterations, D2H of X"},
@@ -1055,6 +1115,9 @@ def main():
                     help="kernel: only the timed persistent-kernel steps (for profiling)")
     ap.add_argument("--batch-p", type=int, default=BATCH_P,
                     help="batched workload: number of problems (default 4096)")
+    ap.add_argument("--shard", action="store_true",
+                    help="batched / mrhs: split one problem set (one set of right-hand sides) "
+                         "across the ranks instead of running a replica per rank")
     ap.add_argument("--iters", type=int, default=None,
                     help="iterations per step (default 300; profiling uses fewer)")
     args = ap.parse_args()

@@ -273,7 +273,8 @@ int rska_linearized_bregman(rska_ctx *ctx, int64_t K, double step);
 /* ------------------------------------------------------------------------ */
 /* Batched independent systems: eq. (rska) / Algorithm 1 run on P problems   */
 /* (A_p, b_p) in one persistent launch, each with its own index stream       */
-/* (counter word 3 of the index contract = p) and its own stopping test.     */
+/* (counter word 3 of the index contract = the problem's stream id, p unless */
+/* rska_batch_set_stream_ids says otherwise) and its own stopping test.      */
 /* ------------------------------------------------------------------------ */
 typedef struct rska_batch rska_batch;
 
@@ -307,6 +308,16 @@ int rska_batch_setup(rska_batch **out, int32_t P, const float *A, const int64_t 
  * problem at a time, problems taken largest first.  Asynchronous.
  */
 int rska_batch_solve(rska_batch *bt, int64_t max_iters, double tol, int64_t check_every);
+
+/*
+ * rska_batch_set_stream_ids -- HOST: the index-stream id of each problem
+ * (counter word 3 of the index contract), P entries read during the call;
+ * by default problem p uses id p.  A caller that splits one problem set
+ * across several batches (one per GPU) gives every problem its id in the
+ * whole set, so each problem draws the same tau_k wherever it runs.  Applies
+ * from the next rska_batch_solve.  Synchronizes.  Errors: EINVAL, ECUDA.
+ */
+int rska_batch_set_stream_ids(rska_batch *bt, const uint32_t *ids);
 
 /* rska_batch_results -- HOST outputs (P entries each, nullable): iterations
  * run and the last exact relative residual per problem.  Synchronizes. */

@@ -44,6 +44,7 @@ def _declare(lib):
         "rska_sigma_max2": ([P, i32, u64, ctypes.POINTER(f64), ctypes.POINTER(f64),
                              ctypes.POINTER(f64)], c_int),
         "rska_batch_setup": ([PP, i32, P, P, P, P, P, P, P, f32, i32, f32, u64, P], c_int),
+        "rska_batch_set_stream_ids": ([P, P], c_int),
         "rska_batch_solve": ([P, i64, f64, i64], c_int),
         "rska_batch_results": ([P, P, P], c_int),
         "rska_batch_offsets": ([P, P], c_int),

@@ -78,6 +78,7 @@ struct BatchArgs {
   const double* W;           // sum of ||a_i||^2 per problem
   const double* bnorm2;      // ||b_p||^2
   const int64_t* x_off;      // offset of problem p in z / x (n rounded up to 4)
+  const uint32_t* sid;       // index-stream id of problem p (counter word 3; default p)
   float* z;
   float* x;
   int64_t* iters;
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(BT, 1) rska_batched_kernel(BatchArgs a) {
           ++jj;
         }
         int32_t i0, i1;
-        draw_pair(a.seed, jj, (uint32_t)(s >> 1), (uint32_t)p, a.thr + ro, a.alias + ro,
+        draw_pair(a.seed, jj, (uint32_t)(s >> 1), a.sid[p], a.thr + ro, a.alias + ro,
                   (uint32_t)m, &i0, &i1);
         const int32_t row = (s & 1) ? i1 : i0;
         const int slot = (int)(e + lane) & (BIR - 1);
@@ -747,6 +748,7 @@ struct rska_batch {
   int* pstat = nullptr;
   int* queue = nullptr;
   int* status = nullptr;
+  uint32_t* d_sid = nullptr;        // index-stream id per problem
   int sticky = RSKA_OK;
   uint64_t limit_ns = 2000000000ull;
 };
@@ -757,7 +759,7 @@ void batch_free(rska_batch* bt) {
   void* ptrs[] = {bt->d_order, bt->d_a_off, bt->d_m,   bt->d_n,     bt->d_lda,  bt->d_b_off,
                   bt->d_row_off, bt->d_x_off, bt->nu,  bt->inv_nu,  bt->thr,    bt->alias,
                   bt->W,       bt->bnorm2,  bt->z,     bt->x,       bt->iters,  bt->relres,
-                  bt->pstat,   bt->queue,   bt->status};
+                  bt->pstat,   bt->queue,   bt->status, bt->d_sid};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -785,6 +787,7 @@ BatchArgs make_args(rska_batch* bt) {
   a.W = bt->W;
   a.bnorm2 = bt->bnorm2;
   a.x_off = bt->d_x_off;
+  a.sid = bt->d_sid;
   a.z = bt->z;
   a.x = bt->x;
   a.iters = bt->iters;
@@ -874,9 +877,13 @@ int rska_batch_setup(rska_batch** out, int32_t P, const float* A, const int64_t*
        (e = dalloc(&bt->x, xs)) != cudaSuccess || (e = dalloc(&bt->iters, P)) != cudaSuccess ||
        (e = dalloc(&bt->relres, P)) != cudaSuccess || (e = dalloc(&bt->pstat, P)) != cudaSuccess ||
        (e = dalloc(&bt->queue, 1)) != cudaSuccess || (e = dalloc(&bt->status, 1)) != cudaSuccess ||
+       (e = dalloc(&bt->d_sid, P)) != cudaSuccess ||
        (e = dalloc(&q, rows)) != cudaSuccess || (e = dalloc(&stk, rows)) != cudaSuccess)) {
   }
   cudaStream_t s = bt->stream;
+  std::vector<uint32_t> sid(P);
+  std::iota(sid.begin(), sid.end(), 0u);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_sid, sid.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_order, order.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_a_off, a_off, sizeof(int64_t) * P, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(bt->d_m, hm.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice, s);
@@ -921,6 +928,14 @@ int rska_batch_setup(rska_batch** out, int32_t P, const float* A, const int64_t*
   }
   *out = bt;
   return RSKA_OK;
+}
+
+int rska_batch_set_stream_ids(rska_batch* bt, const uint32_t* ids) {
+  if (!bt || !ids) return RSKA_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(bt->d_sid, ids, sizeof(uint32_t) * bt->P, cudaMemcpyHostToDevice,
+                                  bt->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);
+  return e == cudaSuccess ? RSKA_OK : RSKA_ECUDA;
 }
 
 int rska_batch_solve(rska_batch* bt, int64_t max_iters, double tol, int64_t check_every) {

@@ -269,6 +269,16 @@ class BatchSolver:
     def __exit__(self, *exc):
         self.close()
 
+    def set_stream_ids(self, ids):
+        """Index-stream id of each problem (counter word 3 of the index
+        contract; default: its position in this batch)."""
+        import numpy as np
+        arr = np.ascontiguousarray(ids, dtype=np.uint32)
+        if arr.shape != (self.P,):
+            raise ValueError("one stream id per problem")
+        check(lib().rska_batch_set_stream_ids(self._h, ctypes.c_void_p(arr.ctypes.data)),
+              "rska_batch_set_stream_ids")
+
     def solve(self, max_iters: int, tol: float = 0.0, check_every: int = 0):
         check(lib().rska_batch_solve(self._h, int(max_iters), float(tol), int(check_every)),
               "rska_batch_solve")

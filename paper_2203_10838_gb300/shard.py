@@ -4,7 +4,8 @@ Every form of the path shards without a data-path collective: the batched
 and unrolled forms are independent problems, the multi-RHS form has
 independent right-hand sides that share A and the index stream (each rank
 holds A and draws the same tau from the same seed).  Ranks only agree on the
-timing (maximum over ranks).  No device work happens here.
+timing (maximum over ranks) and, after the timed region, gather the
+per-problem (or per-right-hand-side) results.  No device work happens here.
 """
 from __future__ import annotations
 
@@ -54,3 +55,38 @@ def max_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def gather_by_unit(mine, results, world: int):
+    """Every rank's per-unit results gathered on every rank: a dict from unit
+    index (problem or right-hand side) to its result.  `mine` lists this
+    rank's units and `results` their results in the same order."""
+    mine = [int(u) for u in mine]
+    results = list(results)
+    if len(mine) != len(results):
+        raise ValueError("one result per unit")
+    if world == 1:
+        return dict(zip(mine, results))
+    import torch.distributed as dist
+    gathered = [None] * world
+    dist.all_gather_object(gathered, (mine, results))
+    out = {}
+    for units, res in gathered:
+        for u, r in zip(units, res):
+            if u in out:
+                raise RuntimeError(f"unit {u} solved on two ranks")
+            out[u] = r
+    return out
+
+
+def sharded_run(shards, solve, rank: int, world: int, device=None):
+    """The rank loop of the sharded batched and multi-RHS forms: this rank
+    solves its share `shards[rank]` (a list of unit indices) with
+    `solve(units) -> (results, seconds)`, results in the order of `units` and
+    seconds the rank's timed solve; then the slowest rank's time is agreed
+    (maximum over ranks) and the results of every rank are gathered.
+    Returns (results by unit index, this rank's seconds, slowest seconds)."""
+    mine = list(shards[rank])
+    results, seconds = solve(mine)
+    slowest = max_over_ranks(seconds, device)
+    return gather_by_unit(mine, results, world), float(seconds), slowest

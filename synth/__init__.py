@@ -104,15 +104,21 @@ def pack_batch(problems):
     return A, as64(a_off), as64(m), as64(n), as64(lda), b, as64(b_off)
 
 
-def batched_problem_set(P: int, seed: int, m_lo: int = 200, m_hi: int = 4000, threads: int = 0):
+def batched_problem_set(P: int, seed: int, m_lo: int = 200, m_hi: int = 4000, threads: int = 0,
+                        subset=None):
     """The batched workload of independent Gaussian systems, generated straight
     into packed arrays: m_p log-uniform in [m_lo, m_hi], n_p = m_p / 2 rounded
     to a multiple of 8, s_p = n_p / 20, problem p drawn exactly as
     gaussian_problem(m_p, n_p, s_p, seed + 1 + p).  Returns (A_flat, a_off, m,
-    n, lda, b_flat, b_off, xhats)."""
+    n, lda, b_flat, b_off, xhats).  With ``subset`` (problem indices of the
+    P-problem set) only those problems are generated and packed, in the given
+    order, each with exactly the values it has in the whole set."""
     import concurrent.futures
     import os
     ms, ns = batched_sizes(P, seed, m_lo, m_hi)
+    ids = np.arange(P, dtype=np.int64) if subset is None else np.asarray(subset, dtype=np.int64)
+    ms, ns = ms[ids], ns[ids]
+    P = len(ids)
     ldas = np.array([round_up(int(v), 4) for v in ns], dtype=np.int64)
     sizes = np.array([round_up(int(mm) * int(ll), 4) for mm, ll in zip(ms, ldas)], dtype=np.int64)
     a_off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
@@ -124,7 +130,7 @@ def batched_problem_set(P: int, seed: int, m_lo: int = 200, m_hi: int = 4000, th
     def make(p):
         m, n, lda = int(ms[p]), int(ns[p]), int(ldas[p])
         view = A[a_off[p]:a_off[p] + m * lda].reshape(m, lda)
-        rng = np.random.default_rng(seed + 1 + p)
+        rng = np.random.default_rng(seed + 1 + int(ids[p]))
         if lda == n:
             rng.standard_normal(out=view, dtype=np.float32)
         else:
