@@ -317,38 +317,60 @@ def run_gpu(args):
             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1000.0,
             "grid": sol.query("grid"), "rows_resident": sol.query("rows_resident")}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers.  One context is
+    # made from the pinned host buffers before the loop (rska_setup_host: it
+    # allocates the library's device copy of A once); every step then loads the
+    # step's problem from pinned host memory into it (rska_load_host: H2D in
+    # row chunks overlapped with the FP64 row norms and the sum of W, then the
+    # alias table), solves, and reads x back to pinned host memory.
     e2e = None
-    e2e_steps = 0 if args.skip_e2e else max(2, min(args.steps, 5))
+    e2e_steps = 0 if args.skip_e2e else max(3, min(args.steps, 10))
     torch.cuda.synchronize(dev)
     x_host = torch.empty(N, dtype=torch.float32).pin_memory()
-    # rska_setup_host takes the pinned host buffers: the library copies A in row
-    # chunks while the row norms and the sum of W run on the landed chunks
-    parts = {"setup_with_h2d_ms": 0.0, "solve_ms": 0.0, "d2h_and_teardown_ms": 0.0}
-    e0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        c_setup = time.perf_counter()
-        with Solver(A_host, b_host, LAM, ETA, T_STEP, SEED, n=N, stream=stream) as s2:
-            setup_host = time.perf_counter() - c_setup
+    if e2e_steps:
+        parts = {"load_with_h2d_ms": 0.0, "solve_ms": 0.0, "d2h_ms": 0.0}
+        inside = {"h2d_norms_w_ms": 0.0, "alias_table_ms": 0.0}
+        c_first = time.perf_counter()
+        s2 = Solver(A_host, b_host, LAM, ETA, T_STEP, SEED, n=N, stream=stream)
+        first_setup = {"setup_ms": (time.perf_counter() - c_first) * 1000.0,
+                       "alloc_ms": s2.query("setup_alloc_us") / 1000.0,
+                       "h2d_norms_w_ms": s2.query("setup_norms_us") / 1000.0,
+                       "alias_table_ms": s2.query("setup_alias_us") / 1000.0}
+        s2.solve(ITERS)   # warm the path once
+        s2.get_x()
+        torch.cuda.synchronize(dev)
+        e0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            c_load = time.perf_counter()
+            s2.load_host(A_host, b_host)
+            load_s = time.perf_counter() - c_load
+            inside["h2d_norms_w_ms"] += s2.query("setup_norms_us") / 1000.0
+            inside["alias_table_ms"] += s2.query("setup_alias_us") / 1000.0
             ev[0].record(stream)
             s2.solve(ITERS)
             ev[1].record(stream)
+            c_d2h = time.perf_counter()
             xd, _ = s2.get_x()
             x_host.copy_(xd, non_blocking=True)
-        c_end = time.perf_counter()
-        torch.cuda.synchronize(dev)
-        parts["setup_with_h2d_ms"] += setup_host * 1000.0
-        parts["solve_ms"] += ev[0].elapsed_time(ev[1])
-        parts["d2h_and_teardown_ms"] += (time.perf_counter() - c_end) * 1000.0
-    if e2e_steps:
+            torch.cuda.synchronize(dev)
+            parts["load_with_h2d_ms"] += load_s * 1000.0
+            parts["solve_ms"] += ev[0].elapsed_time(ev[1])
+            parts["d2h_ms"] += (time.perf_counter() - c_d2h) * 1000.0
         e2e_s = (time.perf_counter() - e0) / e2e_steps
+        s2.close()
         e2e = {"value": ETA * ITERS * world / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(A_host.numel() * 4 + b_host.numel() * 4),
                "d2h_bytes_per_step": int(N * 4),
-               "includes": "rska_setup_host from pinned host A and b (H2D overlapped with the "
-                           "FP64 norms and the sum of W, then the alias table), solve, D2H of x",
-               "parts_ms_per_step": {k: v / e2e_steps for k, v in parts.items()}}
+               "includes": "per step: rska_load_host of A and b from pinned host memory into a "
+                           "context made once by rska_setup_host (H2D in row chunks overlapped "
+                           "with the FP64 row norms and the sum of W, then the alias table), "
+                           f"the {ITERS}-iteration solve, D2H of x",
+               "parts_ms_per_step": {k: v / e2e_steps for k, v in parts.items()},
+               "load_inside_ms_per_step": {k: v / e2e_steps for k, v in inside.items()},
+               "h2d_gbs_link_bound": (A_host.numel() * 4) / (inside["h2d_norms_w_ms"] / e2e_steps
+                                                              / 1000.0) / 1e9,
+               "first_setup": first_setup}
 
     # plain per-iteration PyTorch RSKA on the same GPU (comparator)
     plain = None
@@ -458,10 +480,8 @@ def run_gpu(args):
                              "after_iterations": ITERS},
                 "plain_rska_gpu": plain, "time_to_accuracy": tta, "eta_sweep": sweep,
                 "step": step, "linearized_bregman": lb}
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+        return line
+    return None
 
 
 # --------------------------------------------------------------------------
@@ -633,9 +653,7 @@ def run_batched(args):
             "prep": {"generate_s": gen_s, "h2d_s": h2d_s, "setup_s": setup_s},
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": args.steps}   # one rska_batched_kernel per solve
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line if rank == 0 else None
 
 
 # --------------------------------------------------------------------------
@@ -808,9 +826,7 @@ def run_unrolled(args):
             "cpu_baseline": cpu, "clocks": clk,
             # per step: unrolled_gather_b_kernel, unrolled_fwd_rows_kernel, unrolled_bwd_rows_kernel
             "gpu_launches": 3 * args.steps}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line if rank == 0 else None
 
 
 # --------------------------------------------------------------------------
@@ -881,11 +897,9 @@ def run_mrhs(args):
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     if args.mode == "kernel":
         h.close()
-        if rank == 0:
-            print(json.dumps({"metric": "shared-A multi-RHS RSKA (kernel-only run for profiling)",
-                              "ms_per_step": ms, "iters_per_step": MR_K,
-                              "tflops": achieved}), flush=True)
-        return 0
+        return ({"metric": "shared-A multi-RHS RSKA (kernel-only run for profiling)",
+                 "ms_per_step": ms, "iters_per_step": MR_K, "tflops": achieved}
+                if rank == 0 else None)
     # accuracy of the timed solve: relative residual and error per right-hand side (FP64)
     x, _ = h.get_x()
     A64 = A.double()
@@ -983,9 +997,7 @@ def run_mrhs(args):
             "gpu_launches": 4 * MR_K * args.steps + 2 * args.steps,
             "prep": {"generate_s": gen_s},
             "cpu_baseline": cpu, "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line if rank == 0 else None
 
 
 # --------------------------------------------------------------------------
@@ -1024,7 +1036,7 @@ def run_plateau(args):
     from synth import gaussian_problem
     rank, world, local = dist_env()
     if rank != 0:
-        return 0
+        return None
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
@@ -1095,8 +1107,7 @@ def run_plateau(args):
             # per timed solve chunk: the pre-sampler and the solve kernel (each
             # chunk of ceil(m/eta) iterations fits one pre-sample of 2^21 draws)
             "gpu_launches": 2 * sum(r["checks"] for r in runs)}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def main():
@@ -1118,6 +1129,8 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="batched / mrhs: split one problem set (one set of right-hand sides) "
                          "across the ranks instead of running a replica per rank")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="single workload: leave out the batched, unrolled and multi-RHS keys")
     ap.add_argument("--iters", type=int, default=None,
                     help="iterations per step (default 300; profiling uses fewer)")
     args = ap.parse_args()
@@ -1131,15 +1144,46 @@ def main():
         args.skip_e2e = False
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batched":
-        return run_batched(args)
-    if args.workload == "unrolled":
-        return run_unrolled(args)
-    if args.workload == "mrhs":
-        return run_mrhs(args)
-    if args.workload == "plateau":
-        return run_plateau(args)
-    return run_gpu(args)
+    runners = {"single": run_gpu, "batched": run_batched, "unrolled": run_unrolled,
+               "mrhs": run_mrhs, "plateau": run_plateau}
+    line = runners[args.workload](args)
+    _, world, _ = dist_env()
+    if (line is not None and args.workload == "single" and args.mode == "full"
+            and not args.no_forms and world == 1):
+        # the other forms of the path, each in its own timed region with its
+        # own clocks, at their full per-problem sizes
+        line.update(run_other_forms(args))
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+    return 0
+
+
+def run_other_forms(args):
+    """The batched (4096 systems to 1e-6), unrolled (64 x 2048 x 1024 forward +
+    adjoint) and shared-A multi-RHS (16384 x 8192, 512 right-hand sides)
+    workloads, each with a few timed steps, returned as extra keys of the
+    single-system line.  Device memory is released between them."""
+    import copy
+
+    import torch
+    out = {}
+    plan = [("batched", run_batched, 2, 1), ("unrolled", run_unrolled, 10, 3),
+            ("mrhs", run_mrhs, 5, 3)]
+    for key, fn, steps, warmup in plan:
+        sub = copy.copy(args)
+        sub.steps, sub.warmup, sub.workload, sub.shard, sub.iters = steps, warmup, key, False, None
+        sub.batch_p = BATCH_P
+        t0 = time.perf_counter()
+        res = fn(sub)
+        if res is not None:
+            res["wall_s"] = time.perf_counter() - t0
+        out[key] = res
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

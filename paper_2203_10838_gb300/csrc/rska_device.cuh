@@ -125,16 +125,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
     const uint64_t t0 = global_timer_ns();
     uint32_t spins = 0;
     while (ld_acquire_u64(counter) < target) {
-      if ((++spins & 63u) == 0) {
-        if (ld_relaxed_s32(status) != kStatusOk) {
-          ok = 0;
-          break;
-        }
-        if (global_timer_ns() - t0 > limit_ns) {
-          atomicCAS(status, kStatusOk, kStatusTimeout);
-          ok = 0;
-          break;
-        }
+      if (global_timer_ns() - t0 > limit_ns) {
+        atomicCAS(status, kStatusOk, kStatusTimeout);
+        ok = 0;
+        break;
+      }
+      if ((++spins & 7u) == 0 && ld_relaxed_s32(status) != kStatusOk) {
+        ok = 0;
+        break;
       }
     }
     __threadfence();

@@ -79,9 +79,8 @@ __device__ __forceinline__ bool mb_try_wait(uint64_t* b, uint32_t parity) {
 __device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns) {
   if (mb_try_wait(b, parity)) return true;
   const uint64_t t0 = global_timer_ns();
-  uint32_t spins = 0;
   while (!mb_try_wait(b, parity)) {
-    if ((++spins & 255u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
+    if (global_timer_ns() - t0 > limit_ns) return false;
   }
   return true;
 }

@@ -116,17 +116,15 @@ __device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
 }
 
 // Bounded wait on an mbarrier phase: false after limit_ns, or once *abort is
-// set (when abort is given).  The timer is read every 64 polls.
+// set (when abort is given).  The timer is read after every poll, so even a
+// limit of a microsecond is enforced.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity, uint64_t limit_ns,
                                                   const volatile int* abort) {
   if (mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = global_timer_ns();
-  uint32_t spins = 0;
   while (!mbar_try_wait(b, parity)) {
-    if ((++spins & 63u) == 0) {
-      if (global_timer_ns() - t0 > limit_ns) return false;
-      if (abort != nullptr && *abort) return false;
-    }
+    if (global_timer_ns() - t0 > limit_ns) return false;
+    if (abort != nullptr && *abort) return false;
   }
   return true;
 }
@@ -440,16 +438,14 @@ __global__ void __launch_bounds__(NT, 1)
       const uint64_t t0 = global_timer_ns();
       uint32_t spins = 0;
       while (ld_acquire_u64(a.bar) < target) {
-        if ((++spins & 15u) == 0) {
-          if (ld_relaxed_s32(a.status) != kStatusOk) {
-            ok = 0;
-            break;
-          }
-          if (global_timer_ns() - t0 > a.limit_ns) {
-            atomicCAS(a.status, kStatusOk, kStatusTimeout);
-            ok = 0;
-            break;
-          }
+        if (global_timer_ns() - t0 > a.limit_ns) {
+          atomicCAS(a.status, kStatusOk, kStatusTimeout);
+          ok = 0;
+          break;
+        }
+        if ((++spins & 7u) == 0 && ld_relaxed_s32(a.status) != kStatusOk) {
+          ok = 0;
+          break;
         }
       }
       // the acquire load that saw the count orders this CTA's reads of the
