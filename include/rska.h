@@ -422,6 +422,13 @@ int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_
  * launches every kernel directly.  what = 4: 1 (default) launches each
  * kernel of an iteration as a programmatic dependent of the previous one
  * (its prologue overlaps the previous kernel's tail), 0 orders them fully.
+ * what = 5: form of the iteration: 0 automatic, 1 staged kernels (gather,
+ * residual product, scale, update product per iteration; options 1, 3, 4
+ * apply), 2 one persistent kernel per launch of up to 512 iterations that
+ * keeps Z^T in tensor memory (each CTA owns 128 right-hand sides x 256
+ * columns; needs eta <= 256 and (n_p / 256) (R_p / 128) CTAs resident at
+ * once, else EUNSUPPORTED).  what = 6: terms of the scaled residual in the
+ * second product (1 or 2; 0 = the same as option 0).
  * EINVAL for an unknown `what` or value.
  */
 int rska_mrhs_set_option(rska_mrhs *h, int what, int64_t value);
@@ -429,7 +436,9 @@ int rska_mrhs_set_option(rska_mrhs *h, int what, int64_t value);
 /*
  * rska_mrhs_query -- HOST *value: what = 0 iterations done, 1 CTAs of the
  * first product's split over n, 2 n padded (multiple of 256), 3 eta padded
- * (multiple of 128), 4 R padded (multiple of 256), 5 terms (option 0).
+ * (multiple of 128), 4 R padded (multiple of 256), 5 terms (option 0),
+ * 6 form of the next solve (1 staged, 2 persistent), 7 terms of the scaled
+ * residual.
  */
 int rska_mrhs_query(rska_mrhs *h, int what, int64_t *value);
 

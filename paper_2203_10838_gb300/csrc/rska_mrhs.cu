@@ -35,6 +35,8 @@
 
 #include "rska_device.cuh"
 #include "rska_internal.h"
+#include "rska_mrhs_tmem.h"
+#include "rska_tc.cuh"
 
 namespace rska {
 namespace {
@@ -50,180 +52,12 @@ constexpr size_t ZREG0 = 131072;                  // update: first half of the z
 
 enum GemmMode { kResidual = 0, kUpdate = 1 };
 
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mb_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mb_try_wait(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(saddr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase: false after limit_ns (the caller records
-// the timeout and winds down instead of hanging).
-__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns) {
-  if (mb_try_wait(b, parity)) return true;
-  const uint64_t t0 = global_timer_ns();
-  while (!mb_try_wait(b, parity)) {
-    if (global_timer_ns() - t0 > limit_ns) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-      "%3}], [%4];" ::"r"(saddr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
-      : "memory");
-}
-
-// Bulk tensor store / reduce-add of a shared-memory box to global memory
-// (bulk-group completion), and the L2 prefetch of a box.
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-          reinterpret_cast<uint64_t>(map)),
-      "r"(x), "r"(y), "r"(saddr(src))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, const void* src, int x,
-                                                  int y) {
-  asm volatile(
-      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], "
-      "[%3];" ::"l"(reinterpret_cast<uint64_t>(map)),
-      "r"(x), "r"(y), "r"(saddr(src))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(x), "r"(y)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() {
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-
-// All committed bulk groups have finished reading their shared-memory source.
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-
-// All but the most recent committed bulk group have finished reading their
-// shared-memory source.
-__device__ __forceinline__ void bulk_wait_read_all_but_one() {
-  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-}
-
-// Programmatic dependent launch: wait until the preceding kernel in the
-// stream has completed and its writes are visible (returns at once for an
-// ordinary launch); let the next kernel start its prologue.
-__device__ __forceinline__ void pdl_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// Generic-proxy shared-memory writes become visible to the async proxy (TMA).
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Byte offset of 16-byte chunk `chunk` of row `row` in a box of 128-byte rows
-// written or read by TMA with the 128-byte swizzle (box base 1024-aligned).
-__device__ __forceinline__ uint32_t sw128_off(int row, int chunk) {
-  return (uint32_t)(row * 128 + ((chunk ^ (row & 7)) << 4));
-}
-
-// Shared-memory matrix descriptor of a K-major tile written by TMA with the
-// 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart
-// (stride byte offset), descriptor version 1, swizzle mode 2 (128 B).  The
-// leading byte offset is unused for this layout.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t smem_addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
+using namespace tc;
 
 // Instruction descriptor for kind::f16: D FP32, A and B BF16, both K-major,
 // M = 128, N = 256.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                             ((uint32_t)(TM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          saddr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-// 32 consecutive FP32 columns of this warp's 32 tensor-memory lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// v = hi + lo with hi = bf16(v), lo = bf16(v - hi) (round to nearest even).
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  *hi = h;
-  *lo = __float2bfloat16_rn(v - __bfloat162float(h));
-}
 
 struct GemmArgs {
   int nsplit;          // 1: the inexact operand as one BF16 term, 2: hi + lo
@@ -691,6 +525,18 @@ struct rska_mrhs {
   cudaGraphExec_t graph = nullptr;   // one chunk of idx_cap iterations
   int graph_nsplit = -1, graph_ksplit = -1, graph_pdl = -1;
   uint64_t graph_limit_ns = 0;       // the wait limit baked into the graph's kernel arguments
+  // persistent form (rska_mrhs_tmem.cu): Z^T in tensor memory for a launch
+  int form_opt = 0;                  // 0 automatic, 1 staged kernels, 2 persistent
+  int form = 1;                      // form of the next solve
+  int nsplit_r = 0;                  // terms of the scaled residual (0: as nsplit)
+  bool x_stale = false;              // X hi/lo (staged form state) lag behind Z
+  int64_t eta_p64 = 0;               // eta rounded up to 64
+  __nv_bfloat16* G = nullptr;        // 2 x eta_p64 x n_p dense A_tau copies
+  float* Res3 = nullptr;             // 3 x R_p x eta_p64 residual accumulators
+  unsigned long long* pbar = nullptr;
+  int32_t* pidx = nullptr;           // tau of one persistent launch
+  int64_t pidx_cap = 0;
+  CUtensorMap mapG;
 };
 
 namespace {
@@ -742,7 +588,7 @@ void mrhs_free(rska_mrhs* h) {
   if (h->side) cudaStreamDestroy(h->side);
   void* ptrs[] = {h->nu,       h->inv_nu,   h->thr, h->alias, h->Bt,  h->Atau[0], h->Atau[1],
                   h->AtauT[0], h->AtauT[1], h->Xhi, h->Xlo,   h->Rhi, h->Rlo,     h->Zt,
-                  h->Res,      h->idx,      h->status};
+                  h->Res,      h->idx,      h->status, h->G,  h->Res3, h->pbar,   h->pidx};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -868,6 +714,118 @@ __global__ void mrhs_out_kernel(const float* __restrict__ Zt, int64_t ldz, int64
   }
 }
 
+// X hi/lo of the staged form from Z^T (after persistent launches, which keep
+// no X in global memory): x = S_lambda(z) split into BF16 high and low parts.
+__global__ void mrhs_x_from_z_kernel(const float* __restrict__ Zt, int64_t total, float lambda,
+                                     __nv_bfloat16* __restrict__ xhi,
+                                     __nv_bfloat16* __restrict__ xlo) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    __nv_bfloat16 hv, lv;
+    rska::tc::split_bf16(rska::soft_shrink(Zt[e], lambda), &hv, &lv);
+    xhi[e] = hv;
+    xlo[e] = lv;
+  }
+}
+
+// K iterations with the staged kernels (gather, residual product, scale,
+// update product per iteration; 64-iteration chunks replayed as a graph).
+cudaError_t solve_staged(rska_mrhs* h, int64_t K) {
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaSuccess;
+  if (h->x_stale && K > 0) {
+    // the persistent form kept X in tensor memory only
+    const int64_t total = h->R_p * h->n_p;
+    mrhs_x_from_z_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(
+        h->Zt, total, h->lambda, h->Xhi, h->Xlo);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    h->x_stale = false;
+  }
+  for (int64_t done = 0; done < K && e == cudaSuccess;) {
+    const int64_t cnt = std::min(h->idx_cap, K - done);
+    e = rska::launch_indices(h->thr, h->alias, h->m, h->seed, 0, h->k_host + done, cnt, h->eta,
+                             h->idx, s);
+    if (e != cudaSuccess) break;
+    if (cnt == h->idx_cap && h->use_graph) {
+      if (!h->graph || h->graph_nsplit != h->nsplit || h->graph_ksplit != h->ksplit ||
+          h->graph_pdl != h->use_pdl || h->graph_limit_ns != h->limit_ns) {
+        if (h->graph) {
+          cudaGraphExecDestroy(h->graph);
+          h->graph = nullptr;
+        }
+        cudaStream_t cap = nullptr;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          const cudaError_t e1 = enqueue_iterations(h, cnt, cap);
+          e = cudaStreamEndCapture(cap, &g);
+          if (e == cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (cap) cudaStreamDestroy(cap);
+        if (e != cudaSuccess) break;
+        h->graph_nsplit = h->nsplit;
+        h->graph_ksplit = h->ksplit;
+        h->graph_pdl = h->use_pdl;
+        h->graph_limit_ns = h->limit_ns;
+      }
+      e = cudaGraphLaunch(h->graph, s);
+    } else {
+      e = enqueue_iterations(h, cnt, s);
+    }
+    done += cnt;
+  }
+  return e;
+}
+
+// K iterations with the persistent kernel: per launch of up to pidx_cap
+// iterations, the indices are drawn, the residual accumulators and the
+// barrier counter cleared, and Z^T stays in tensor memory for the launch.
+cudaError_t solve_tmem(rska_mrhs* h, int64_t K) {
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaSuccess;
+  rska::MrhsTmemArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.A = h->A;
+  a.lda = h->lda;
+  a.n = h->n;
+  a.n_p = h->n_p;
+  a.R_p = h->R_p;
+  a.eta = h->eta;
+  a.eta_p = (int32_t)h->eta_p64;
+  a.n_slices = (int32_t)(h->n_p / 256);
+  a.r_slices = (int32_t)(h->R_p / 128);
+  a.idx = h->pidx;
+  a.inv_nu = h->inv_nu;
+  a.Bt = h->Bt;
+  a.G = h->G;
+  a.Zt = h->Zt;
+  a.Res = h->Res3;
+  a.bar = h->pbar;
+  a.lambda = h->lambda;
+  a.coef = h->t / (float)h->eta;
+  a.nsplit_x = h->nsplit;
+  a.nsplit_r = h->nsplit_r > 0 ? h->nsplit_r : h->nsplit;
+  a.status = h->status;
+  a.limit_ns = h->limit_ns;
+  for (int64_t done = 0; done < K && e == cudaSuccess;) {
+    const int64_t cnt = std::min(h->pidx_cap, K - done);
+    e = rska::launch_indices(h->thr, h->alias, h->m, h->seed, 0, h->k_host + done, cnt, h->eta,
+                             h->pidx, s);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(h->Res3, 0, sizeof(float) * 3 * (size_t)h->R_p * h->eta_p64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->pbar, 0, sizeof(unsigned long long), s);
+    a.cnt = (int32_t)cnt;
+    if (e == cudaSuccess) e = rska::launch_mrhs_tmem(h->mapG, a, s);
+    done += cnt;
+  }
+  if (K > 0) h->x_stale = true;
+  return e;
+}
+
 int fail(rska_mrhs* h, cudaError_t e) {
   h->sticky = (e == cudaErrorMemoryAllocation) ? RSKA_ENOMEM : RSKA_ECUDA;
   return h->sticky;
@@ -902,6 +860,8 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
   h->eta_p = round_up(eta, rska::TM);
   h->R_p = round_up(R, rska::TN);
   h->idx_cap = 64;
+  h->eta_p64 = round_up(eta, 64);
+  h->pidx_cap = 512;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -924,7 +884,18 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
        (e = dalloc(&h->status, 1)) != cudaSuccess || (e = dalloc(&q, m)) != cudaSuccess ||
        (e = dalloc(&stk, m)) != cudaSuccess)) {
   }
+  const bool tmem_ok =
+      e == cudaSuccess && rska::mrhs_tmem_fits(h->n_p, h->R_p, h->eta_p64, h->num_sms);
+  const size_t gs = (size_t)2 * h->eta_p64 * h->n_p;
+  if (tmem_ok &&
+      ((e = dalloc(&h->G, gs)) != cudaSuccess ||
+       (e = dalloc(&h->Res3, (size_t)3 * h->R_p * h->eta_p64)) != cudaSuccess ||
+       (e = dalloc(&h->pbar, 1)) != cudaSuccess ||
+       (e = dalloc(&h->pidx, (size_t)h->pidx_cap * eta)) != cudaSuccess)) {
+  }
+  h->form = tmem_ok ? 2 : 1;
   cudaStream_t s = h->stream;
+  if (e == cudaSuccess && tmem_ok) e = cudaMemsetAsync(h->G, 0, gs * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
   for (int b = 0; b < 2; ++b) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->Atau[b], 0, as * 2, s);
@@ -972,7 +943,8 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
         make_map(&h->mapRes, h->Res, h->eta_p, h->R_p, h->R_p, rska::TM, true) &&
         make_map(&h->mapZ, h->Zt, h->R_p, h->n_p, h->n_p, rska::TM, true) &&
         make_map(&h->mapXs[0], h->Xhi, h->R_p, h->n_p, h->n_p, rska::TM) &&
-        make_map(&h->mapXs[1], h->Xlo, h->R_p, h->n_p, h->n_p, rska::TM)))
+        make_map(&h->mapXs[1], h->Xlo, h->R_p, h->n_p, h->n_p, rska::TM) &&
+        (!tmem_ok || make_map(&h->mapG, h->G, 2 * h->eta_p64, h->n_p, h->n_p, (uint32_t)h->eta_p64))))
     rc = RSKA_ECUDA;
   if (rc == RSKA_OK &&
       (cudaFuncSetAttribute(rska::mrhs_gemm_kernel<rska::kResidual>,
@@ -1014,6 +986,16 @@ int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
       if (value != 0 && value != 1) return RSKA_EINVAL;
       h->use_pdl = (int)value;
       return RSKA_OK;
+    case 5:
+      if (value < 0 || value > 2) return RSKA_EINVAL;
+      if (value == 2 && h->G == nullptr) return RSKA_EUNSUPPORTED;
+      h->form_opt = (int)value;
+      h->form = value == 1 ? 1 : (h->G != nullptr ? 2 : 1);
+      return RSKA_OK;
+    case 6:
+      if (value < 0 || value > 2) return RSKA_EINVAL;
+      h->nsplit_r = (int)value;
+      return RSKA_OK;
     default:
       return RSKA_EINVAL;
   }
@@ -1029,6 +1011,8 @@ int rska_mrhs_query(rska_mrhs* h, int what, int64_t* value) {
     case 3: *value = h->eta_p; return RSKA_OK;
     case 4: *value = h->R_p; return RSKA_OK;
     case 5: *value = h->nsplit; return RSKA_OK;
+    case 6: *value = h->form; return RSKA_OK;
+    case 7: *value = h->nsplit_r > 0 ? h->nsplit_r : h->nsplit; return RSKA_OK;
     default: return RSKA_EINVAL;
   }
 }
@@ -1036,44 +1020,7 @@ int rska_mrhs_query(rska_mrhs* h, int what, int64_t* value) {
 int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
   if (!h || K < 0) return RSKA_EINVAL;
   if (h->sticky) return h->sticky;
-  cudaStream_t s = h->stream;
-  cudaError_t e = cudaSuccess;
-  for (int64_t done = 0; done < K && e == cudaSuccess;) {
-    const int64_t cnt = std::min(h->idx_cap, K - done);
-    e = rska::launch_indices(h->thr, h->alias, h->m, h->seed, 0, h->k_host + done, cnt, h->eta,
-                             h->idx, s);
-    if (e != cudaSuccess) break;
-    if (cnt == h->idx_cap && h->use_graph) {
-      if (!h->graph || h->graph_nsplit != h->nsplit || h->graph_ksplit != h->ksplit ||
-          h->graph_pdl != h->use_pdl || h->graph_limit_ns != h->limit_ns) {
-        if (h->graph) {
-          cudaGraphExecDestroy(h->graph);
-          h->graph = nullptr;
-        }
-        cudaStream_t cap = nullptr;
-        cudaGraph_t g = nullptr;
-        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-          const cudaError_t e1 = enqueue_iterations(h, cnt, cap);
-          e = cudaStreamEndCapture(cap, &g);
-          if (e == cudaSuccess) e = e1;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
-        if (g) cudaGraphDestroy(g);
-        if (cap) cudaStreamDestroy(cap);
-        if (e != cudaSuccess) break;
-        h->graph_nsplit = h->nsplit;
-        h->graph_ksplit = h->ksplit;
-        h->graph_pdl = h->use_pdl;
-        h->graph_limit_ns = h->limit_ns;
-      }
-      e = cudaGraphLaunch(h->graph, s);
-    } else {
-      e = enqueue_iterations(h, cnt, s);
-    }
-    done += cnt;
-  }
+  const cudaError_t e = (h->form == 2) ? solve_tmem(h, K) : solve_staged(h, K);
   if (e != cudaSuccess) return fail(h, e);
   h->k_host += K;
   return RSKA_OK;
@@ -1129,6 +1076,7 @@ int rska_mrhs_reset(rska_mrhs* h) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
   if (e != cudaSuccess) return fail(h, e);
   h->k_host = 0;
+  h->x_stale = false;
   h->sticky = RSKA_OK;
   return RSKA_OK;
 }

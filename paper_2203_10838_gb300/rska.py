@@ -308,8 +308,11 @@ class BatchSolver:
         return nu, thr, alias
 
 
-MRHS_OPTION = {"terms": 0, "ksplit": 1, "watchdog_us": 2, "graph": 3, "pdl": 4}
-MRHS_QUERY = {"k": 0, "ksplit": 1, "n_pad": 2, "eta_pad": 3, "R_pad": 4, "terms": 5}
+MRHS_OPTION = {"terms": 0, "ksplit": 1, "watchdog_us": 2, "graph": 3, "pdl": 4, "form": 5,
+               "terms_update": 6}
+MRHS_QUERY = {"k": 0, "ksplit": 1, "n_pad": 2, "eta_pad": 3, "R_pad": 4, "terms": 5, "form": 6,
+              "terms_update": 7}
+MRHS_FORM = {"auto": 0, "staged": 1, "persistent": 2}
 
 
 class MultiRHS:

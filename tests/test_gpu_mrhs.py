@@ -42,12 +42,21 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def run_case(env, m, n, R, s, eta, lam, t, K, seed, check_rows, tol, terms=2, pseed=21):
+FORMS = ["staged", "persistent"]
+
+
+def run_case(env, m, n, R, s, eta, lam, t, K, seed, check_rows, tol, terms=2, pseed=21,
+             form="auto", terms_update=0):
     torch, orc, MultiRHS = env
+    from paper_2203_10838_gb300.rska import MRHS_FORM
     p = multi_rhs_problem(m, n, R, s, seed=pseed)
     A, B = to_dev(torch, p)
     with MultiRHS(A, B, lam, eta, t, seed, n=n) as h:
+        h.set_option("form", MRHS_FORM[form])
+        if form != "auto":
+            assert h.query("form") == MRHS_FORM[form]
         h.set_option("terms", terms)
+        h.set_option("terms_update", terms_update)
         nu_g, thr_g, al_g = [v.cpu().numpy() for v in h.get_tables()]
         tau_g = h.get_indices(0, K).cpu().numpy()
         h.solve(K)
@@ -72,38 +81,82 @@ def run_case(env, m, n, R, s, eta, lam, t, K, seed, check_rows, tol, terms=2, ps
     return worst, x
 
 
-def test_mrhs_small_ragged(env):
-    # n = 300 (padded to 512), eta = 100 (padded to 128), R = 40 (padded to 256)
+@pytest.mark.parametrize("K", [1, 2, 5])
+def test_mrhs_persistent_first_iterations(env, K):
+    """The first iterations of the persistent form one by one (lambda = 0, so
+    x = z and both products see nonzero operands from the second iteration
+    on): 128 right-hand sides on two column slices, eta = 64."""
+    run_case(env, 600, 512, 128, 8, eta=64, lam=0.0, t=2.0, K=K, seed=9,
+             check_rows=range(0, 128, 5), tol=1e-4, form="persistent")
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_mrhs_small_ragged(env, form):
+    # n = 300 (padded to 512), eta = 100 (padded to 128 / 128), R = 40 (padded to 256)
     run_case(env, 700, 300, 40, 10, eta=100, lam=0.3, t=1.0, K=30, seed=7,
-             check_rows=range(40), tol=1e-4)
+             check_rows=range(40), tol=1e-4, form=form)
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("m,n,R,eta", [(5, 3, 1, 1), (1, 7, 3, 3)])
-def test_mrhs_degenerate_shapes(env, m, n, R, eta):
+def test_mrhs_degenerate_shapes(env, m, n, R, eta, form):
     """One right-hand side with eta = 1 on a 5 x 3 system (every operand a
     sliver of its padded tile), and a single row drawn eta times per iteration
     for three right-hand sides."""
     run_case(env, m, n, R, 1, eta=eta, lam=0.001, t=1.0, K=40, seed=3,
-             check_rows=range(R), tol=1e-4)
+             check_rows=range(R), tol=1e-4, form=form)
 
 
-def test_mrhs_single_term_within_spec(env):
+@pytest.mark.parametrize("form", FORMS)
+def test_mrhs_single_term_within_spec(env, form):
     run_case(env, 700, 300, 40, 10, eta=100, lam=0.3, t=1.0, K=30, seed=7,
-             check_rows=range(40), tol=SPEC_TOL, terms=1)
+             check_rows=range(40), tol=SPEC_TOL, terms=1, form=form)
 
 
-def test_mrhs_several_tiles(env):
+def test_mrhs_single_term_update_within_spec(env):
+    """X as high + low parts, the scaled residual as one BF16 term."""
+    run_case(env, 700, 300, 40, 10, eta=100, lam=0.3, t=1.0, K=30, seed=7,
+             check_rows=range(40), tol=SPEC_TOL, terms=2, terms_update=1, form="persistent")
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_mrhs_several_tiles(env, form):
     # 9 column tiles of the update product, 2 right-hand-side tiles, eta = 2 x 128
     run_case(env, 3000, 2100, 300, 50, eta=256, lam=0.5, t=8.0, K=20, seed=5,
-             check_rows=[0, 1, 77, 128, 255, 256, 299], tol=1e-4)
+             check_rows=[0, 1, 77, 128, 255, 256, 299], tol=1e-4, form=form)
 
 
-def test_mrhs_full_size_configuration(env):
+@pytest.mark.parametrize("form", FORMS)
+def test_mrhs_full_size_configuration(env, form):
     """A 16384 x 8192 N(0, 1/n) in BF16, 512 right-hand sides with 400
     nonzeros each, lambda = 1, eta = 256, t = 128; 50 iterations, 16
     right-hand sides checked against the FP64 oracle."""
     run_case(env, 16384, 8192, 512, 400, eta=256, lam=1.0, t=128.0, K=50, seed=0,
-             check_rows=list(range(0, 512, 32)), tol=1e-4, pseed=1)
+             check_rows=list(range(0, 512, 32)), tol=1e-4, pseed=1, form=form)
+
+
+def test_mrhs_persistent_launch_boundaries_and_form_switches(env):
+    """One persistent launch runs at most 512 iterations: 600 iterations in
+    one call (two launches), in uneven calls, and alternating between the
+    staged and the persistent form (the staged form's X is rebuilt from Z
+    after persistent launches) all give the same iterate."""
+    torch, orc, MultiRHS = env
+    from paper_2203_10838_gb300.rska import MRHS_FORM
+    p = multi_rhs_problem(900, 500, 64, 12, seed=3)
+    A, B = to_dev(torch, p)
+    outs = []
+    plans = [[("persistent", 600)], [("persistent", 100), ("persistent", 500)],
+             [("staged", 130), ("persistent", 300), ("staged", 70), ("persistent", 100)],
+             [("staged", 600)]]
+    for plan in plans:
+        with MultiRHS(A, B, 0.3, 64, 2.0, 11, n=500) as h:
+            for form, k in plan:
+                h.set_option("form", MRHS_FORM[form])
+                h.solve(k)
+            assert h.query("k") == 600
+            outs.append(h.get_x()[1].cpu().numpy().astype(np.float64))
+    for o in outs[1:]:
+        assert rel(o, outs[0]) <= 1e-4
 
 
 def test_mrhs_resume_and_graph_agree(env):
@@ -111,8 +164,10 @@ def test_mrhs_resume_and_graph_agree(env):
     p = multi_rhs_problem(900, 500, 64, 12, seed=3)
     A, B = to_dev(torch, p)
     outs = []
+    from paper_2203_10838_gb300.rska import MRHS_FORM
     for graph, chunks in [(1, [70]), (0, [70]), (1, [30, 40])]:
         with MultiRHS(A, B, 0.3, 64, 2.0, 11, n=500) as h:
+            h.set_option("form", MRHS_FORM["staged"])
             h.set_option("graph", graph)
             for c in chunks:
                 h.solve(c)

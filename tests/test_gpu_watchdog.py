@@ -79,15 +79,17 @@ def test_single_system_wait_limit_runs_out_and_context_recovers(env, kernel):
     assert rel(x, orc.soft_shrink(zr, lam)) <= 1e-4
 
 
-def test_multi_rhs_wait_limit_runs_out_and_context_recovers(env):
+@pytest.mark.parametrize("form", ["staged", "persistent"])
+def test_multi_rhs_wait_limit_runs_out_and_context_recovers(env, form):
     torch, orc = env
     from paper_2203_10838_gb300._lib import RSKAError
-    from paper_2203_10838_gb300.rska import MultiRHS
+    from paper_2203_10838_gb300.rska import MRHS_FORM, MultiRHS
     m, n, R, s, eta, lam, t, seed, K = 1024, 512, 64, 10, 128, 0.3, 8.0, 4, 20
     p = multi_rhs_problem(m, n, R, s, seed=31)
     A = torch.from_numpy(p.A16.view(np.int16)).cuda().view(torch.bfloat16)
     B = torch.from_numpy(p.B).cuda()
     with MultiRHS(A, B, lam, eta, t, seed, n=n) as h:
+        h.set_option("form", MRHS_FORM[form])
         h.set_option("watchdog_us", 1)
         h.solve(70)
         with pytest.raises(RSKAError) as ei:
