@@ -85,7 +85,8 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = {"rska_rows_kernel": ["rska_rows.cu", "rska_device.cuh"],
+KERNEL_SOURCES = {"mrhs_tmem_kernel": ["rska_mrhs_tmem.cu", "rska_tc.cuh", "rska_device.cuh"],
+                  "rska_rows_kernel": ["rska_rows.cu", "rska_device.cuh"],
                   "rska_persistent_kernel": ["rska_solve.cu", "rska_device.cuh"],
                   "unrolled_bwd_rows_kernel": ["rska_unrolled.cu", "rska_device.cuh"]}
 
@@ -866,6 +867,10 @@ def run_mrhs(args):
     B = B_host.to(dev)
     stream = torch.cuda.current_stream(dev)
     h = MultiRHS(A, B, MR_LAM, MR_ETA, MR_T, MR_SEED, n=MR_N, stream=stream)
+    if args.mrhs_form != "auto":
+        from paper_2203_10838_gb300.rska import MRHS_FORM
+        h.set_option("form", MRHS_FORM[args.mrhs_form])
+    form = h.query("form")
 
     def step():
         h.reset()
@@ -914,6 +919,7 @@ def run_mrhs(args):
         rr = np.array([by_j[j][0] for j in range(MR_R)])
         re = np.array([by_j[j][1] for j in range(MR_R)])
     terms = h.query("terms")
+    terms_update = h.query("terms_update")
     ksplit = h.query("ksplit")
     # end to end through the public API: H2D of A and B, setup, K iterations, D2H of X
     torch.cuda.synchronize(dev)
@@ -921,6 +927,7 @@ def run_mrhs(args):
     A_e = A16_host.to(dev, non_blocking=True).view(torch.bfloat16)
     B_e = B_host.to(dev, non_blocking=True)
     with MultiRHS(A_e, B_e, MR_LAM, MR_ETA, MR_T, MR_SEED, n=MR_N, stream=stream) as he:
+        he.set_option("form", form)
         he.solve(MR_K)
         xe = he.get_x()[0].cpu()
     e2e_s = time.perf_counter() - c0
@@ -968,7 +975,9 @@ def run_mrhs(args):
             "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
             "config": {"workload": "rska_mrhs_16384x8192_R512", "m": MR_M, "n": MR_N, "R": MR_R,
                        "nnz": MR_S, "eta": MR_ETA, "t": MR_T, "lambda": MR_LAM,
-                       "iters_per_step": MR_K, "terms": terms, "ksplit": ksplit,
+                       "iters_per_step": MR_K, "terms": terms, "terms_update": terms_update,
+                       "form": {1: "staged", 2: "persistent"}[form],
+                       "ksplit": ksplit if form == 1 else None,
                        "l2": "A is 256 MB (> L2); rows of A are sampled at random",
                        "parallelism": "sharded" if args.shard else "replicas"},
             "partition": ({"rhs_per_rank": [b - a for a, b in rhs_shards(MR_R, world)],
@@ -976,11 +985,16 @@ def run_mrhs(args):
                                    "index stream", "slowest_rank_ms": ms}
                           if args.shard else None),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (committed_traffic("mrhs_tmem_kernel", MR_K)
+                                     if form == 2 else None),
                          "peak_kind": "measured cuBLAS bf16, sustained",
-                         "kernel": "whole iteration (gather, residual GEMM, scale, update GEMM)",
+                         "kernel": ("mrhs_tmem_kernel (one persistent launch per step; the "
+                                    "step's time includes the index draw before it)"
+                                    if form == 2 else
+                                    "whole iteration (gather, residual GEMM, scale, update GEMM)"),
                          "flops_per_iteration": 4.0 * MR_ETA * MR_N * MR_R,
-                         "executed_mma_flops_factor": terms},
+                         "executed_mma_flops_factor": (terms + terms_update) / 2.0},
             "accuracy": {"rel_residual_median": float(np.median(rr)),
                          "rel_residual_max": float(rr.max()),
                          "rel_error_median": float(np.median(re)),
@@ -994,7 +1008,10 @@ def run_mrhs(args):
                                   "impl": "single-system solver (FP32 copy of the BF16 A) looped "
                                           "over 4 right-hand sides, scaled to 512",
                                   "speedup_of_mrhs": loop_s / (ms / 1000.0)},
-            "gpu_launches": 4 * MR_K * args.steps + 2 * args.steps,
+            # per step: the index draw and one persistent kernel, or per
+            # iteration gather, two products and the scale kernel (+ the draw
+            # and the output kernel per step)
+            "gpu_launches": (2 * args.steps if form == 2 else 4 * MR_K * args.steps + 2 * args.steps),
             "prep": {"generate_s": gen_s},
             "cpu_baseline": cpu, "clocks": clk}
     return line if rank == 0 else None
@@ -1129,6 +1146,8 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="batched / mrhs: split one problem set (one set of right-hand sides) "
                          "across the ranks instead of running a replica per rank")
+    ap.add_argument("--mrhs-form", default="auto", choices=["auto", "staged", "persistent"],
+                    help="mrhs: the form of the iteration (default: the library's choice)")
     ap.add_argument("--no-forms", action="store_true",
                     help="single workload: leave out the batched, unrolled and multi-RHS keys")
     ap.add_argument("--iters", type=int, default=None,

@@ -25,9 +25,12 @@
 //  4. The epilogue reads the reduced products back, forms the scaled
 //     residual -(t/eta) (Res - b_tau) / ||a_tau||^2 for its right-hand sides,
 //     splits it into high and low parts and streams it through the ring;
-//     the MMA thread accumulates Z^T (M 128, N 256, K 16) += R'^T_chunk
-//     A_tau_chunk with A_tau read column-major (the same shared-memory tile
-//     serves as the K-major operand of step 2 and the MN-major operand here).
+//     the MMA thread forms D^T (M 128, N 256, K 16) = sum R'^T_chunk
+//     A_tau_chunk in the tensor-memory columns the residual product used,
+//     with A_tau read column-major (the same shared-memory tile serves as
+//     the K-major operand of step 2 and the MN-major operand here), and the
+//     epilogue adds D^T to Z^T in FP32 (one rounding per iteration, as when
+//     z -= d is applied outside the tensor core).
 //
 // Two helper warps gather the rows of tau_{k+1} into the other dense A_tau
 // buffer (and stage tau_{k+1} and 1/||a||^2 at tau_{k+1}) while iteration k
@@ -297,8 +300,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok) break;
         mma_commit(&bars.res_done);
-        // update: Z^T += R'^T A_tau (R' carries the minus sign), 64 rows of
-        // A_tau (the contraction index) at a time
+        // update: D^T = R'^T A_tau (R' carries the minus sign) into the
+        // columns the residual product has left (its readout precedes the
+        // grid barrier), 64 rows of A_tau (the contraction index) at a time;
+        // the epilogue adds D^T to Z^T in FP32
         for (int qq = 0; qq < rchunks && ok; ++qq) {
           const uint32_t slot = u & 1;
           ok = wait_phase(&bars.full[slot], (u >> 1) & 1, a.limit_ns, &s_abort);
@@ -309,9 +314,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t db =
                 desc_mn_sw128(abase + (uint32_t)(64 * qq + 16 * kk) * 128u, chunk_bytes);
-            mma_bf16(tmem, desc_sw128(rsl) + (uint64_t)(2 * kk), db, id_upd, 1u);
+            mma_bf16(tmem + kTmemRes, desc_sw128(rsl) + (uint64_t)(2 * kk), db, id_upd,
+                     (qq > 0 || kk > 0) ? 1u : 0u);
             if (a.nsplit_r == 2)
-              mma_bf16(tmem, desc_sw128(rsl + 16384) + (uint64_t)(2 * kk), db, id_upd, 1u);
+              mma_bf16(tmem + kTmemRes, desc_sw128(rsl + 16384) + (uint64_t)(2 * kk), db, id_upd,
+                       1u);
           }
           mma_commit(&bars.empty[slot]);
           ++u;
@@ -528,11 +535,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ++u;
       }
-      // ---- Z^T updated in tensor memory ----
+      // ---- Z^T += D^T (FP32, rounded once per iteration) ----
       if (!bad) {
         int w = 1;
         if (lane == 0) w = wait_phase(&bars.upd_done, (uint32_t)(i & 1), lim, &s_abort);
         bad |= !__shfl_sync(0xffffffffu, w, 0);
+      }
+      if (!bad) {
+        tc_fence_after();
+        // the columns this warp reads again for the next X (64 j + 32 half),
+        // so no other warp's tensor-memory writes are involved
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t col = (uint32_t)(64 * j + 32 * half);
+          float z[32], d[32];
+          tmem_ld32(tl + col, z);
+          tmem_ld32(tl + kTmemRes + col, d);
+#pragma unroll
+          for (int t = 0; t < 32; ++t) z[t] += d[t];
+          tmem_st32(tl + col, z);
+        }
+        tc_fence_before();
       }
       if (bad && !s_abort) fail();
     }
