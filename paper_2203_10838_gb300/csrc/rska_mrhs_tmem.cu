@@ -33,8 +33,8 @@
 //     z -= d is applied outside the tensor core).
 //
 // Two helper warps gather the rows of tau_{k+1} into the other dense A_tau
-// buffer (and stage tau_{k+1} and 1/||a||^2 at tau_{k+1}) while iteration k
-// computes, so the only per-iteration exchanges are the residual reduction
+// buffer with bulk copies (and stage tau_{k+1} and 1/||a||^2 at tau_{k+1})
+// while iteration k computes, so the only per-iteration exchanges are the residual reduction
 // and the grid barrier.  Every wait is bounded; on expiry the kernel records
 // a timeout, lets its issued copies and MMAs finish, and returns.
 #include <cuda.h>
@@ -56,6 +56,7 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kSliceR = 128;       // right-hand sides per CTA (tensor-memory lanes)
 constexpr int kSliceN = 256;       // columns of Z^T per CTA
 constexpr uint32_t kRingSlot = 32768;  // one ring slot: high part (16 KB) + low part (16 KB)
+constexpr uint32_t kStage = 16384;     // gather staging buffer: one row piece of 8192 BF16
 constexpr uint32_t kTmemCols = 512;    // Z^T in columns 0..255, the residual product from 256
 constexpr uint32_t kTmemRes = 256;
 
@@ -181,6 +182,7 @@ struct alignas(8) Bars {
   uint64_t passed;      // this CTA has passed grid barrier b (one phase per barrier)
   uint64_t gathered;    // both helper warps finished the next iteration's gather
   uint64_t fin;         // every MMA of this CTA complete (exit drain)
+  uint64_t stage;       // gather staging buffer filled (bulk copy)
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t chunk_bytes = (uint32_t)eta_p * 128u;  // one 64-column chunk of A_tau
   unsigned char* atile = smem;                            // 4 chunks
   unsigned char* ring = smem + 4 * (size_t)chunk_bytes;  // 2 slots of 32 KB
+  unsigned char* stagebuf = ring + 2 * (size_t)kRingSlot;  // 16 KB
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -220,6 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mb_init(&bars.passed, 1);
     mb_init(&bars.gathered, 2);
     mb_init(&bars.fin, 1);
+    mb_init(&bars.stage, 1);
     s_abort = 0;
     s_flag = 1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -334,45 +338,61 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp < 4) {
     // ------------------------------------------------ gather helpers ------
-    // tau_{i} and 1/||a||^2 at tau_i into s_tau / s_iv [i % 3]; the rows of
-    // A_tau(i) into the dense buffer i % 2 (columns < n; the rest stay zero)
-    const int ht = tid - 64;
-    const int64_t n8 = a.n >> 3;
+    // Warp 3 stages tau_i and 1/||a||^2 at tau_i into s_tau / s_iv [i % 3];
+    // lane 0 of warp 2 copies this CTA's rows of A_tau(i) (rows s = blockIdx
+    // mod grid) into the dense buffer i % 2 with bulk copies through a 16 KB
+    // staging buffer (global -> shared -> global), columns < n only; the
+    // rest of the buffer stays zero.
+    const int64_t n8 = a.n >> 3;  // whole 16-byte pieces of a row
+    uint32_t stage_uses = 0;
+    bool gok = true;
     auto stage = [&](int i) {
       const int32_t* tau = a.idx + (int64_t)i * a.eta;
-      for (int s = ht; s < eta_p; s += 64) {
-        int32_t r = 0;
-        float iv = 0.f;
-        if (s < a.eta) {
-          r = __ldg(tau + s);
-          iv = __ldg(a.inv_nu + r);
+      if (warp == 3) {
+        for (int s = lane; s < eta_p; s += 32) {
+          int32_t r = 0;
+          float iv = 0.f;
+          if (s < a.eta) {
+            r = __ldg(tau + s);
+            iv = __ldg(a.inv_nu + r);
+          }
+          s_tau[i % 3][s] = r;
+          s_iv[i % 3][s] = iv;
         }
-        s_tau[i % 3][s] = r;
-        s_iv[i % 3][s] = iv;
-      }
-      __nv_bfloat16* G = a.G + (int64_t)(i & 1) * eta_p * a.n_p;
-      for (int s = blockIdx.x; s < a.eta; s += nCTA) {
-        const int32_t r = __ldg(tau + s);
-        const uint4* src = reinterpret_cast<const uint4*>(a.A + (int64_t)r * a.lda);
-        uint4* dst = reinterpret_cast<uint4*>(G + (int64_t)s * a.n_p);
-        int64_t v = ht;
-        for (; v + 3 * 64 < n8; v += 4 * 64) {
-          const uint4 x0 = __ldg(src + v), x1 = __ldg(src + v + 64), x2 = __ldg(src + v + 128),
-                      x3 = __ldg(src + v + 192);
-          dst[v] = x0;
-          dst[v + 64] = x1;
-          dst[v + 128] = x2;
-          dst[v + 192] = x3;
+      } else {
+        __nv_bfloat16* G = a.G + (int64_t)(i & 1) * eta_p * a.n_p;
+        for (int s = blockIdx.x; s < a.eta; s += nCTA) {
+          const int32_t r = __ldg(tau + s);
+          const __nv_bfloat16* src = a.A + (int64_t)r * a.lda;
+          __nv_bfloat16* dst = G + (int64_t)s * a.n_p;
+          for (int64_t v0 = 0; v0 < n8; v0 += kStage / 16) {
+            const int64_t left = n8 - v0;
+            const uint32_t bytes = (uint32_t)((left < (int64_t)(kStage / 16) ? left : (int64_t)(kStage / 16)) * 16);
+            if (lane == 0 && gok) {
+              mb_expect_tx(&bars.stage, bytes);
+              bulk_load(stagebuf, src + 8 * v0, bytes, &bars.stage);
+              gok = wait_phase(&bars.stage, stage_uses & 1u, drain_limit(a.limit_ns), nullptr);
+              if (gok) {
+                bulk_store(dst + 8 * v0, stagebuf, bytes);
+                bulk_commit();
+                bulk_wait_read();  // the staging buffer may be refilled
+              }
+            }
+            ++stage_uses;
+          }
+          // the last n mod 8 columns, one element per lane
+          for (int64_t e = n8 * 8 + lane; e < a.n; e += 32) dst[e] = src[e];
         }
-        for (; v < n8; v += 64) dst[v] = __ldg(src + v);
-        for (int64_t e = n8 * 8 + ht; e < a.n; e += 64)
-          G[(int64_t)s * a.n_p + e] = a.A[(int64_t)r * a.lda + e];
+        if (lane == 0) bulk_wait_all();  // this CTA's rows written to global memory
       }
-      // generic-proxy writes of this thread become visible to the TMA reads
-      // that follow the grid barrier
+      // generic- and async-proxy writes of this thread become visible to the
+      // TMA reads that follow the grid barrier
       fence_proxy_async_global();
       __syncwarp();
-      if (lane == 0) mb_arrive(&bars.gathered);
+      if (lane == 0) {
+        if (!gok && !s_abort) fail();
+        mb_arrive(&bars.gathered);
+      }
     };
     stage(0);
     for (int i = 0; i + 1 < cnt; ++i) {
@@ -586,7 +606,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
-size_t mrhs_tmem_smem(int eta_p) { return 4u * (size_t)eta_p * 128u + 2u * kRingSlot + 1024u; }
+size_t mrhs_tmem_smem(int eta_p) {
+  return 4u * (size_t)eta_p * 128u + 2u * kRingSlot + kStage + 1024u;
+}
 
 bool mrhs_tmem_fits(int64_t n_p, int64_t R_p, int64_t eta_p, int num_sms) {
   return eta_p >= 64 && eta_p <= 256 && (eta_p % 64) == 0 && (n_p % kSliceN) == 0 &&
