@@ -20,10 +20,12 @@
 //     P^T (128 x eta_p, tensor-memory columns 256..) += X^T_chunk A_tau_chunk^T
 //     (M 128, N eta_p, K 16; both operands K-major).
 //  3. P^T is this CTA's share of the residual product; the epilogue adds it
-//     into a global accumulator of the right-hand-side slice with vector
-//     reductions, and every CTA passes one bounded grid barrier.
-//  4. The epilogue reads the reduced products back, forms the scaled
-//     residual -(t/eta) (Res - b_tau) / ||a_tau||^2 for its right-hand sides,
+//     with vector reductions into a global accumulator of the right-hand-side
+//     slice that starts at -b_tau (each CTA of the slice writes 1/32 of that
+//     start value one iteration ahead), and every CTA passes one bounded grid
+//     barrier.
+//  4. The epilogue reads the residuals back, forms the scaled residual
+//     -(t/eta) (A_tau x - b_tau) / ||a_tau||^2 for its right-hand sides,
 //     splits it into high and low parts and streams it through the ring;
 //     the MMA thread forms D^T (M 128, N 256, K 16) = sum R'^T_chunk
 //     A_tau_chunk in the tensor-memory columns the residual product used,
@@ -151,25 +153,24 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
 
 // 32 FP32 values of one row (row `row` of a 128-row, 64-column K-major BF16
 // operand, columns 32 half .. + 31) into the high part at `hi` and, when
-// `two`, the low part at `lo` (128-byte swizzle as TMA would write it).
+// `two`, the low part at `lo` (128-byte swizzle as TMA would write it); eight
+// values (one 16-byte piece of each part) at a time.
 __device__ __forceinline__ void store_split_row(unsigned char* hi, unsigned char* lo, int row,
                                                 int half, const float (&v)[32], bool two) {
-  uint32_t hw[16], lw[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    __nv_bfloat16 h0, l0, h1, l1;
-    split_bf16(v[2 * j], &h0, &l0);
-    split_bf16(v[2 * j + 1], &h1, &l1);
-    hw[j] = pack_bf16(h0, h1);
-    lw[j] = pack_bf16(l0, l1);
-  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat16 h0, l0, h1, l1;
+      split_bf16(v[8 * q + 2 * j], &h0, &l0);
+      split_bf16(v[8 * q + 2 * j + 1], &h1, &l1);
+      hw[j] = pack_bf16(h0, h1);
+      lw[j] = pack_bf16(l0, l1);
+    }
     const uint32_t off = sw128_off(row, 4 * half + q);
-    *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-    if (two)
-      *reinterpret_cast<uint4*>(lo + off) =
-          make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    if (two) *reinterpret_cast<uint4*>(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   }
 }
 
@@ -192,7 +193,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ int s_flag;
-  __shared__ int32_t s_tau[3][256];
   __shared__ float s_iv[3][256];
 
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp < 4) {
     // ------------------------------------------------ gather helpers ------
-    // Warp 3 stages tau_i and 1/||a||^2 at tau_i into s_tau / s_iv [i % 3];
+    // Warp 3 stages 1/||a||^2 at tau_i into s_iv [i % 3];
     // lane 0 of warp 2 copies this CTA's rows of A_tau(i) (rows s = blockIdx
     // mod grid) into the dense buffer i % 2 with bulk copies through a 16 KB
     // staging buffer (global -> shared -> global), columns < n only; the
@@ -356,7 +356,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             r = __ldg(tau + s);
             iv = __ldg(a.inv_nu + r);
           }
-          s_tau[i % 3][s] = r;
           s_iv[i % 3][s] = iv;
         }
       } else {
@@ -461,6 +460,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       return epi_sync_or(0) ? 0 : s_flag;
     };
+    // accumulator it % 3 of this right-hand-side slice starts at -b_tau of
+    // iteration it; the 32 column-slice CTAs of the slice each write 1/32 of
+    // it (slots beyond eta: zero).  Its previous use (iteration it - 3) was
+    // read before every CTA passed grid barrier it - 1.
+    auto init_acc = [&](int it) {
+      float4* acc = reinterpret_cast<float4*>(a.Res + ((int64_t)(it % 3) * a.R_p +
+                                                       (int64_t)rs * kSliceR) * eta_p);
+      const int32_t* tau = a.idx + (int64_t)it * a.eta;
+      const int64_t total4 = (int64_t)kSliceR * eta_p / 4;
+      const int64_t share = (total4 + a.n_slices - 1) / a.n_slices;
+      const int64_t end = min(total4, (int64_t)(cs + 1) * share);
+      for (int64_t x = (int64_t)cs * share + (tid - 128); x < end; x += kEpiThreads) {
+        const int64_t e4 = x * 4;
+        const int64_t rr = e4 / eta_p;
+        const int s = (int)(e4 - rr * eta_p);
+        const float* bcol = a.Bt + (int64_t)rs * kSliceR + rr;
+        float v4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          v4[j] = (s + j < a.eta) ? -__ldg(bcol + (int64_t)__ldg(tau + s + j) * a.R_p) : 0.f;
+        acc[x] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+      }
+    };
+    init_acc(0);
     int ok = grid_sync(0, 1);
     for (int i = 0; i < cnt && ok; ++i) {
       // ---- X = S_lambda(Z), split, into the ring: 4 chunks of 64 columns ----
@@ -505,55 +528,47 @@ __global__ void __launch_bounds__(kThreads, 1)
             red_add_v4(resb + col + 4 * t, v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
         }
         tc_fence_before();
-        // this CTA's share of the next accumulator of the slice, cleared
-        float4* nxt = reinterpret_cast<float4*>(a.Res + ((int64_t)((i + 1) % 3) * a.R_p +
-                                                         (int64_t)rs * kSliceR) * eta_p);
-        const int64_t total4 = (int64_t)kSliceR * eta_p / 4;
-        const int64_t share = (total4 + a.n_slices - 1) / a.n_slices;
-        for (int64_t x = (int64_t)cs * share + (tid - 128); x < min(total4, (int64_t)(cs + 1) * share);
-             x += kEpiThreads)
-          nxt[x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // this CTA's share of the next iteration's accumulator of the slice
+        if (i + 1 < cnt) init_acc(i + 1);
       }
+      // slots s of tau beyond eta carry 1/||a||^2 = 0 (their residual is zero)
+      const float* siv = s_iv[i % 3];
       ok = grid_sync(i + 1, (i + 1 < cnt) ? 1 : 0);
       if (!ok) break;
-      // ---- scaled residual R' = -(t/eta)(Res - b_tau)/||a_tau||^2, split ----
+      // ---- scaled residual R' = -(t/eta)(A_tau x - b_tau)/||a_tau||^2, split
+      // (the accumulator started at -b_tau) ----
       for (int qq = 0; qq < rchunks; ++qq) {
-        const uint32_t slot = u & 1;
-        if (!bad && u >= 2) {
-          int w = 1;
-          if (lane == 0) w = wait_phase(&bars.empty[slot], ((u >> 1) - 1) & 1, lim, &s_abort);
-          bad |= !__shfl_sync(0xffffffffu, w, 0);
-        }
-        if (!bad) {
+        {
+          const uint32_t slot = u & 1;
           const int s0 = 64 * qq + 32 * half;
           float v[32];
-          const float4* rp = reinterpret_cast<const float4*>(resb + s0);
+          if (!bad) {
+            const float4* rp = reinterpret_cast<const float4*>(resb + s0);
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const float4 r4 = __ldcg(rp + t);
-            v[4 * t] = r4.x;
-            v[4 * t + 1] = r4.y;
-            v[4 * t + 2] = r4.z;
-            v[4 * t + 3] = r4.w;
-          }
-#pragma unroll
-          for (int t = 0; t < 32; ++t) {
-            const int s = s0 + t;
-            float r = 0.f;
-            if (s < a.eta) {
-              const int32_t tr = s_tau[i % 3][s];
-              const float bv = __ldg(a.Bt + (int64_t)tr * a.R_p + rhs);
-              r = -a.coef * ((v[t] - bv) * s_iv[i % 3][s]);
+            for (int t = 0; t < 8; ++t) {
+              const float4 r4 = __ldcg(rp + t);
+              v[4 * t] = r4.x;
+              v[4 * t + 1] = r4.y;
+              v[4 * t + 2] = r4.z;
+              v[4 * t + 3] = r4.w;
             }
-            v[t] = r;
           }
-          unsigned char* rsl = ring + (size_t)slot * kRingSlot;
-          store_split_row(rsl, rsl + 16384, row, half, v, a.nsplit_r == 2);
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mb_arrive(&bars.full[slot]);
+          if (!bad && u >= 2) {
+            int w = 1;
+            if (lane == 0) w = wait_phase(&bars.empty[slot], ((u >> 1) - 1) & 1, lim, &s_abort);
+            bad |= !__shfl_sync(0xffffffffu, w, 0);
+          }
+          if (!bad) {
+#pragma unroll
+            for (int t = 0; t < 32; ++t) v[t] = -a.coef * (v[t] * siv[s0 + t]);
+            unsigned char* rsl = ring + (size_t)slot * kRingSlot;
+            store_split_row(rsl, rsl + 16384, row, half, v, a.nsplit_r == 2);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mb_arrive(&bars.full[slot]);
+          }
+          ++u;
         }
-        ++u;
       }
       // ---- Z^T += D^T (FP32, rounded once per iteration) ----
       if (!bad) {
