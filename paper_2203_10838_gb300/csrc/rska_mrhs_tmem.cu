@@ -113,6 +113,57 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Distributed shared memory: the address of the same shared-memory location
+// in CTA `rank` of the cluster, a 16-byte load from it, and an arrival on an
+// mbarrier there (release at cluster scope).
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ float4 ld_dsmem_v4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void mb_arrive_cluster(uint32_t remote_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar)
+               : "memory");
+}
+
+// Bounded wait on a local mbarrier whose arrivals come from other CTAs of the
+// cluster (acquire at cluster scope).
+__device__ __forceinline__ bool wait_phase_cluster(uint64_t* b, uint32_t parity, uint64_t limit_ns,
+                                                   const volatile int* abort) {
+  auto try_once = [&]() -> bool {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+  };
+  if (try_once()) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (!try_once()) {
+    if (global_timer_ns() - t0 > limit_ns) return false;
+    if (abort != nullptr && *abort) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
 // Barrier over the eight epilogue warps (named barrier 1) that also ORs a
 // flag across them.
 __device__ __forceinline__ int epi_sync_or(int pred) {
@@ -147,8 +198,16 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) 
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+// Two FP32 values as BF16 high parts (one packed conversion, round to nearest
+// even) and the low parts of what remains: v = hi + lo + O(2^-17 |v|).
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t* hi, uint32_t* lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+  const uint32_t hb = *reinterpret_cast<const uint32_t*>(&h);
+  const float h0 = __uint_as_float(hb << 16);           // the BF16 value of v0, exactly
+  const float h1 = __uint_as_float(hb & 0xFFFF0000u);  // the BF16 value of v1
+  const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - h0, v1 - h1);
+  *hi = hb;
+  *lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // 32 FP32 values of one row (row `row` of a 128-row, 64-column K-major BF16
@@ -161,13 +220,7 @@ __device__ __forceinline__ void store_split_row(unsigned char* hi, unsigned char
   for (int q = 0; q < 4; ++q) {
     uint32_t hw[4], lw[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      __nv_bfloat16 h0, l0, h1, l1;
-      split_bf16(v[8 * q + 2 * j], &h0, &l0);
-      split_bf16(v[8 * q + 2 * j + 1], &h1, &l1);
-      hw[j] = pack_bf16(h0, h1);
-      lw[j] = pack_bf16(l0, l1);
-    }
+    for (int j = 0; j < 4; ++j) split2(v[8 * q + 2 * j], v[8 * q + 2 * j + 1], &hw[j], &lw[j]);
     const uint32_t off = sw128_off(row, 4 * half + q);
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     if (two) *reinterpret_cast<uint4*>(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -184,6 +237,8 @@ struct alignas(8) Bars {
   uint64_t gathered;    // both helper warps finished the next iteration's gather
   uint64_t fin;         // every MMA of this CTA complete (exit drain)
   uint64_t stage;       // gather staging buffer filled (bulk copy)
+  uint64_t rb_full;     // every CTA of the cluster has staged its partial products
+  uint64_t rb_empty;    // every CTA of the cluster has finished reading this CTA's stage
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -207,8 +262,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = tid >> 5;
   const int lane = tid & 31;
   const int nCTA = gridDim.x;
-  const int rs = blockIdx.x % a.r_slices;
-  const int cs = blockIdx.x / a.r_slices;
+  // consecutive CTAs take consecutive column slices of one right-hand-side
+  // slice, so a cluster (consecutive CTAs) shares the slice's accumulator
+  const int rs = blockIdx.x / a.n_slices;
+  const int cs = blockIdx.x % a.n_slices;
+  const int crank = blockIdx.x % a.cluster;
   const int rchunks = eta_p / 64;                        // scaled-residual chunks
   const int cnt = a.cnt;
 
@@ -224,6 +282,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     mb_init(&bars.gathered, 2);
     mb_init(&bars.fin, 1);
     mb_init(&bars.stage, 1);
+    mb_init(&bars.rb_full, (uint32_t)a.cluster);
+    mb_init(&bars.rb_empty, (uint32_t)a.cluster);
     s_abort = 0;
     s_flag = 1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -237,6 +297,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // every CTA of the cluster has initialised its mbarriers before any remote
+  // arrival on them
+  if (a.cluster > 1) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   auto fail = [&]() {
@@ -429,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     uint32_t u = 0;  // ring uses
+    uint32_t rb_rounds = 0;  // cluster pre-reduction rounds
     const uint64_t lim = a.limit_ns;
     // grid barrier b: every CTA's reductions, clears and gathers before it
     // are visible to every CTA after it
@@ -516,21 +580,96 @@ __global__ void __launch_bounds__(kThreads, 1)
         bad |= !__shfl_sync(0xffffffffu, w, 0);
       }
       float* resb = a.Res + ((int64_t)(i % 3) * a.R_p + rhs) * eta_p;
-      if (!bad) {
-        tc_fence_after();
-        for (int j = 0; j < 4; ++j) {
-          const int col = 128 * half + 32 * j;
-          if (col >= eta_p) break;
-          float v[32];
-          tmem_ld32(tl + kTmemRes + (uint32_t)col, v);
+      if (a.cluster == 1) {
+        if (!bad) {
+          tc_fence_after();
+          for (int j = 0; j < 4; ++j) {
+            const int col = 128 * half + 32 * j;
+            if (col >= eta_p) break;
+            float v[32];
+            tmem_ld32(tl + kTmemRes + (uint32_t)col, v);
 #pragma unroll
-          for (int t = 0; t < 8; ++t)
-            red_add_v4(resb + col + 4 * t, v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+            for (int t = 0; t < 8; ++t)
+              red_add_v4(resb + col + 4 * t, v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+          }
+          tc_fence_before();
         }
-        tc_fence_before();
-        // this CTA's share of the next iteration's accumulator of the slice
-        if (i + 1 < cnt) init_acc(i + 1);
+      } else {
+        // pre-reduction inside the cluster, 128 columns of P^T at a time: each
+        // CTA stages its partial products (128 rows x 128 FP32, 16-byte
+        // granules XOR-swizzled by row) in the free ring, then CTA `crank`
+        // sums rows [crank, crank + 1) x 128 / cluster over the cluster's
+        // stages and adds them to the global accumulator
+        const uint32_t rb = saddr(ring);
+        const int rows_per = kSliceR / a.cluster;
+        for (int h2 = 0; 128 * h2 < eta_p; ++h2) {
+          const int cols = min(128, eta_p - 128 * h2);
+          if (!bad && rb_rounds > 0) {
+            int w = 1;
+            if (lane == 0)
+              w = wait_phase_cluster(&bars.rb_empty, (uint32_t)((rb_rounds - 1) & 1), lim, &s_abort);
+            bad |= !__shfl_sync(0xffffffffu, w, 0);
+          }
+          if (!bad) {
+            tc_fence_after();
+            for (int j = 0; j < 2; ++j) {
+              const int cl = 64 * half + 32 * j;  // column within the round
+              if (cl >= cols) break;
+              float v[32];
+              tmem_ld32(tl + kTmemRes + (uint32_t)(128 * h2 + cl), v);
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                const int g = (cl >> 2) + t;
+                *reinterpret_cast<float4*>(ring + row * 512 + ((g ^ (row & 31)) << 4)) =
+                    make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+              }
+            }
+            tc_fence_before();
+          }
+          if (epi_sync_or(bad)) {
+            bad = 1;
+            break;
+          }
+          if (tid == 128) {
+            for (int p = 0; p < a.cluster; ++p) mb_arrive_cluster(mapa(saddr(&bars.rb_full), (uint32_t)p));
+          }
+          {
+            int w = 1;
+            if (lane == 0) w = wait_phase_cluster(&bars.rb_full, (uint32_t)(rb_rounds & 1), lim, &s_abort);
+            bad |= !__shfl_sync(0xffffffffu, w, 0);
+            __syncwarp();  // lane 0's acquire orders the other lanes' reads of the stages
+          }
+          if (!bad) {
+            const int gpr = cols >> 2;  // granules per row in this round
+            for (int x = tid - 128; x < rows_per * gpr; x += kEpiThreads) {
+              const int rr = crank * rows_per + x / gpr;
+              const int g = x % gpr;
+              const uint32_t off = (uint32_t)(rr * 512 + ((g ^ (rr & 31)) << 4));
+              float4 acc = ld_dsmem_v4(mapa(rb + off, 0u));
+              for (int p = 1; p < a.cluster; ++p) {
+                const float4 q4 = ld_dsmem_v4(mapa(rb + off, (uint32_t)p));
+                acc.x += q4.x;
+                acc.y += q4.y;
+                acc.z += q4.z;
+                acc.w += q4.w;
+              }
+              red_add_v4(a.Res + ((int64_t)(i % 3) * a.R_p + (int64_t)rs * kSliceR + rr) * eta_p +
+                             128 * h2 + 4 * g,
+                         acc.x, acc.y, acc.z, acc.w);
+            }
+          }
+          if (epi_sync_or(bad)) {
+            bad = 1;
+            break;
+          }
+          if (tid == 128) {
+            for (int p = 0; p < a.cluster; ++p) mb_arrive_cluster(mapa(saddr(&bars.rb_empty), (uint32_t)p));
+          }
+          ++rb_rounds;
+        }
       }
+      // this CTA's share of the next iteration's accumulator of the slice
+      if (!bad && i + 1 < cnt) init_acc(i + 1);
       // slots s of tau beyond eta carry 1/||a||^2 = 0 (their residual is zero)
       const float* siv = s_iv[i % 3];
       ok = grid_sync(i + 1, (i + 1 < cnt) ? 1 : 0);
@@ -611,6 +750,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
   }
   __syncthreads();
+  // no CTA leaves while another CTA of its cluster may still read its stage
+  if (a.cluster > 1) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -641,11 +782,49 @@ cudaError_t launch_mrhs_tmem(const CUtensorMap& mapG, const MrhsTmemArgs& a, cud
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barrier needs it
-  attr[0].val.cooperative = 1;
+  if (a.cluster > 1) {
+    // clusters of consecutive CTAs; mrhs_tmem_cluster has checked that every
+    // cluster of the grid can be resident at once, as the grid barrier needs
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+  } else {
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barrier needs it
+    attr[0].val.cooperative = 1;
+  }
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, mrhs_tmem_kernel, mapG, a);
+}
+
+int mrhs_tmem_cluster(int n_slices, int r_slices, int eta_p) {
+  const size_t smem = mrhs_tmem_smem(eta_p);
+  if (cudaFuncSetAttribute(mrhs_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return 1;
+  const int grid = n_slices * r_slices;
+  for (int c = 4; c >= 2; c /= 2) {
+    if (n_slices % c != 0) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, mrhs_tmem_kernel, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if ((int64_t)nc * c >= grid) return c;
+  }
+  return 1;
 }
 
 }  // namespace rska
