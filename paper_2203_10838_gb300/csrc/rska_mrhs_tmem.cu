@@ -99,10 +99,8 @@ __device__ __forceinline__ bool wait_phase(uint64_t* b, uint32_t parity, uint64_
   return true;
 }
 
-__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
-               "f"(d)
-               : "memory");
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
 __device__ __forceinline__ void red_release_u64(unsigned long long* p, unsigned long long v) {
@@ -524,27 +522,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       return epi_sync_or(0) ? 0 : s_flag;
     };
-    // accumulator it % 3 of this right-hand-side slice starts at -b_tau of
-    // iteration it; the 32 column-slice CTAs of the slice each write 1/32 of
-    // it (slots beyond eta: zero).  Its previous use (iteration it - 3) was
-    // read before every CTA passed grid barrier it - 1.
+    // accumulator it % 3 of this right-hand-side slice (rows s of tau,
+    // columns = the slice's 128 right-hand sides) starts at -b_tau of
+    // iteration it; the column-slice CTAs of the slice each write a block of
+    // its rows (rows beyond eta: zero).  Its previous use (iteration it - 3)
+    // was read before every CTA passed grid barrier it - 1.
     auto init_acc = [&](int it) {
-      float4* acc = reinterpret_cast<float4*>(a.Res + ((int64_t)(it % 3) * a.R_p +
-                                                       (int64_t)rs * kSliceR) * eta_p);
       const int32_t* tau = a.idx + (int64_t)it * a.eta;
-      const int64_t total4 = (int64_t)kSliceR * eta_p / 4;
-      const int64_t share = (total4 + a.n_slices - 1) / a.n_slices;
-      const int64_t end = min(total4, (int64_t)(cs + 1) * share);
-      for (int64_t x = (int64_t)cs * share + (tid - 128); x < end; x += kEpiThreads) {
-        const int64_t e4 = x * 4;
-        const int64_t rr = e4 / eta_p;
-        const int s = (int)(e4 - rr * eta_p);
-        const float* bcol = a.Bt + (int64_t)rs * kSliceR + rr;
-        float v4[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          v4[j] = (s + j < a.eta) ? -__ldg(bcol + (int64_t)__ldg(tau + s + j) * a.R_p) : 0.f;
-        acc[x] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+      const int rows = (eta_p + a.n_slices - 1) / a.n_slices;
+      const int s_lo = cs * rows, s_hi = min(eta_p, s_lo + rows);
+      for (int x = tid - 128; x < (s_hi - s_lo) * (kSliceR / 4); x += kEpiThreads) {
+        const int s = s_lo + x / (kSliceR / 4);
+        const int g = x % (kSliceR / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (s < a.eta) {
+          const float4 bv = __ldg(reinterpret_cast<const float4*>(
+              a.Bt + (int64_t)__ldg(tau + s) * a.R_p + (int64_t)rs * kSliceR + 4 * g));
+          v = make_float4(-bv.x, -bv.y, -bv.z, -bv.w);
+        }
+        *reinterpret_cast<float4*>(a.Res + (((int64_t)(it % 3) * a.r_slices + rs) * eta_p + s) *
+                                               kSliceR + 4 * g) = v;
       }
     };
     init_acc(0);
@@ -579,7 +576,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) w = wait_phase(&bars.res_done, (uint32_t)(i & 1), lim, &s_abort);
         bad |= !__shfl_sync(0xffffffffu, w, 0);
       }
-      float* resb = a.Res + ((int64_t)(i % 3) * a.R_p + rhs) * eta_p;
+      // residual accumulator of this iteration and slice: rows s of 128
+      // right-hand sides, so a warp's 32 right-hand sides are one 128-byte line
+      float* resb = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR + row;
       if (a.cluster == 1) {
         if (!bad) {
           tc_fence_after();
@@ -589,8 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             float v[32];
             tmem_ld32(tl + kTmemRes + (uint32_t)col, v);
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
-              red_add_v4(resb + col + 4 * t, v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+            for (int t = 0; t < 32; ++t) red_add(resb + (col + t) * kSliceR, v[t]);
           }
           tc_fence_before();
         }
@@ -653,9 +651,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 acc.z += q4.z;
                 acc.w += q4.w;
               }
-              red_add_v4(a.Res + ((int64_t)(i % 3) * a.R_p + (int64_t)rs * kSliceR + rr) * eta_p +
-                             128 * h2 + 4 * g,
-                         acc.x, acc.y, acc.z, acc.w);
+              float* dst = a.Res + (((int64_t)(i % 3) * a.r_slices + rs) * eta_p + 128 * h2 + 4 * g) *
+                                       kSliceR + rr;
+              red_add(dst, acc.x);
+              red_add(dst + kSliceR, acc.y);
+              red_add(dst + 2 * kSliceR, acc.z);
+              red_add(dst + 3 * kSliceR, acc.w);
             }
           }
           if (epi_sync_or(bad)) {
@@ -682,15 +683,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int s0 = 64 * qq + 32 * half;
           float v[32];
           if (!bad) {
-            const float4* rp = reinterpret_cast<const float4*>(resb + s0);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              const float4 r4 = __ldcg(rp + t);
-              v[4 * t] = r4.x;
-              v[4 * t + 1] = r4.y;
-              v[4 * t + 2] = r4.z;
-              v[4 * t + 3] = r4.w;
-            }
+            for (int t = 0; t < 32; ++t) v[t] = __ldcg(resb + (s0 + t) * kSliceR);
           }
           if (!bad && u >= 2) {
             int w = 1;

@@ -29,7 +29,8 @@ struct MrhsTmemArgs {
   const float* Bt;         // m x R_p: Bt[i][j] = (b_j)_i
   __nv_bfloat16* G;        // 2 x eta_p x n_p: dense copies of A_tau (padding zero)
   float* Zt;               // R_p x n_p: Z^T, read at the start, written at the end
-  float* Res;              // 3 x R_p x eta_p residual-product accumulators (zero at launch)
+  float* Res;              // 3 x r_slices x eta_p x 128 residual accumulators (per iteration
+                           // buffer and right-hand-side slice: row s, one column per right-hand side)
   unsigned long long* bar; // grid barrier counter (zero at launch)
   float lambda;
   float coef;              // t / eta
