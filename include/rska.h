@@ -429,8 +429,8 @@ int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_
  * columns; needs eta <= 256 and (n_p / 256) (R_p / 128) CTAs resident at
  * once, else EUNSUPPORTED).  what = 6: terms of the scaled residual in the
  * second product (1 or 2; 0 = the same as option 0).  what = 7: CTAs per
- * cluster of the persistent form (0 automatic: the largest of 4, 2, 1 that
- * divides n_p / 256 and whose clusters can all be resident; 1, 2, 4): the
+ * cluster of the persistent form (0 automatic; 1, 2 or 4, dividing n_p / 256
+ * with every cluster of the grid resident at once, else EUNSUPPORTED): the
  * partial residual products of a cluster are summed in distributed shared
  * memory before the global reduction.
  * EINVAL for an unknown `what` or value.

@@ -537,7 +537,8 @@ struct rska_mrhs {
   int32_t* pidx = nullptr;           // tau of one persistent launch
   int64_t pidx_cap = 0;
   int cluster_opt = 0;               // CTAs per cluster of the persistent form (0 automatic)
-  int cluster_auto = 1;              // the largest size whose clusters are all resident
+  int cluster_auto = 1;              // automatic choice (the tuner's, else 1)
+  int cluster_max = 1;               // the largest size whose clusters are all resident
   CUtensorMap mapG;
 };
 
@@ -898,8 +899,8 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
   }
   h->form = tmem_ok ? 2 : 1;
   if (tmem_ok)
-    h->cluster_auto = rska::mrhs_tmem_cluster((int)(h->n_p / 256), (int)(h->R_p / 128),
-                                              (int)h->eta_p64);
+    h->cluster_max = rska::mrhs_tmem_cluster((int)(h->n_p / 256), (int)(h->R_p / 128),
+                                             (int)h->eta_p64);
   cudaStream_t s = h->stream;
   if (e == cudaSuccess && tmem_ok) e = cudaMemsetAsync(h->G, 0, gs * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
@@ -1004,7 +1005,7 @@ int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
       return RSKA_OK;
     case 7:
       if (value != 0 && value != 1 && value != 2 && value != 4) return RSKA_EINVAL;
-      if (value > 1 && (h->G == nullptr || (h->n_p / 256) % value != 0 || value > h->cluster_auto))
+      if (value > 1 && (h->G == nullptr || (h->n_p / 256) % value != 0 || value > h->cluster_max))
         return RSKA_EUNSUPPORTED;
       h->cluster_opt = (int)value;
       return RSKA_OK;
