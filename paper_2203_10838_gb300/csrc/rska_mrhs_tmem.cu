@@ -19,9 +19,10 @@
 //     two-slot ring in shared memory; one thread issues the tcgen05 MMAs
 //     P^T (128 x eta_p, tensor-memory columns 256..) += X^T_chunk A_tau_chunk^T
 //     (M 128, N eta_p, K 16; both operands K-major).
-//  3. P^T is this CTA's share of the residual product; the epilogue adds it
-//     with vector reductions into a global accumulator of the right-hand-side
-//     slice that starts at -b_tau (each CTA of the slice writes 1/32 of that
+//  3. P^T is this CTA's share of the residual product; the epilogue stages
+//     it in shared memory and adds it with bulk reductions into a global
+//     accumulator of the right-hand-side slice that starts at -b_tau (the
+//     helper warps of each CTA of the slice write a block of rows of that
 //     start value one iteration ahead), and every CTA passes one bounded grid
 //     barrier.
 //  4. The epilogue reads the residuals back, forms the scaled residual
@@ -419,6 +420,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           s_iv[i % 3][s] = iv;
         }
+        // this CTA's block of rows of the residual accumulator i % 3 of its
+        // right-hand-side slice starts at -b_tau(i) (rows beyond eta: zero);
+        // its previous use (iteration i - 3) was read before every CTA passed
+        // grid barrier i - 1, and grid barrier i precedes this stage
+        const int rows = (eta_p + a.n_slices - 1) / a.n_slices;
+        const int s_lo = cs * rows, s_hi = min(eta_p, s_lo + rows);
+        float* acc = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR;
+        for (int x = lane; x < (s_hi - s_lo) * (kSliceR / 4); x += 32) {
+          const int s = s_lo + x / (kSliceR / 4);
+          const int g = x % (kSliceR / 4);
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (s < a.eta) {
+            const float4 bv = __ldg(reinterpret_cast<const float4*>(
+                a.Bt + (int64_t)__ldg(tau + s) * a.R_p + (int64_t)rs * kSliceR + 4 * g));
+            v = make_float4(-bv.x, -bv.y, -bv.z, -bv.w);
+          }
+          *reinterpret_cast<float4*>(acc + (int64_t)s * kSliceR + 4 * g) = v;
+        }
       } else {
         __nv_bfloat16* G = a.G + (int64_t)(i & 1) * eta_p * a.n_p;
         for (int s = blockIdx.x; s < a.eta; s += nCTA) {
@@ -522,29 +541,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       return epi_sync_or(0) ? 0 : s_flag;
     };
-    // accumulator it % 3 of this right-hand-side slice (rows s of tau,
-    // columns = the slice's 128 right-hand sides) starts at -b_tau of
-    // iteration it; the column-slice CTAs of the slice each write a block of
-    // its rows (rows beyond eta: zero).  Its previous use (iteration it - 3)
-    // was read before every CTA passed grid barrier it - 1.
-    auto init_acc = [&](int it) {
-      const int32_t* tau = a.idx + (int64_t)it * a.eta;
-      const int rows = (eta_p + a.n_slices - 1) / a.n_slices;
-      const int s_lo = cs * rows, s_hi = min(eta_p, s_lo + rows);
-      for (int x = tid - 128; x < (s_hi - s_lo) * (kSliceR / 4); x += kEpiThreads) {
-        const int s = s_lo + x / (kSliceR / 4);
-        const int g = x % (kSliceR / 4);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (s < a.eta) {
-          const float4 bv = __ldg(reinterpret_cast<const float4*>(
-              a.Bt + (int64_t)__ldg(tau + s) * a.R_p + (int64_t)rs * kSliceR + 4 * g));
-          v = make_float4(-bv.x, -bv.y, -bv.z, -bv.w);
-        }
-        *reinterpret_cast<float4*>(a.Res + (((int64_t)(it % 3) * a.r_slices + rs) * eta_p + s) *
-                                               kSliceR + 4 * g) = v;
-      }
-    };
-    init_acc(0);
     int ok = grid_sync(0, 1);
     for (int i = 0; i < cnt && ok; ++i) {
       // ---- X = S_lambda(Z), split, into the ring: 4 chunks of 64 columns ----
@@ -580,17 +576,43 @@ __global__ void __launch_bounds__(kThreads, 1)
       // right-hand sides, so a warp's 32 right-hand sides are one 128-byte line
       float* resb = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR + row;
       if (a.cluster == 1) {
-        if (!bad) {
+        // P^T staged in the free ring as rows s of 128 right-hand sides (the
+        // accumulator's layout), 128 rows of s at a time, and added to the
+        // accumulator by one bulk reduction per round
+        float* accs = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR;
+        float* stg = reinterpret_cast<float*>(ring);
+        for (int h2 = 0; 128 * h2 < eta_p; ++h2) {
+          const int cols = min(128, eta_p - 128 * h2);
+          if (h2 > 0 && tid == 128) bulk_wait_read();  // the previous round has read the stage
+          if (epi_sync_or(bad)) {
+            bad = 1;
+            break;
+          }
           tc_fence_after();
-          for (int j = 0; j < 4; ++j) {
-            const int col = 128 * half + 32 * j;
-            if (col >= eta_p) break;
+          for (int j = 0; j < 2; ++j) {
+            const int cl = 64 * half + 32 * j;
+            if (cl >= cols) break;
             float v[32];
-            tmem_ld32(tl + kTmemRes + (uint32_t)col, v);
+            tmem_ld32(tl + kTmemRes + (uint32_t)(128 * h2 + cl), v);
 #pragma unroll
-            for (int t = 0; t < 32; ++t) red_add(resb + (col + t) * kSliceR, v[t]);
+            for (int t = 0; t < 32; ++t) stg[(cl + t) * kSliceR + row] = v[t];
           }
           tc_fence_before();
+          fence_proxy_async_smem();
+          if (epi_sync_or(bad)) {
+            bad = 1;
+            break;
+          }
+          if (tid == 128) {
+            bulk_reduce_add_f32(accs + (int64_t)128 * h2 * kSliceR, stg,
+                                (uint32_t)cols * kSliceR * 4u);
+            bulk_commit();
+          }
+        }
+        // the reductions are complete before this CTA arrives at the grid barrier
+        if (tid == 128) {
+          bulk_wait_all();
+          fence_proxy_async_global();
         }
       } else {
         // pre-reduction inside the cluster, 128 columns of P^T at a time: each
@@ -669,29 +691,35 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++rb_rounds;
         }
       }
-      // this CTA's share of the next iteration's accumulator of the slice
-      if (!bad && i + 1 < cnt) init_acc(i + 1);
+
       // slots s of tau beyond eta carry 1/||a||^2 = 0 (their residual is zero)
       const float* siv = s_iv[i % 3];
       ok = grid_sync(i + 1, (i + 1 < cnt) ? 1 : 0);
       if (!ok) break;
       // ---- scaled residual R' = -(t/eta)(A_tau x - b_tau)/||a_tau||^2, split
-      // (the accumulator started at -b_tau) ----
-      for (int qq = 0; qq < rchunks; ++qq) {
-        {
+      // (the accumulator started at -b_tau); the loads of chunk qq + 1 are in
+      // flight while chunk qq is formed ----
+      {
+        float vq[2][32];
+        auto load_res = [&](int qq, float (&v)[32]) {
+          const int s0 = 64 * qq + 32 * half;
+#pragma unroll
+          for (int t = 0; t < 32; ++t) v[t] = __ldcg(resb + (s0 + t) * kSliceR);
+        };
+        if (!bad) load_res(0, vq[0]);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          if (qq >= rchunks) break;
           const uint32_t slot = u & 1;
           const int s0 = 64 * qq + 32 * half;
-          float v[32];
-          if (!bad) {
-#pragma unroll
-            for (int t = 0; t < 32; ++t) v[t] = __ldcg(resb + (s0 + t) * kSliceR);
-          }
+          if (!bad && qq + 1 < rchunks) load_res(qq + 1, vq[(qq + 1) & 1]);
           if (!bad && u >= 2) {
             int w = 1;
             if (lane == 0) w = wait_phase(&bars.empty[slot], ((u >> 1) - 1) & 1, lim, &s_abort);
             bad |= !__shfl_sync(0xffffffffu, w, 0);
           }
           if (!bad) {
+            float (&v)[32] = vq[qq & 1];
 #pragma unroll
             for (int t = 0; t < 32; ++t) v[t] = -a.coef * (v[t] * siv[s0 + t]);
             unsigned char* rsl = ring + (size_t)slot * kRingSlot;

@@ -103,6 +103,15 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
                : "memory");
 }
 
+// Untiled bulk reduction: global[dst .. + bytes) += shared[src ..] as FP32
+// (addresses 16-byte aligned, size a multiple of 16), in a bulk group.
+__device__ __forceinline__ void bulk_reduce_add_f32(float* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                   dst),
+               "r"(saddr(src)), "r"(bytes)
+               : "memory");
+}
+
 // All committed bulk groups complete (their global writes performed).
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
