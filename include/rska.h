@@ -428,11 +428,7 @@ int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_
  * keeps Z^T in tensor memory (each CTA owns 128 right-hand sides x 256
  * columns; needs eta <= 256 and (n_p / 256) (R_p / 128) CTAs resident at
  * once, else EUNSUPPORTED).  what = 6: terms of the scaled residual in the
- * second product (1 or 2; 0 = the same as option 0).  what = 7: CTAs per
- * cluster of the persistent form (0 automatic; 1, 2 or 4, dividing n_p / 256
- * with every cluster of the grid resident at once, else EUNSUPPORTED): the
- * partial residual products of a cluster are summed in distributed shared
- * memory before the global reduction.
+ * second product (1 or 2; 0 = the same as option 0).
  * EINVAL for an unknown `what` or value.
  */
 int rska_mrhs_set_option(rska_mrhs *h, int what, int64_t value);
@@ -442,7 +438,7 @@ int rska_mrhs_set_option(rska_mrhs *h, int what, int64_t value);
  * first product's split over n, 2 n padded (multiple of 256), 3 eta padded
  * (multiple of 128), 4 R padded (multiple of 256), 5 terms (option 0),
  * 6 form of the next solve (1 staged, 2 persistent), 7 terms of the scaled
- * residual, 8 CTAs per cluster of the persistent form.
+ * residual.
  */
 int rska_mrhs_query(rska_mrhs *h, int what, int64_t *value);
 

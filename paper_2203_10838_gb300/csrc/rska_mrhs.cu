@@ -536,9 +536,6 @@ struct rska_mrhs {
   unsigned long long* pbar = nullptr;
   int32_t* pidx = nullptr;           // tau of one persistent launch
   int64_t pidx_cap = 0;
-  int cluster_opt = 0;               // CTAs per cluster of the persistent form (0 automatic)
-  int cluster_auto = 1;              // automatic choice (the tuner's, else 1)
-  int cluster_max = 1;               // the largest size whose clusters are all resident
   CUtensorMap mapG;
 };
 
@@ -814,7 +811,6 @@ cudaError_t solve_tmem(rska_mrhs* h, int64_t K) {
   a.nsplit_r = h->nsplit_r > 0 ? h->nsplit_r : h->nsplit;
   a.status = h->status;
   a.limit_ns = h->limit_ns;
-  a.cluster = h->cluster_opt > 0 ? h->cluster_opt : h->cluster_auto;
   for (int64_t done = 0; done < K && e == cudaSuccess;) {
     const int64_t cnt = std::min(h->pidx_cap, K - done);
     e = rska::launch_indices(h->thr, h->alias, h->m, h->seed, 0, h->k_host + done, cnt, h->eta,
@@ -898,9 +894,6 @@ int rska_mrhs_setup(rska_mrhs** out, const void* A, int64_t m, int64_t n, int64_
        (e = dalloc(&h->pidx, (size_t)h->pidx_cap * eta)) != cudaSuccess)) {
   }
   h->form = tmem_ok ? 2 : 1;
-  if (tmem_ok)
-    h->cluster_max = rska::mrhs_tmem_cluster((int)(h->n_p / 256), (int)(h->R_p / 128),
-                                             (int)h->eta_p64);
   cudaStream_t s = h->stream;
   if (e == cudaSuccess && tmem_ok) e = cudaMemsetAsync(h->G, 0, gs * 2, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
@@ -1003,12 +996,6 @@ int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
       if (value < 0 || value > 2) return RSKA_EINVAL;
       h->nsplit_r = (int)value;
       return RSKA_OK;
-    case 7:
-      if (value != 0 && value != 1 && value != 2 && value != 4) return RSKA_EINVAL;
-      if (value > 1 && (h->G == nullptr || (h->n_p / 256) % value != 0 || value > h->cluster_max))
-        return RSKA_EUNSUPPORTED;
-      h->cluster_opt = (int)value;
-      return RSKA_OK;
     default:
       return RSKA_EINVAL;
   }
@@ -1026,7 +1013,6 @@ int rska_mrhs_query(rska_mrhs* h, int what, int64_t* value) {
     case 5: *value = h->nsplit; return RSKA_OK;
     case 6: *value = h->form; return RSKA_OK;
     case 7: *value = h->nsplit_r > 0 ? h->nsplit_r : h->nsplit; return RSKA_OK;
-    case 8: *value = h->cluster_opt > 0 ? h->cluster_opt : h->cluster_auto; return RSKA_OK;
     default: return RSKA_EINVAL;
   }
 }

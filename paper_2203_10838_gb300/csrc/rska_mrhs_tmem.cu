@@ -19,8 +19,8 @@
 //     two-slot ring in shared memory; one thread issues the tcgen05 MMAs
 //     P^T (128 x eta_p, tensor-memory columns 256..) += X^T_chunk A_tau_chunk^T
 //     (M 128, N eta_p, K 16; both operands K-major).
-//  3. P^T is this CTA's share of the residual product; the epilogue stages
-//     it in shared memory and adds it with bulk reductions into a global
+//  3. P^T is this CTA's share of the residual product; the epilogue adds it
+//     with reductions (one 128-byte line per warp instruction) into a global
 //     accumulator of the right-hand-side slice that starts at -b_tau (the
 //     helper warps of each CTA of the slice write a block of rows of that
 //     start value one iteration ahead), and every CTA passes one bounded grid
@@ -112,57 +112,6 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Distributed shared memory: the address of the same shared-memory location
-// in CTA `rank` of the cluster, a 16-byte load from it, and an arrival on an
-// mbarrier there (release at cluster scope).
-__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-  return r;
-}
-
-__device__ __forceinline__ float4 ld_dsmem_v4(uint32_t addr) {
-  float4 v;
-  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(addr)
-               : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void mb_arrive_cluster(uint32_t remote_bar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar)
-               : "memory");
-}
-
-// Bounded wait on a local mbarrier whose arrivals come from other CTAs of the
-// cluster (acquire at cluster scope).
-__device__ __forceinline__ bool wait_phase_cluster(uint64_t* b, uint32_t parity, uint64_t limit_ns,
-                                                   const volatile int* abort) {
-  auto try_once = [&]() -> bool {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-  };
-  if (try_once()) return true;
-  const uint64_t t0 = global_timer_ns();
-  while (!try_once()) {
-    if (global_timer_ns() - t0 > limit_ns) return false;
-    if (abort != nullptr && *abort) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-
 // Barrier over the eight epilogue warps (named barrier 1) that also ORs a
 // flag across them.
 __device__ __forceinline__ int epi_sync_or(int pred) {
@@ -236,8 +185,6 @@ struct alignas(8) Bars {
   uint64_t gathered;    // both helper warps finished the next iteration's gather
   uint64_t fin;         // every MMA of this CTA complete (exit drain)
   uint64_t stage;       // gather staging buffer filled (bulk copy)
-  uint64_t rb_full;     // every CTA of the cluster has staged its partial products
-  uint64_t rb_empty;    // every CTA of the cluster has finished reading this CTA's stage
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -261,11 +208,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = tid >> 5;
   const int lane = tid & 31;
   const int nCTA = gridDim.x;
-  // consecutive CTAs take consecutive column slices of one right-hand-side
-  // slice, so a cluster (consecutive CTAs) shares the slice's accumulator
+  // consecutive CTAs take consecutive column slices of one right-hand-side slice
   const int rs = blockIdx.x / a.n_slices;
   const int cs = blockIdx.x % a.n_slices;
-  const int crank = blockIdx.x % a.cluster;
   const int rchunks = eta_p / 64;                        // scaled-residual chunks
   const int cnt = a.cnt;
 
@@ -281,8 +226,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     mb_init(&bars.gathered, 2);
     mb_init(&bars.fin, 1);
     mb_init(&bars.stage, 1);
-    mb_init(&bars.rb_full, (uint32_t)a.cluster);
-    mb_init(&bars.rb_empty, (uint32_t)a.cluster);
     s_abort = 0;
     s_flag = 1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -296,9 +239,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  // every CTA of the cluster has initialised its mbarriers before any remote
-  // arrival on them
-  if (a.cluster > 1) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   auto fail = [&]() {
@@ -475,10 +415,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     stage(0);
     for (int i = 0; i + 1 < cnt; ++i) {
-      // buffer (i + 1) % 2 and tables (i + 1) % 3 are free once grid barrier
-      // i has passed (every CTA has finished iteration i - 1)
+      // buffer (i + 1) % 2, tables (i + 1) % 3 and accumulator (i + 1) % 3
+      // are free once grid barrier i has passed (every CTA has finished
+      // iteration i - 1); waiting instead for this CTA's update of iteration
+      // i - 1 (which follows that barrier) starts the gather with iteration
+      // i's residual product, while the tensor pipe, not memory, is busy
       int ok = 1;
-      if (lane == 0) ok = wait_phase(&bars.passed, (uint32_t)(i & 1), a.limit_ns, &s_abort);
+      if (lane == 0)
+        ok = (i == 0) ? wait_phase(&bars.passed, 0u, a.limit_ns, &s_abort)
+                      : wait_phase(&bars.upd_done, (uint32_t)((i - 1) & 1), a.limit_ns, &s_abort);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       stage(i + 1);
@@ -509,7 +454,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     uint32_t u = 0;  // ring uses
-    uint32_t rb_rounds = 0;  // cluster pre-reduction rounds
     const uint64_t lim = a.limit_ns;
     // grid barrier b: every CTA's reductions, clears and gathers before it
     // are visible to every CTA after it
@@ -575,123 +519,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       // residual accumulator of this iteration and slice: rows s of 128
       // right-hand sides, so a warp's 32 right-hand sides are one 128-byte line
       float* resb = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR + row;
-      if (a.cluster == 1) {
-        // P^T staged in the free ring as rows s of 128 right-hand sides (the
-        // accumulator's layout), 128 rows of s at a time, and added to the
-        // accumulator by one bulk reduction per round
-        float* accs = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR;
-        float* stg = reinterpret_cast<float*>(ring);
-        for (int h2 = 0; 128 * h2 < eta_p; ++h2) {
-          const int cols = min(128, eta_p - 128 * h2);
-          if (h2 > 0 && tid == 128) bulk_wait_read();  // the previous round has read the stage
-          if (epi_sync_or(bad)) {
-            bad = 1;
-            break;
-          }
-          tc_fence_after();
-          for (int j = 0; j < 2; ++j) {
-            const int cl = 64 * half + 32 * j;
-            if (cl >= cols) break;
-            float v[32];
-            tmem_ld32(tl + kTmemRes + (uint32_t)(128 * h2 + cl), v);
+      if (!bad) {
+        tc_fence_after();
+        for (int j = 0; j < 4; ++j) {
+          const int col = 128 * half + 32 * j;
+          if (col >= eta_p) break;
+          float v[32];
+          tmem_ld32(tl + kTmemRes + (uint32_t)col, v);
 #pragma unroll
-            for (int t = 0; t < 32; ++t) stg[(cl + t) * kSliceR + row] = v[t];
-          }
-          tc_fence_before();
-          fence_proxy_async_smem();
-          if (epi_sync_or(bad)) {
-            bad = 1;
-            break;
-          }
-          if (tid == 128) {
-            bulk_reduce_add_f32(accs + (int64_t)128 * h2 * kSliceR, stg,
-                                (uint32_t)cols * kSliceR * 4u);
-            bulk_commit();
-          }
+          for (int t = 0; t < 32; ++t) red_add(resb + (col + t) * kSliceR, v[t]);
         }
-        // the reductions are complete before this CTA arrives at the grid barrier
-        if (tid == 128) {
-          bulk_wait_all();
-          fence_proxy_async_global();
-        }
-      } else {
-        // pre-reduction inside the cluster, 128 columns of P^T at a time: each
-        // CTA stages its partial products (128 rows x 128 FP32, 16-byte
-        // granules XOR-swizzled by row) in the free ring, then CTA `crank`
-        // sums rows [crank, crank + 1) x 128 / cluster over the cluster's
-        // stages and adds them to the global accumulator
-        const uint32_t rb = saddr(ring);
-        const int rows_per = kSliceR / a.cluster;
-        for (int h2 = 0; 128 * h2 < eta_p; ++h2) {
-          const int cols = min(128, eta_p - 128 * h2);
-          if (!bad && rb_rounds > 0) {
-            int w = 1;
-            if (lane == 0)
-              w = wait_phase_cluster(&bars.rb_empty, (uint32_t)((rb_rounds - 1) & 1), lim, &s_abort);
-            bad |= !__shfl_sync(0xffffffffu, w, 0);
-          }
-          if (!bad) {
-            tc_fence_after();
-            for (int j = 0; j < 2; ++j) {
-              const int cl = 64 * half + 32 * j;  // column within the round
-              if (cl >= cols) break;
-              float v[32];
-              tmem_ld32(tl + kTmemRes + (uint32_t)(128 * h2 + cl), v);
-#pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                const int g = (cl >> 2) + t;
-                *reinterpret_cast<float4*>(ring + row * 512 + ((g ^ (row & 31)) << 4)) =
-                    make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
-              }
-            }
-            tc_fence_before();
-          }
-          if (epi_sync_or(bad)) {
-            bad = 1;
-            break;
-          }
-          if (tid == 128) {
-            for (int p = 0; p < a.cluster; ++p) mb_arrive_cluster(mapa(saddr(&bars.rb_full), (uint32_t)p));
-          }
-          {
-            int w = 1;
-            if (lane == 0) w = wait_phase_cluster(&bars.rb_full, (uint32_t)(rb_rounds & 1), lim, &s_abort);
-            bad |= !__shfl_sync(0xffffffffu, w, 0);
-            __syncwarp();  // lane 0's acquire orders the other lanes' reads of the stages
-          }
-          if (!bad) {
-            const int gpr = cols >> 2;  // granules per row in this round
-            for (int x = tid - 128; x < rows_per * gpr; x += kEpiThreads) {
-              const int rr = crank * rows_per + x / gpr;
-              const int g = x % gpr;
-              const uint32_t off = (uint32_t)(rr * 512 + ((g ^ (rr & 31)) << 4));
-              float4 acc = ld_dsmem_v4(mapa(rb + off, 0u));
-              for (int p = 1; p < a.cluster; ++p) {
-                const float4 q4 = ld_dsmem_v4(mapa(rb + off, (uint32_t)p));
-                acc.x += q4.x;
-                acc.y += q4.y;
-                acc.z += q4.z;
-                acc.w += q4.w;
-              }
-              float* dst = a.Res + (((int64_t)(i % 3) * a.r_slices + rs) * eta_p + 128 * h2 + 4 * g) *
-                                       kSliceR + rr;
-              red_add(dst, acc.x);
-              red_add(dst + kSliceR, acc.y);
-              red_add(dst + 2 * kSliceR, acc.z);
-              red_add(dst + 3 * kSliceR, acc.w);
-            }
-          }
-          if (epi_sync_or(bad)) {
-            bad = 1;
-            break;
-          }
-          if (tid == 128) {
-            for (int p = 0; p < a.cluster; ++p) mb_arrive_cluster(mapa(saddr(&bars.rb_empty), (uint32_t)p));
-          }
-          ++rb_rounds;
-        }
+        tc_fence_before();
       }
-
       // slots s of tau beyond eta carry 1/||a||^2 = 0 (their residual is zero)
       const float* siv = s_iv[i % 3];
       ok = grid_sync(i + 1, (i + 1 < cnt) ? 1 : 0);
@@ -700,26 +539,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       // (the accumulator started at -b_tau); the loads of chunk qq + 1 are in
       // flight while chunk qq is formed ----
       {
-        float vq[2][32];
-        auto load_res = [&](int qq, float (&v)[32]) {
-          const int s0 = 64 * qq + 32 * half;
-#pragma unroll
-          for (int t = 0; t < 32; ++t) v[t] = __ldcg(resb + (s0 + t) * kSliceR);
-        };
-        if (!bad) load_res(0, vq[0]);
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          if (qq >= rchunks) break;
+        for (int qq = 0; qq < rchunks; ++qq) {
           const uint32_t slot = u & 1;
           const int s0 = 64 * qq + 32 * half;
-          if (!bad && qq + 1 < rchunks) load_res(qq + 1, vq[(qq + 1) & 1]);
+          float v[32];
+          if (!bad) {
+#pragma unroll
+            for (int t = 0; t < 32; ++t) v[t] = __ldcg(resb + (s0 + t) * kSliceR);
+          }
           if (!bad && u >= 2) {
             int w = 1;
             if (lane == 0) w = wait_phase(&bars.empty[slot], ((u >> 1) - 1) & 1, lim, &s_abort);
             bad |= !__shfl_sync(0xffffffffu, w, 0);
           }
           if (!bad) {
-            float (&v)[32] = vq[qq & 1];
 #pragma unroll
             for (int t = 0; t < 32; ++t) v[t] = -a.coef * (v[t] * siv[s0 + t]);
             unsigned char* rsl = ring + (size_t)slot * kRingSlot;
@@ -772,8 +605,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
   }
   __syncthreads();
-  // no CTA leaves while another CTA of its cluster may still read its stage
-  if (a.cluster > 1) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -804,49 +635,11 @@ cudaError_t launch_mrhs_tmem(const CUtensorMap& mapG, const MrhsTmemArgs& a, cud
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  if (a.cluster > 1) {
-    // clusters of consecutive CTAs; mrhs_tmem_cluster has checked that every
-    // cluster of the grid can be resident at once, as the grid barrier needs
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)a.cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-  } else {
-    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barrier needs it
-    attr[0].val.cooperative = 1;
-  }
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barrier needs it
+  attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, mrhs_tmem_kernel, mapG, a);
-}
-
-int mrhs_tmem_cluster(int n_slices, int r_slices, int eta_p) {
-  const size_t smem = mrhs_tmem_smem(eta_p);
-  if (cudaFuncSetAttribute(mrhs_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return 1;
-  const int grid = n_slices * r_slices;
-  for (int c = 4; c >= 2; c /= 2) {
-    if (n_slices % c != 0) continue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)c;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, mrhs_tmem_kernel, &cfg) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    if ((int64_t)nc * c >= grid) return c;
-  }
-  return 1;
 }
 
 }  // namespace rska

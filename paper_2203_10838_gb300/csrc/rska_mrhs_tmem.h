@@ -22,8 +22,6 @@ struct MrhsTmemArgs {
   int32_t n_slices;        // n_p / 256
   int32_t r_slices;        // R_p / 128
   int32_t cnt;             // iterations of this launch
-  int32_t cluster;         // CTAs per cluster along the column slices (1, 2 or 4): the
-                           // residual product is pre-reduced among them in shared memory
   const int32_t* idx;      // tau of the cnt iterations, iteration-major, eta each
   const float* inv_nu;     // 1 / ||a_i||^2 (FP32 of the FP64 norms)
   const float* Bt;         // m x R_p: Bt[i][j] = (b_j)_i
@@ -48,8 +46,5 @@ bool mrhs_tmem_fits(int64_t n_p, int64_t R_p, int64_t eta_p, int num_sms);
 // mapG: 2-D map over G (n_p columns, 2 eta_p rows, BF16), box 64 x eta_p,
 // 128-byte swizzle
 cudaError_t launch_mrhs_tmem(const CUtensorMap& mapG, const MrhsTmemArgs& a, cudaStream_t s);
-// largest cluster size among 4, 2, 1 that divides n_slices and for which every
-// cluster of the grid can be resident at once
-int mrhs_tmem_cluster(int n_slices, int r_slices, int eta_p);
 
 }  // namespace rska

@@ -309,9 +309,9 @@ class BatchSolver:
 
 
 MRHS_OPTION = {"terms": 0, "ksplit": 1, "watchdog_us": 2, "graph": 3, "pdl": 4, "form": 5,
-               "terms_update": 6, "cluster": 7}
+               "terms_update": 6}
 MRHS_QUERY = {"k": 0, "ksplit": 1, "n_pad": 2, "eta_pad": 3, "R_pad": 4, "terms": 5, "form": 6,
-              "terms_update": 7, "cluster": 8}
+              "terms_update": 7}
 MRHS_FORM = {"auto": 0, "staged": 1, "persistent": 2}
 
 

@@ -46,7 +46,7 @@ FORMS = ["staged", "persistent"]
 
 
 def run_case(env, m, n, R, s, eta, lam, t, K, seed, check_rows, tol, terms=2, pseed=21,
-             form="auto", terms_update=0, cluster=0):
+             form="auto", terms_update=0):
     torch, orc, MultiRHS = env
     from paper_2203_10838_gb300.rska import MRHS_FORM
     p = multi_rhs_problem(m, n, R, s, seed=pseed)
@@ -57,9 +57,6 @@ def run_case(env, m, n, R, s, eta, lam, t, K, seed, check_rows, tol, terms=2, ps
             assert h.query("form") == MRHS_FORM[form]
         h.set_option("terms", terms)
         h.set_option("terms_update", terms_update)
-        if cluster:
-            h.set_option("cluster", cluster)
-            assert h.query("cluster") == cluster
         nu_g, thr_g, al_g = [v.cpu().numpy() for v in h.get_tables()]
         tau_g = h.get_indices(0, K).cpu().numpy()
         h.solve(K)
@@ -91,15 +88,6 @@ def test_mrhs_persistent_first_iterations(env, K):
     on): 128 right-hand sides on two column slices, eta = 64."""
     run_case(env, 600, 512, 128, 8, eta=64, lam=0.0, t=2.0, K=K, seed=9,
              check_rows=range(0, 128, 5), tol=1e-4, form="persistent")
-
-
-@pytest.mark.parametrize("cluster", [1, 2, 4])
-def test_mrhs_persistent_cluster_sizes(env, cluster):
-    """The persistent form with its residual products pre-reduced in clusters
-    of 1, 2 and 4 CTAs (4 column slices x 2 right-hand-side slices; eta = 200
-    padded to 256, so both 128-column rounds of the pre-reduction run)."""
-    run_case(env, 2000, 1000, 200, 20, eta=200, lam=0.5, t=8.0, K=25, seed=13,
-             check_rows=range(0, 200, 9), tol=1e-4, form="persistent", cluster=cluster)
 
 
 @pytest.mark.parametrize("form", FORMS)
