@@ -203,7 +203,8 @@ int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
  * rska_set_option -- tuning knobs, applied from the next solve:
  *   what = 0: CTAs in the persistent grid (0 = automatic)
  *          1: watchdog limit of each device-side wait, in microseconds
- *             (default 2,000,000)
+ *             (default 2,000,000; 0: a wait that is not satisfied at its first
+ *             poll expires, which exercises the failure path)
  *          2: solver kernel: 0 automatic (row-split when n <= 11520, else
  *             column-split), 1 column-split, 2 row-split
  * The row-split kernel gives each CTA whole rows of tau_k (TMA bulk copies)
@@ -417,7 +418,8 @@ int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_
  * first product, the scaled residual in the second): 2 (default) = BF16 high
  * + BF16 low part (relative representation error 2^-17), 1 = one BF16 term
  * (2^-9).  what = 1: CTAs splitting the first product's contraction over n
- * (0 = automatic, one wave).  what = 2: device wait limit in microseconds.
+ * (0 = automatic, one wave).  what = 2: device wait limit in microseconds (0: a wait not satisfied at
+ * its first poll expires).
  * what = 3: 1 (default) replays 64-iteration chunks as a CUDA graph, 0
  * launches every kernel directly.  what = 4: 1 (default) launches each
  * kernel of an iteration as a programmatic dependent of the previous one

@@ -690,7 +690,7 @@ int rska_set_option(rska_ctx* h, int what, int64_t value) {
       return rc;
     }
     case 1:
-      if (value < 1) return RSKA_EINVAL;
+      if (value < 0) return RSKA_EINVAL;
       c->limit_ns = (uint64_t)value * 1000ull;
       return RSKA_OK;
     case 2: {

@@ -341,7 +341,7 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
         uint32_t spins = 0;
         while ((drawn = S.drawn) <= e) {
           if (S.abort) return -1;
-          if ((++spins & 63u) == 0 && global_timer_ns() - t0 > a.limit_ns) return -1;
+          if ((++spins & 63u) == 0 && (a.limit_ns == 0 || global_timer_ns() - t0 > a.limit_ns)) return -1;
         }
       }
       __threadfence_block();
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(BT, 1) rska_batched_kernel(BatchArgs a) {
             // far ahead: sleep rather than spin, a spinning warp steals the
             // shared-memory pipe from the consumers
             __nanosleep(500);
-            if ((++spins & 15u) == 0 && global_timer_ns() - t0 > a.limit_ns) {
+            if ((++spins & 15u) == 0 && (a.limit_ns == 0 || global_timer_ns() - t0 > a.limit_ns)) {
               atomicCAS(a.status, kStatusOk, kStatusTimeout);
               S.abort = 1;
             }

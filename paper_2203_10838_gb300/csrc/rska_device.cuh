@@ -125,7 +125,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
     const uint64_t t0 = global_timer_ns();
     uint32_t spins = 0;
     while (ld_acquire_u64(counter) < target) {
-      if (global_timer_ns() - t0 > limit_ns) {
+      if (limit_ns == 0 || global_timer_ns() - t0 > limit_ns) {
         atomicCAS(status, kStatusOk, kStatusTimeout);
         ok = 0;
         break;

@@ -975,7 +975,7 @@ int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
       h->ksplit = (int)value;
       return RSKA_OK;
     case 2:
-      if (value < 1) return RSKA_EINVAL;
+      if (value < 0) return RSKA_EINVAL;
       h->limit_ns = (uint64_t)value * 1000ull;
       return RSKA_OK;
     case 3:

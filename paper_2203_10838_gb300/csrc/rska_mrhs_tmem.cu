@@ -92,6 +92,7 @@ __device__ __forceinline__ void mb_arrive(uint64_t* b) {
 __device__ __forceinline__ bool wait_phase(uint64_t* b, uint32_t parity, uint64_t limit_ns,
                                            const volatile int* abort) {
   if (mb_try_wait(b, parity)) return true;
+  if (limit_ns == 0) return false;  // a zero limit expires at the first failed poll
   const uint64_t t0 = global_timer_ns();
   while (!mb_try_wait(b, parity)) {
     if (global_timer_ns() - t0 > limit_ns) return false;
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t t0 = global_timer_ns();
           uint32_t spins = 0;
           while (ld_acquire_u64(a.bar) < target) {
-            if (global_timer_ns() - t0 > lim) {
+            if (lim == 0 || global_timer_ns() - t0 > lim) {
               ok = 0;
               break;
             }

@@ -121,6 +121,7 @@ __device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity, uint64_t limit_ns,
                                                   const volatile int* abort) {
   if (mbar_try_wait(b, parity)) return true;
+  if (limit_ns == 0) return false;  // a zero limit expires at the first failed poll
   const uint64_t t0 = global_timer_ns();
   while (!mbar_try_wait(b, parity)) {
     if (global_timer_ns() - t0 > limit_ns) return false;
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(NT, 1)
       const uint64_t t0 = global_timer_ns();
       uint32_t spins = 0;
       while (ld_acquire_u64(a.bar) < target) {
-        if (global_timer_ns() - t0 > a.limit_ns) {
+        if (a.limit_ns == 0 || global_timer_ns() - t0 > a.limit_ns) {
           atomicCAS(a.status, kStatusOk, kStatusTimeout);
           ok = 0;
           break;

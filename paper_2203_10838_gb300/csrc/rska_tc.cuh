@@ -44,6 +44,7 @@ __device__ __forceinline__ bool mb_try_wait(uint64_t* b, uint32_t parity) {
 // the timeout and winds down instead of hanging).
 __device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns) {
   if (mb_try_wait(b, parity)) return true;
+  if (limit_ns == 0) return false;  // a zero limit expires at the first failed poll
   const uint64_t t0 = global_timer_ns();
   while (!mb_try_wait(b, parity)) {
     if (global_timer_ns() - t0 > limit_ns) return false;

@@ -92,7 +92,7 @@ def test_load_host_reuses_the_context_for_a_new_problem(env):
         assert sol.query("setup_total_us") > 0 and sol.query("setup_alias_us") > 0
         sol.solve(K)
         sol.set_weights(torch.full((m,), 2.0, device="cuda"), couple=True)
-        sol.set_option("watchdog_us", 1)
+        sol.set_option("watchdog_us", 0)
         sol.solve(50)
         with pytest.raises(RSKAError):
             sol.get_x()

@@ -4,10 +4,11 @@ GPU fault).
 Every wait inside the solver kernels (the grid barrier, the mbarrier ring of
 the row-split kernel, the tensor-core pipeline of the multi-right-hand-side
 form) gives up after a limit set per context (rska_set_option(ctx, 1, us),
-rska_mrhs_set_option(h, 2, us)).  A limit of one microsecond is shorter than
-one grid barrier or one row copy, so the first wait that does not complete at
-once runs out: the kernel records RSKA_ETIMEOUT in the context's status word,
-lets the copies it has already issued land, and returns.  Nothing hangs: the
+rska_mrhs_set_option(h, 2, us)).  With a limit of zero the first wait that is
+not satisfied at its first poll runs out (every grid barrier has a CTA that
+arrives first and must wait): the kernel records RSKA_ETIMEOUT in the
+context's status word, lets the copies it has already issued land, and
+returns.  Nothing hangs: the
 waits give up and return, and copies in flight are always drained.
 
 Checked: the next synchronizing call reports RSKA_ETIMEOUT, the error is
@@ -53,7 +54,7 @@ def test_single_system_wait_limit_runs_out_and_context_recovers(env, kernel):
     b = torch.from_numpy(prob.b).cuda()
     with Solver(A, b, lam, eta, t, seed, n=n) as sol:
         sol.set_option("kernel", KERNEL[kernel])
-        sol.set_option("watchdog_us", 1)
+        sol.set_option("watchdog_us", 0)
         sol.solve(200)
         with pytest.raises(RSKAError) as ei:
             sol.get_x()
@@ -90,7 +91,7 @@ def test_multi_rhs_wait_limit_runs_out_and_context_recovers(env, form):
     B = torch.from_numpy(p.B).cuda()
     with MultiRHS(A, B, lam, eta, t, seed, n=n) as h:
         h.set_option("form", MRHS_FORM[form])
-        h.set_option("watchdog_us", 1)
+        h.set_option("watchdog_us", 0)
         h.solve(70)
         with pytest.raises(RSKAError) as ei:
             h.get_x()
