@@ -430,7 +430,12 @@ int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_
  * keeps Z^T in tensor memory (each CTA owns 128 right-hand sides x 256
  * columns; needs eta <= 256 and (n_p / 256) (R_p / 128) CTAs resident at
  * once, else EUNSUPPORTED).  what = 6: terms of the scaled residual in the
- * second product (1 or 2; 0 = the same as option 0).
+ * second product (1 or 2; 0 = the same as option 0).  what = 7: gather
+ * schedule of the persistent form: 0 the helper warps copy the next
+ * iteration's rows of A while the residual product runs, 1 as soon as the
+ * grid barrier has passed.
+ * Setting option 1, 4, 5 (non-zero) or 7 pins the schedule; otherwise the
+ * first rska_mrhs_solve of at least 128 iterations picks it (rska_mrhs_tune).
  * EINVAL for an unknown `what` or value.
  */
 int rska_mrhs_set_option(rska_mrhs *h, int what, int64_t value);
@@ -440,9 +445,49 @@ int rska_mrhs_set_option(rska_mrhs *h, int what, int64_t value);
  * first product's split over n, 2 n padded (multiple of 256), 3 eta padded
  * (multiple of 128), 4 R padded (multiple of 256), 5 terms (option 0),
  * 6 form of the next solve (1 staged, 2 persistent), 7 terms of the scaled
- * residual.
+ * residual, 8 gather schedule, 9 the autotuner's choice (a code as in
+ * rska_mrhs_tune; 0 before tuning), 10 its time per iteration in
+ * nanoseconds, 11 the split over n of the staged form (0 = one wave), 12
+ * programmatic dependent launches on (1) or off.
  */
 int rska_mrhs_query(rska_mrhs *h, int what, int64_t *value);
+
+/*
+ * rska_mrhs_tune -- pick the fastest schedule of the iteration on this device
+ * (the matrix form of Sec. 3 has several valid ways to run): every candidate
+ * of rska_tune_candidates runs `iters` iterations (1..100000) after a
+ * warm-up, timed with CUDA events on the context's stream, starting each time
+ * from a saved copy of the iterate; afterwards the iterate and the iteration
+ * count are what they were, and the fastest candidate is used from the next
+ * solve and cached under the problem's shape, precision options and device
+ * (see rska_tune_cache).  HOST outputs (nullable): the chosen code and its
+ * microseconds per iteration.  Synchronous; allocates a temporary copy of the
+ * iterate.  Errors: EINVAL, ENOMEM, ECUDA, a sticky code.
+ */
+int rska_mrhs_tune(rska_mrhs *h, int32_t iters, int32_t *code_out, double *us_per_iter_out);
+
+/*
+ * rska_tune_candidates -- HOST, no device work: the candidate schedules of a
+ * multi-right-hand-side problem with n columns, R right-hand sides and batch
+ * size eta on a GPU with num_sms SMs.  Each is a code: bits 0-1 the form
+ * (1 staged kernels, 2 persistent kernel); staged: bits 8-15 the split of the
+ * first product over n (0 = one wave), bit 16 programmatic dependent
+ * launches; persistent: bit 17 the gather schedule.  Writes up to `max` codes
+ * and the total count (count_out).  Errors: EINVAL.
+ */
+int rska_tune_candidates(int64_t n, int64_t R, int32_t eta, int32_t num_sms, int32_t *codes_out,
+                         int32_t max, int32_t *count_out);
+
+/*
+ * rska_tune_cache -- HOST, no device work: the process-wide cache of tuned
+ * choices.  op 0: look up `key` (code and us out; EUNSUPPORTED when absent);
+ * 1: store code and us under `key` (no spaces, at most 500 characters);
+ * 2: write every entry to the file `key_or_path`; 3: read entries from it;
+ * 4: clear.  With the environment variable RSKA_TUNE_CACHE naming a file,
+ * that file is read at the first lookup and each new entry is appended.
+ * Errors: EINVAL.
+ */
+int rska_tune_cache(int32_t op, const char *key_or_path, int32_t *code, double *us);
 
 /*
  * rska_mrhs_solve -- K more iterations (K >= 0) for every right-hand side,

@@ -60,6 +60,9 @@ def _declare(lib):
         "rska_mrhs_set_option": ([P, c_int, i64], c_int),
         "rska_mrhs_query": ([P, c_int, ctypes.POINTER(i64)], c_int),
         "rska_mrhs_solve": ([P, i64], c_int),
+        "rska_mrhs_tune": ([P, i32, ctypes.POINTER(i32), ctypes.POINTER(f64)], c_int),
+        "rska_tune_candidates": ([i64, i64, i32, i32, P, i32, ctypes.POINTER(i32)], c_int),
+        "rska_tune_cache": ([i32, ctypes.c_char_p, ctypes.POINTER(i32), ctypes.POINTER(f64)], c_int),
         "rska_mrhs_get_x": ([P, P, P], c_int),
         "rska_mrhs_get_indices": ([P, i64, i64, P], c_int),
         "rska_mrhs_get_tables": ([P, P, P, P], c_int),

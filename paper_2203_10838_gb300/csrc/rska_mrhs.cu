@@ -29,14 +29,17 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "rska_device.cuh"
 #include "rska_internal.h"
 #include "rska_mrhs_tmem.h"
 #include "rska_tc.cuh"
+#include "rska_tune.h"
 
 namespace rska {
 namespace {
@@ -536,6 +539,14 @@ struct rska_mrhs {
   unsigned long long* pbar = nullptr;
   int32_t* pidx = nullptr;           // tau of one persistent launch
   int64_t pidx_cap = 0;
+  int gather_sched = 0;              // persistent form: gather with the residual product (0) or
+                                     // after the grid barrier (1)
+  // autotuner: the schedule in use comes from it while the options that
+  // choose a schedule (1, 4, 5, 7) are left automatic
+  bool pinned = false;               // a schedule option was set explicitly
+  bool tuned = false;
+  int32_t tuned_code = 0;
+  double tuned_us = 0.0;
   CUtensorMap mapG;
 };
 
@@ -811,6 +822,7 @@ cudaError_t solve_tmem(rska_mrhs* h, int64_t K) {
   a.nsplit_r = h->nsplit_r > 0 ? h->nsplit_r : h->nsplit;
   a.status = h->status;
   a.limit_ns = h->limit_ns;
+  a.gather_sched = h->gather_sched;
   for (int64_t done = 0; done < K && e == cudaSuccess;) {
     const int64_t cnt = std::min(h->pidx_cap, K - done);
     e = rska::launch_indices(h->thr, h->alias, h->m, h->seed, 0, h->k_host + done, cnt, h->eta,
@@ -824,6 +836,121 @@ cudaError_t solve_tmem(rska_mrhs* h, int64_t K) {
   }
   if (K > 0) h->x_stale = true;
   return e;
+}
+
+int fail(rska_mrhs* h, cudaError_t e);
+
+// solves of at least this many iterations choose the schedule automatically
+constexpr int64_t kAutoTuneMinIters = 128;
+
+// The autotuner's key: problem shape, precision options and device.
+std::string tune_key(const rska_mrhs* h) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::memset(&prop, 0, sizeof(prop));
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    std::snprintf(prop.name, sizeof(prop.name), "unknown");
+  std::string name(prop.name);
+  for (char& ch : name)
+    if (ch == ' ') ch = '_';
+  char buf[400];
+  std::snprintf(buf, sizeof(buf), "mrhs:m=%lld:n=%lld:R=%lld:eta=%d:terms=%d/%d:%s:sms=%d",
+                (long long)h->m, (long long)h->n, (long long)h->R, (int)h->eta, h->nsplit,
+                h->nsplit_r > 0 ? h->nsplit_r : h->nsplit, name.c_str(), h->num_sms);
+  return std::string(buf);
+}
+
+void apply_code(rska_mrhs* h, int32_t code) {
+  if (rska::tune_form(code) == rska::kFormPersistent && h->G != nullptr) {
+    h->form = 2;
+    h->gather_sched = rska::tune_gsched(code);
+  } else {
+    h->form = 1;
+    h->ksplit = rska::tune_ksplit(code);
+    h->use_pdl = rska::tune_pdl(code);
+  }
+}
+
+cudaError_t solve_current(rska_mrhs* h, int64_t K) {
+  return (h->form == 2) ? solve_tmem(h, K) : solve_staged(h, K);
+}
+
+// Time every candidate schedule for `iters` iterations (after a warm-up that
+// also builds any CUDA graph) from a saved copy of the iterate, put the state
+// back, and keep the fastest.  The iterate and the iteration count are the
+// same afterwards as before.
+int tune_impl(rska_mrhs* h, int32_t iters, int32_t* code_out, double* us_out) {
+  int32_t cands[32];
+  const int nc = rska::tune_candidates(h->n_p, h->R_p, h->eta_p64, h->num_sms, h->G != nullptr,
+                                       cands, 32);
+  cudaStream_t s = h->stream;
+  const size_t zbytes = sizeof(float) * (size_t)h->R_p * h->n_p;
+  float* zsave = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaError_t e = cudaMalloc(&zsave, zbytes);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(zsave, h->Zt, zbytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+  const int64_t k0 = h->k_host;
+  const int save_form = h->form, save_ks = h->ksplit, save_pdl = h->use_pdl, save_g = h->gather_sched;
+  const bool save_stale = h->x_stale;
+  auto restore = [&]() -> cudaError_t {
+    h->k_host = k0;
+    h->x_stale = true;  // the staged form rebuilds X from Z
+    return cudaMemcpyAsync(h->Zt, zsave, zbytes, cudaMemcpyDeviceToDevice, s);
+  };
+  int32_t best = 0;
+  double best_us = 0.0;
+  for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+    apply_code(h, cands[c]);
+    e = restore();
+    if (e == cudaSuccess) e = solve_current(h, std::min<int64_t>(iters, 64));
+    if (e == cudaSuccess) e = restore();
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
+    if (e == cudaSuccess) e = solve_current(h, iters);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) break;
+    if (st != 0) {
+      h->sticky = st;
+      break;
+    }
+    const double us = 1000.0 * ms / iters;
+    if (best == 0 || us < best_us) {
+      best = cands[c];
+      best_us = us;
+    }
+  }
+  // back to the state before tuning, with the fastest schedule (or the
+  // previous one when nothing could be timed)
+  h->form = save_form;
+  h->ksplit = save_ks;
+  h->use_pdl = save_pdl;
+  h->gather_sched = save_g;
+  if (e == cudaSuccess && zsave) {
+    e = restore();
+    h->x_stale = save_stale || best != 0;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (zsave) cudaFree(zsave);
+  if (e != cudaSuccess) return fail(h, e);
+  if (h->sticky) return h->sticky;
+  if (best != 0) {
+    apply_code(h, best);
+    h->tuned = true;
+    h->tuned_code = best;
+    h->tuned_us = best_us;
+    rska::tune_cache_put(tune_key(h), best, best_us);
+  }
+  if (code_out) *code_out = best;
+  if (us_out) *us_out = best_us;
+  return RSKA_OK;
 }
 
 int fail(rska_mrhs* h, cudaError_t e) {
@@ -973,6 +1100,7 @@ int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
     case 1:
       if (value < 0 || value > 4096) return RSKA_EINVAL;
       h->ksplit = (int)value;
+      h->pinned = true;
       return RSKA_OK;
     case 2:
       if (value < 0) return RSKA_EINVAL;
@@ -985,16 +1113,23 @@ int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
     case 4:
       if (value != 0 && value != 1) return RSKA_EINVAL;
       h->use_pdl = (int)value;
+      h->pinned = true;
       return RSKA_OK;
     case 5:
       if (value < 0 || value > 2) return RSKA_EINVAL;
       if (value == 2 && h->G == nullptr) return RSKA_EUNSUPPORTED;
       h->form_opt = (int)value;
       h->form = value == 1 ? 1 : (h->G != nullptr ? 2 : 1);
+      h->pinned = value != 0;
       return RSKA_OK;
     case 6:
       if (value < 0 || value > 2) return RSKA_EINVAL;
       h->nsplit_r = (int)value;
+      return RSKA_OK;
+    case 7:
+      if (value != 0 && value != 1) return RSKA_EINVAL;
+      h->gather_sched = (int)value;
+      h->pinned = true;
       return RSKA_OK;
     default:
       return RSKA_EINVAL;
@@ -1013,13 +1148,39 @@ int rska_mrhs_query(rska_mrhs* h, int what, int64_t* value) {
     case 5: *value = h->nsplit; return RSKA_OK;
     case 6: *value = h->form; return RSKA_OK;
     case 7: *value = h->nsplit_r > 0 ? h->nsplit_r : h->nsplit; return RSKA_OK;
+    case 8: *value = h->gather_sched; return RSKA_OK;
+    case 9: *value = h->tuned ? h->tuned_code : 0; return RSKA_OK;
+    case 10: *value = h->tuned ? (int64_t)(1000.0 * h->tuned_us) : 0; return RSKA_OK;
+    case 11: *value = h->form == 2 ? 0 : h->ksplit; return RSKA_OK;
+    case 12: *value = h->use_pdl; return RSKA_OK;
     default: return RSKA_EINVAL;
   }
+}
+
+int rska_mrhs_tune(rska_mrhs* h, int32_t iters, int32_t* code_out, double* us_out) {
+  if (!h || iters < 1 || iters > 100000) return RSKA_EINVAL;
+  if (h->sticky) return h->sticky;
+  return tune_impl(h, iters, code_out, us_out);
 }
 
 int rska_mrhs_solve(rska_mrhs* h, int64_t K) {
   if (!h || K < 0) return RSKA_EINVAL;
   if (h->sticky) return h->sticky;
+  if (!h->pinned && !h->tuned && K >= kAutoTuneMinIters) {
+    // the first long solve picks the schedule: from the cache when this
+    // shape was measured before on this device, else by timing the candidates
+    int32_t code = 0;
+    double us = 0.0;
+    if (rska::tune_cache_get(tune_key(h), &code, &us)) {
+      apply_code(h, code);
+      h->tuned = true;
+      h->tuned_code = code;
+      h->tuned_us = us;
+    } else {
+      const int rc = tune_impl(h, 64, nullptr, nullptr);
+      if (rc != RSKA_OK) return rc;
+    }
+  }
   const cudaError_t e = (h->form == 2) ? solve_tmem(h, K) : solve_staged(h, K);
   if (e != cudaSuccess) return fail(h, e);
   h->k_host += K;

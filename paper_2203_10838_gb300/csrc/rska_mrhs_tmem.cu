@@ -418,13 +418,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = 0; i + 1 < cnt; ++i) {
       // buffer (i + 1) % 2, tables (i + 1) % 3 and accumulator (i + 1) % 3
       // are free once grid barrier i has passed (every CTA has finished
-      // iteration i - 1); waiting instead for this CTA's update of iteration
-      // i - 1 (which follows that barrier) starts the gather with iteration
-      // i's residual product, while the tensor pipe, not memory, is busy
+      // iteration i - 1): schedule 1 starts the gather then; schedule 0 waits
+      // for this CTA's update of iteration i - 1 (which follows that
+      // barrier), so the gather runs with iteration i's residual product,
+      // while the tensor pipe, not memory, is busy
       int ok = 1;
       if (lane == 0)
-        ok = (i == 0) ? wait_phase(&bars.passed, 0u, a.limit_ns, &s_abort)
-                      : wait_phase(&bars.upd_done, (uint32_t)((i - 1) & 1), a.limit_ns, &s_abort);
+        ok = (i == 0 || a.gather_sched == 1)
+                 ? wait_phase(&bars.passed, (uint32_t)(i & 1), a.limit_ns, &s_abort)
+                 : wait_phase(&bars.upd_done, (uint32_t)((i - 1) & 1), a.limit_ns, &s_abort);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       stage(i + 1);

@@ -22,6 +22,9 @@ struct MrhsTmemArgs {
   int32_t n_slices;        // n_p / 256
   int32_t r_slices;        // R_p / 128
   int32_t cnt;             // iterations of this launch
+  int32_t gather_sched;    // when the helper warps gather the next iteration's rows:
+                           // 0 with the residual product (after this CTA's previous
+                           // update), 1 as soon as the grid barrier has passed
   const int32_t* idx;      // tau of the cnt iterations, iteration-major, eta each
   const float* inv_nu;     // 1 / ||a_i||^2 (FP32 of the FP64 norms)
   const float* Bt;         // m x R_p: Bt[i][j] = (b_j)_i

@@ -309,9 +309,41 @@ class BatchSolver:
 
 
 MRHS_OPTION = {"terms": 0, "ksplit": 1, "watchdog_us": 2, "graph": 3, "pdl": 4, "form": 5,
-               "terms_update": 6}
+               "terms_update": 6, "gather_sched": 7}
 MRHS_QUERY = {"k": 0, "ksplit": 1, "n_pad": 2, "eta_pad": 3, "R_pad": 4, "terms": 5, "form": 6,
-              "terms_update": 7}
+              "terms_update": 7, "gather_sched": 8, "tuned_code": 9, "tuned_ns": 10,
+              "ksplit_used": 11, "pdl": 12}
+
+
+def decode_schedule(code: int) -> dict:
+    """A schedule code of rska_mrhs_tune / rska_tune_candidates as a dict."""
+    form = code & 3
+    if form == 2:
+        return {"form": "persistent", "gather_sched": (code >> 17) & 1}
+    return {"form": "staged", "ksplit": (code >> 8) & 0xff, "pdl": (code >> 16) & 1}
+
+
+def tune_candidates(n: int, R: int, eta: int, num_sms: int) -> list:
+    """rska_tune_candidates: the candidate schedule codes (no device work)."""
+    count = ctypes.c_int32()
+    check(lib().rska_tune_candidates(int(n), int(R), int(eta), int(num_sms), None, 0,
+                                     ctypes.byref(count)), "rska_tune_candidates")
+    buf = (ctypes.c_int32 * max(1, count.value))()
+    check(lib().rska_tune_candidates(int(n), int(R), int(eta), int(num_sms), buf, count.value,
+                                     ctypes.byref(count)), "rska_tune_candidates")
+    return [int(buf[i]) for i in range(count.value)]
+
+
+def tune_cache(op: str, key_or_path: str | None = None, code: int = 0, us: float = 0.0):
+    """rska_tune_cache: op "get" -> (code, us) or None, "put", "save", "load", "clear"."""
+    ops = {"get": 0, "put": 1, "save": 2, "load": 3, "clear": 4}
+    c = ctypes.c_int32(int(code))
+    u = ctypes.c_double(float(us))
+    k = key_or_path.encode() if key_or_path is not None else None
+    rc = lib().rska_tune_cache(ops[op], k, ctypes.byref(c), ctypes.byref(u))
+    if op == "get":
+        return (int(c.value), float(u.value)) if rc == 0 else None
+    check(rc, "rska_tune_cache")
 MRHS_FORM = {"auto": 0, "staged": 1, "persistent": 2}
 
 
@@ -389,6 +421,14 @@ class MultiRHS:
     def set_option(self, what: str, value: int):
         check(lib().rska_mrhs_set_option(self._h, MRHS_OPTION[what], int(value)),
               "rska_mrhs_set_option")
+
+    def tune(self, iters: int = 64):
+        """rska_mrhs_tune: (chosen code, microseconds per iteration)."""
+        c = ctypes.c_int32()
+        u = ctypes.c_double()
+        check(lib().rska_mrhs_tune(self._h, int(iters), ctypes.byref(c), ctypes.byref(u)),
+              "rska_mrhs_tune")
+        return int(c.value), float(u.value)
 
     def query(self, what: str) -> int:
         v = ctypes.c_int64()
