@@ -889,6 +889,7 @@ def run_mrhs(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
+    form = h.query("form")   # the schedule the timed steps ran (the autotuner may have picked it)
     ms = e0.elapsed_time(e1) / args.steps
     from paper_2203_10838_gb300.shard import max_over_ranks
     ms = max_over_ranks(ms, dev)
@@ -921,6 +922,14 @@ def run_mrhs(args):
     terms = h.query("terms")
     terms_update = h.query("terms_update")
     ksplit = h.query("ksplit")
+    from paper_2203_10838_gb300.rska import decode_schedule
+    tuned_code = h.query("tuned_code")
+    schedule = {"chosen_by": "autotuner (rska_mrhs_tune, first long solve)" if tuned_code else
+                "pinned by --mrhs-form",
+                **decode_schedule(tuned_code if tuned_code else
+                                  (2 | (h.query("gather_sched") << 17) if form == 2 else
+                                   1 | (h.query("ksplit_used") << 8) | (h.query("pdl") << 16))),
+                "tuned_us_per_iter": h.query("tuned_ns") / 1000.0 if tuned_code else None}
     # end to end through the public API: H2D of A and B, setup, K iterations, D2H of X
     torch.cuda.synchronize(dev)
     c0 = time.perf_counter()
@@ -977,6 +986,7 @@ def run_mrhs(args):
                        "nnz": MR_S, "eta": MR_ETA, "t": MR_T, "lambda": MR_LAM,
                        "iters_per_step": MR_K, "terms": terms, "terms_update": terms_update,
                        "form": {1: "staged", 2: "persistent"}[form],
+                       "schedule": schedule,
                        "ksplit": ksplit if form == 1 else None,
                        "l2": "A is 256 MB (> L2); rows of A are sampled at random",
                        "parallelism": "sharded" if args.shard else "replicas"},

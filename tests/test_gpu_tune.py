@@ -82,8 +82,8 @@ def test_tuning_keeps_the_state_and_a_long_solve_tunes_itself(env):
     with rska.MultiRHS(A, B, lam, eta, t, seed, n=n) as h:
         h.solve(30)
         code, us = h.tune(16)
-        assert code in rska.tune_candidates(n, R, eta, h.device.index is None and 152 or
-                                            torch.cuda.get_device_properties(0).multi_processor_count)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert code in rska.tune_candidates(n, R, eta, sms)
         assert us > 0 and h.query("k") == 30 and h.query("tuned_code") == code
         h.solve(40)
         z = h.get_x()[1].cpu().numpy().astype(np.float64)
