@@ -101,8 +101,10 @@ __device__ __forceinline__ bool wait_phase(uint64_t* b, uint32_t parity, uint64_
   return true;
 }
 
-__device__ __forceinline__ void red_add(float* p, float v) {
-  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
 }
 
 __device__ __forceinline__ void red_release_u64(unsigned long long* p, unsigned long long v) {
@@ -365,19 +367,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         // right-hand-side slice starts at -b_tau(i) (rows beyond eta: zero);
         // its previous use (iteration i - 3) was read before every CTA passed
         // grid barrier i - 1, and grid barrier i precedes this stage
-        const int rows = (eta_p + a.n_slices - 1) / a.n_slices;
-        const int s_lo = cs * rows, s_hi = min(eta_p, s_lo + rows);
+        // (blocks of four rows of tau; a lane writes the four rows of one
+        // right-hand side as one 16-byte piece)
+        const int quads = (eta_p / 4 + a.n_slices - 1) / a.n_slices;
+        const int q_lo = cs * quads, q_hi = min(eta_p / 4, q_lo + quads);
         float* acc = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR;
-        for (int x = lane; x < (s_hi - s_lo) * (kSliceR / 4); x += 32) {
-          const int s = s_lo + x / (kSliceR / 4);
-          const int g = x % (kSliceR / 4);
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (s < a.eta) {
-            const float4 bv = __ldg(reinterpret_cast<const float4*>(
-                a.Bt + (int64_t)__ldg(tau + s) * a.R_p + (int64_t)rs * kSliceR + 4 * g));
-            v = make_float4(-bv.x, -bv.y, -bv.z, -bv.w);
+        const float* bcol = a.Bt + (int64_t)rs * kSliceR;
+        for (int x = lane; x < (q_hi - q_lo) * kSliceR; x += 32) {
+          const int q = q_lo + x / kSliceR;
+          const int r = x % kSliceR;
+          float v4[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int s = 4 * q + j;
+            v4[j] = (s < a.eta) ? -__ldg(bcol + (int64_t)__ldg(tau + s) * a.R_p + r) : 0.f;
           }
-          *reinterpret_cast<float4*>(acc + (int64_t)s * kSliceR + 4 * g) = v;
+          *reinterpret_cast<float4*>(acc + ((int64_t)q * kSliceR + r) * 4) =
+              make_float4(v4[0], v4[1], v4[2], v4[3]);
         }
       } else {
         __nv_bfloat16* G = a.G + (int64_t)(i & 1) * eta_p * a.n_p;
@@ -519,9 +525,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) w = wait_phase(&bars.res_done, (uint32_t)(i & 1), lim, &s_abort);
         bad |= !__shfl_sync(0xffffffffu, w, 0);
       }
-      // residual accumulator of this iteration and slice: rows s of 128
-      // right-hand sides, so a warp's 32 right-hand sides are one 128-byte line
-      float* resb = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR + row;
+      // residual accumulator of this iteration and slice, in blocks of four
+      // rows of tau: element (s, r) at ((s / 4) * 128 + r) * 4 + s % 4, so a
+      // thread's four consecutive s are one 16-byte piece and a warp's 32
+      // right-hand sides one 512-byte run
+      float* resb = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR + 4 * row;
       if (!bad) {
         tc_fence_after();
         for (int j = 0; j < 4; ++j) {
@@ -530,7 +538,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           float v[32];
           tmem_ld32(tl + kTmemRes + (uint32_t)col, v);
 #pragma unroll
-          for (int t = 0; t < 32; ++t) red_add(resb + (col + t) * kSliceR, v[t]);
+          for (int t = 0; t < 8; ++t)
+            red_add_v4(resb + ((col >> 2) + t) * (4 * kSliceR), v[4 * t], v[4 * t + 1],
+                       v[4 * t + 2], v[4 * t + 3]);
         }
         tc_fence_before();
       }
@@ -548,7 +558,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           float v[32];
           if (!bad) {
 #pragma unroll
-            for (int t = 0; t < 32; ++t) v[t] = __ldcg(resb + (s0 + t) * kSliceR);
+            for (int t = 0; t < 8; ++t) {
+              const float4 r4 = __ldcg(reinterpret_cast<const float4*>(
+                  resb + ((s0 >> 2) + t) * (4 * kSliceR)));
+              v[4 * t] = r4.x;
+              v[4 * t + 1] = r4.y;
+              v[4 * t + 2] = r4.z;
+              v[4 * t + 3] = r4.w;
+            }
           }
           if (!bad && u >= 2) {
             int w = 1;

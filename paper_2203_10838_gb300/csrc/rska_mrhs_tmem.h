@@ -31,7 +31,8 @@ struct MrhsTmemArgs {
   __nv_bfloat16* G;        // 2 x eta_p x n_p: dense copies of A_tau (padding zero)
   float* Zt;               // R_p x n_p: Z^T, read at the start, written at the end
   float* Res;              // 3 x r_slices x eta_p x 128 residual accumulators (per iteration
-                           // buffer and right-hand-side slice: row s, one column per right-hand side)
+                           // buffer and right-hand-side slice, blocks of four rows of tau:
+                           // element (s, r) at ((s / 4) 128 + r) 4 + s % 4)
   unsigned long long* bar; // grid barrier counter (zero at launch)
   float lambda;
   float coef;              // t / eta
