@@ -88,7 +88,8 @@ def load_peaks():
 KERNEL_SOURCES = {"mrhs_tmem_kernel": ["rska_mrhs_tmem.cu", "rska_tc.cuh", "rska_device.cuh"],
                   "rska_rows_kernel": ["rska_rows.cu", "rska_device.cuh"],
                   "rska_persistent_kernel": ["rska_solve.cu", "rska_device.cuh"],
-                  "unrolled_bwd_rows_kernel": ["rska_unrolled.cu", "rska_device.cuh"]}
+                  "unrolled_bwd_rows_kernel": ["rska_unrolled.cu", "rska_device.cuh"],
+                  "rska_batched_kernel": ["rska_batched.cu", "rska_device.cuh"]}
 
 
 def kernel_source_hash(kernel):
@@ -110,6 +111,21 @@ def committed_traffic(kernel, iters=ITERS):
     if d.get("source_hash") != kernel_source_hash(kernel) or d.get("iters_per_launch") != iters:
         return None
     return d.get("dram_bytes_per_launch")
+
+
+def committed_traffic_ratio(kernel):
+    """DRAM bytes per algorithmic byte of `kernel` from the committed ncu
+    summary of a smaller launch of the same kernel, or None when the kernel's
+    source changed since the counters were taken.  Used where the benchmark's
+    own launch is too large to capture and traffic grows in proportion to the
+    row updates processed."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash(kernel):
+        return None
+    return d.get("dram_bytes_per_algorithmic_byte")
 
 
 class ClockSampler:
@@ -329,7 +345,12 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     x_host = torch.empty(N, dtype=torch.float32).pin_memory()
     if e2e_steps:
-        parts = {"load_with_h2d_ms": 0.0, "solve_ms": 0.0, "d2h_ms": 0.0}
+        # the two host-visible parts of a step add up to it: the load call
+        # (returns once A, b and the tables are on the device) and the time
+        # from the solve call to x in pinned host memory (the asynchronous
+        # solve, then the copy); the device time of the solve is reported
+        # beside them
+        parts = {"load_with_h2d_ms": 0.0, "solve_then_d2h_ms": 0.0, "solve_device_ms": 0.0}
         inside = {"h2d_norms_w_ms": 0.0, "alias_table_ms": 0.0}
         c_first = time.perf_counter()
         s2 = Solver(A_host, b_host, LAM, ETA, T_STEP, SEED, n=N, stream=stream)
@@ -348,16 +369,16 @@ def run_gpu(args):
             load_s = time.perf_counter() - c_load
             inside["h2d_norms_w_ms"] += s2.query("setup_norms_us") / 1000.0
             inside["alias_table_ms"] += s2.query("setup_alias_us") / 1000.0
+            c_solve = time.perf_counter()
             ev[0].record(stream)
             s2.solve(ITERS)
             ev[1].record(stream)
-            c_d2h = time.perf_counter()
             xd, _ = s2.get_x()
             x_host.copy_(xd, non_blocking=True)
             torch.cuda.synchronize(dev)
             parts["load_with_h2d_ms"] += load_s * 1000.0
-            parts["solve_ms"] += ev[0].elapsed_time(ev[1])
-            parts["d2h_ms"] += (time.perf_counter() - c_d2h) * 1000.0
+            parts["solve_device_ms"] += ev[0].elapsed_time(ev[1])
+            parts["solve_then_d2h_ms"] += (time.perf_counter() - c_solve) * 1000.0
         e2e_s = (time.perf_counter() - e0) / e2e_steps
         s2.close()
         e2e = {"value": ETA * ITERS * world / e2e_s, "unit": UNIT,
@@ -587,6 +608,8 @@ def run_batched(args):
                             "batch with their own index streams"}
     hbm_peak, peak_kind = load_peaks()
     row_bytes = float((iters * BATCH_ETA * (4.0 * n + 12.0)).sum())
+    ratio = committed_traffic_ratio("rska_batched_kernel")
+    traffic = None if ratio is None else ratio * row_bytes   # this rank's launch
     achieved = row_bytes / (ms_step / 1000.0) / 1e9   # this rank's own rows
     if args.shard:
         # per-problem results of every rank (after the timed region)
@@ -668,7 +691,11 @@ def run_batched(args):
             "iterations_total": int(iters.sum()),
             "iterations_max": int(iters.max()),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "traffic_how": (None if ratio is None else
+                                         f"{ratio:.4f} DRAM bytes per algorithmic byte from an ncu "
+                                         "capture of the 256-problem launch, times this launch's "
+                                         "algorithmic bytes"),
                          "peak_kind": f"{peak_kind} (copy bandwidth)",
                          "kernel": "rska_batched_kernel",
                          "note": "row bytes of all iterations; exact residual checks not counted"},

@@ -432,8 +432,8 @@ int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_
  * once, else EUNSUPPORTED).  what = 6: terms of the scaled residual in the
  * second product (1 or 2; 0 = the same as option 0).  what = 7: gather
  * schedule of the persistent form: 0 the helper warps copy the next
- * iteration's rows of A while the residual product runs, 1 as soon as the
- * grid barrier has passed.
+ * iteration's rows of A while the residual product runs, 1 (the default)
+ * as soon as the grid barrier has passed.
  * Setting option 1, 4, 5 (non-zero) or 7 pins the schedule; otherwise the
  * first rska_mrhs_solve of at least 128 iterations picks it (rska_mrhs_tune).
  * EINVAL for an unknown `what` or value.

@@ -539,8 +539,9 @@ struct rska_mrhs {
   unsigned long long* pbar = nullptr;
   int32_t* pidx = nullptr;           // tau of one persistent launch
   int64_t pidx_cap = 0;
-  int gather_sched = 0;              // persistent form: gather with the residual product (0) or
-                                     // after the grid barrier (1)
+  int gather_sched = 1;              // persistent form: gather with the residual product (0) or
+                                     // after the grid barrier (1, the faster on the 16384 x 8192,
+                                     // R = 512, eta = 256 problem)
   // autotuner: the schedule in use comes from it while the options that
   // choose a schedule (1, 4, 5, 7) are left automatic
   bool pinned = false;               // a schedule option was set explicitly
