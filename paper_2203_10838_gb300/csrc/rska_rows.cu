@@ -101,8 +101,12 @@ __device__ __forceinline__ int consumer_sync_or(int pred) {
   return r;
 }
 
-__device__ __forceinline__ float dot4(float4 a, float4 b) {
-  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+// acc += a * b componentwise (four independent FMA chains)
+__device__ __forceinline__ void fma4(float4& acc, float4 a, float4 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.y = fmaf(a.y, b.y, acc.y);
+  acc.z = fmaf(a.z, b.z, acc.z);
+  acc.w = fmaf(a.w, b.w, acc.w);
 }
 
 __device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
@@ -280,16 +284,13 @@ __global__ void __launch_bounds__(NT, 1)
     consumer_sync();
   };
 
-  // this thread's columns t + NC r are valid for r < nvr; column t + NC tail_r
-  // is the last, partly valid float4 when 4 does not divide n
-  int nvr = 0;
-  if (n4 > tid) {
-    const int64_t q = (n4 - tid + NC - 1) / NC;
-    nvr = (q < ZREG) ? (int)q : ZREG;
-  }
-  const int tail_r = ((a.n & 3) != 0 && (n4 - 1 - tid) >= 0 && (n4 - 1 - tid) % NC == 0)
-                         ? (int)((n4 - 1 - tid) / NC)
-                         : -1;
+  // ZREG = ceil(n4 / NC), so this thread's columns t + NC r with r < ZREG - 1
+  // are always inside the row; only the last one, t + NC (ZREG - 1), may lie
+  // past it (last_ok false) or be the partly valid float4 when 4 does not
+  // divide n (last_tail)
+  const int64_t last_col = tid + (int64_t)NC * (ZREG - 1);
+  const bool last_ok = last_col < n4;
+  const bool last_tail = (a.n & 3) != 0 && last_col == n4 - 1;
   float4 av[G][ZREG];
   float bg[G], ivg[G];
   bool have_pre = false;
@@ -313,10 +314,11 @@ __global__ void __launch_bounds__(NT, 1)
         __syncwarp();
         const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
 #pragma unroll
-        for (int r = 0; r < ZREG; ++r) {
-          float4 v = (r < nvr) ? rowp[tid + NC * r] : make_float4(0.f, 0.f, 0.f, 0.f);
-          if (r == tail_r) v = mask_tail(v, tid + (int64_t)NC * r, a.n);
-          av[g][r] = v;
+        for (int r = 0; r < ZREG - 1; ++r) av[g][r] = rowp[tid + NC * r];
+        {
+          float4 v = last_ok ? rowp[last_col] : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (last_tail) v = mask_tail(v, last_col, a.n);
+          av[g][ZREG - 1] = v;
         }
         bg[g] = sb[sl];
         ivg[g] = siv[sl];
@@ -339,9 +341,10 @@ __global__ void __launch_bounds__(NT, 1)
       if (!(q0 == 0 && have_pre)) tmo = load_group(ng);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        pd[g] = 0.f;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int r = 0; r < ZREG; ++r) pd[g] += dot4(av[g][r], xr[r]);
+        for (int r = 0; r < ZREG; ++r) fma4(acc, av[g][r], xr[r]);
+        pd[g] = (acc.x + acc.y) + (acc.z + acc.w);
       }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
@@ -392,13 +395,13 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
       for (int r = 0; r < ZREG; ++r) {
         const int64_t col = tid + (int64_t)NC * r;
-        if (col < n4) {
+        if (r < ZREG - 1 || last_ok) {
           float4 zv = zsh[(size_t)r * NC + tid];
           zv.x -= dl[r].x;
           zv.y -= dl[r].y;
           zv.z -= dl[r].z;
           zv.w -= dl[r].w;
-          zv = mask_tail(zv, col, a.n);
+          if (r == ZREG - 1 && last_tail) zv = mask_tail(zv, col, a.n);
           zsh[(size_t)r * NC + tid] = zv;
           xr[r] = soft_shrink4(zv, lam);
         }
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
     for (int r = 0; r < ZREG; ++r) {
       const int64_t col = tid + (int64_t)NC * r;
-      if (rpi > 0 && col < n4) red_add_v4(dacc + col * 4, dl[r]);
+      if (rpi > 0 && (r < ZREG - 1 || last_ok)) red_add_v4(dacc + col * 4, dl[r]);
       dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     {
@@ -463,14 +466,14 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
     for (int r = 0; r < ZREG; ++r) {
       const int64_t col = tid + (int64_t)NC * r;
-      if (col < n4) {
+      if (r < ZREG - 1 || last_ok) {
         const float4 d = __ldcg(dtot + col);
         float4 zv = zsh[(size_t)r * NC + tid];
         zv.x -= d.x;
         zv.y -= d.y;
         zv.z -= d.z;
         zv.w -= d.w;
-        zv = mask_tail(zv, col, a.n);
+        if (r == ZREG - 1 && last_tail) zv = mask_tail(zv, col, a.n);
         zsh[(size_t)r * NC + tid] = zv;
         xr[r] = soft_shrink4(zv, lam);
       }
