@@ -309,9 +309,9 @@ __global__ void __launch_bounds__(NT, 1)
           sl -= slots;
           par ^= 1u;
         }
-        // one lane per warp polls; __syncwarp orders the landed row for the others
-        if (lane == 0 && !mbar_wait_bounded(&full[sl], par, a.limit_ns, nullptr)) tmo = 1;
-        __syncwarp();
+        // every lane polls (one warp-wide instruction), so each lane's own
+        // observation of the completed phase orders its reads of the row
+        if (!mbar_wait_bounded(&full[sl], par, a.limit_ns, nullptr)) tmo = 1;
         const float4* rowp = reinterpret_cast<const float4*>(ring + (size_t)sl * rowbytes_pad);
 #pragma unroll
         for (int r = 0; r < ZREG - 1; ++r) av[g][r] = rowp[tid + NC * r];
