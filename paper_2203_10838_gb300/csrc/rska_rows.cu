@@ -346,17 +346,17 @@ __global__ void __launch_bounds__(NT, 1)
         for (int r = 0; r < ZREG; ++r) fma4(acc, av[g][r], xr[r]);
         pd[g] = (acc.x + acc.y) + (acc.z + acc.w);
       }
+      // warp sums of the two rows in one butterfly: after the first exchange
+      // lanes 0-15 hold row 0's partials and lanes 16-31 row 1's, then four
+      // levels finish both; lanes 0 and 16 publish them
+      static_assert(G == 2, "the warp reduction pairs two rows");
+      float ws = (lane & 16) ? pd[1] : pd[0];
+      ws += __shfl_xor_sync(0xffffffffu, (lane & 16) ? pd[0] : pd[1], 16);
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) pd[g] += __shfl_xor_sync(0xffffffffu, pd[g], o);
-      }
+      for (int o = 8; o >= 1; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
       const int wp = gcount & 1;
       ++gcount;
-      if (lane == 0) {
-#pragma unroll
-        for (int g = 0; g < G; ++g) wpart[wp][g][warp] = pd[g];
-      }
+      if ((lane & 15) == 0) wpart[wp][lane >> 4][warp] = ws;
       if (consumer_sync_or(tmo)) {
         if (tid == 0) atomicCAS(a.status, kStatusOk, kStatusTimeout);
         bail();
