@@ -101,6 +101,13 @@ __device__ __forceinline__ int consumer_sync_or(int pred) {
   return r;
 }
 
+// S_lambda(v) as v - clamp(v, -lambda, lambda): the same value as
+// soft_shrink (up to the sign of a zero) in three instructions
+__device__ __forceinline__ float4 shrink4_clamp(float4 v, float lam) {
+  return make_float4(v.x - fminf(fmaxf(v.x, -lam), lam), v.y - fminf(fmaxf(v.y, -lam), lam),
+                     v.z - fminf(fmaxf(v.z, -lam), lam), v.w - fminf(fmaxf(v.w, -lam), lam));
+}
+
 // acc += a * b componentwise (four independent FMA chains)
 __device__ __forceinline__ void fma4(float4& acc, float4 a, float4 b) {
   acc.x = fmaf(a.x, b.x, acc.x);
@@ -403,7 +410,7 @@ __global__ void __launch_bounds__(NT, 1)
           zv.w -= dl[r].w;
           if (r == ZREG - 1 && last_tail) zv = mask_tail(zv, col, a.n);
           zsh[(size_t)r * NC + tid] = zv;
-          xr[r] = soft_shrink4(zv, lam);
+          xr[r] = shrink4_clamp(zv, lam);
         }
         dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -475,7 +482,7 @@ __global__ void __launch_bounds__(NT, 1)
         zv.w -= d.w;
         if (r == ZREG - 1 && last_tail) zv = mask_tail(zv, col, a.n);
         zsh[(size_t)r * NC + tid] = zv;
-        xr[r] = soft_shrink4(zv, lam);
+        xr[r] = shrink4_clamp(zv, lam);
       }
     }
   }
