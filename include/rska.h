@@ -181,11 +181,12 @@ int rska_destroy(rska_ctx *ctx);
 
 /*
  * rska_query -- HOST: launch facts of the solver for this context:
- *   what = 0: CTAs in the persistent grid      1: threads per CTA
+ *   what = 0: CTAs in the persistent grid of the kernel in use
+ *          1: threads per CTA
  *          2: rows of tau_k kept on chip (shared memory + registers) per
  *             iteration by the widest CTA; the rest are fetched twice
  *          3: float4 columns owned by the widest CTA
- *          4: dynamic shared memory bytes per CTA
+ *          4: dynamic shared memory bytes per CTA of the kernel in use
  *          5: row steps per thread held in registers (0 when the shared
  *             memory tile holds all of tau_k)
  *          6: solver kernel in use: 1 column-split, 2 row-split

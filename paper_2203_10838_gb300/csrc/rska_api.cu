@@ -659,11 +659,11 @@ int rska_query(rska_ctx* h, int what, int64_t* value_out) {
   if (!h || !value_out) return RSKA_EINVAL;
   const rska::SolveGeometry& g = h->c.geom;
   switch (what) {
-    case 0: *value_out = g.grid; return RSKA_OK;
+    case 0: *value_out = h->c.use_rows ? h->c.rgeom.grid : g.grid; return RSKA_OK;
     case 1: *value_out = rska::kSolveThreads; return RSKA_OK;
     case 2: *value_out = g.rows_res; return RSKA_OK;
     case 3: *value_out = g.w4max; return RSKA_OK;
-    case 4: *value_out = (int64_t)g.smem; return RSKA_OK;
+    case 4: *value_out = (int64_t)(h->c.use_rows ? h->c.rgeom.smem : g.smem); return RSKA_OK;
     case 5: *value_out = g.rreg; return RSKA_OK;
     case 6: *value_out = h->c.use_rows ? 2 : 1; return RSKA_OK;
     case 7:

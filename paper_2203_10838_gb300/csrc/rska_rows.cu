@@ -538,6 +538,13 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   int64_t P = grid_override > 0 ? grid_override
                                 : (iter_bytes <= (128 << 10) ? 1 : std::min<int64_t>(num_sms, eta));
   P = std::max<int64_t>(1, std::min<int64_t>(P, num_sms));
+  if (grid_override <= 0 && P > 1 && eta > P) {
+    // rows are reduced G at a time, and the busiest CTA sets the number of
+    // reduction rounds: the fewest CTAs that keep that number give every CTA
+    // full groups, and the exchange sums fewer partial updates
+    const int64_t rounds = ((eta + P - 1) / P + G - 1) / G;
+    P = (eta + rounds * G - 1) / (rounds * G);
+  }
   const int64_t rowbytes = n4 * 16;
   const int64_t rowbytes_pad = (rowbytes + 127) / 128 * 128;
   const size_t fixed = (size_t)z * NC * 16 + 2048;
