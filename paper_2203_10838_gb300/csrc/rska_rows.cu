@@ -449,12 +449,15 @@ __global__ void __launch_bounds__(NT, 1)
       const uint64_t t0 = global_timer_ns();
       uint32_t spins = 0;
       while (ld_acquire_u64(a.bar) < target) {
-        if (a.limit_ns == 0 || global_timer_ns() - t0 > a.limit_ns) {
+        // the clock and the status word every fourth poll (a zero limit
+        // expires at the first failed poll)
+        ++spins;
+        if (a.limit_ns == 0 || ((spins & 3u) == 0 && global_timer_ns() - t0 > a.limit_ns)) {
           atomicCAS(a.status, kStatusOk, kStatusTimeout);
           ok = 0;
           break;
         }
-        if ((++spins & 7u) == 0 && ld_relaxed_s32(a.status) != kStatusOk) {
+        if ((spins & 7u) == 0 && ld_relaxed_s32(a.status) != kStatusOk) {
           ok = 0;
           break;
         }
