@@ -128,22 +128,98 @@ def committed_traffic_ratio(kernel):
     return d.get("dram_bytes_per_algorithmic_byte")
 
 
+class _NvmlClocks:
+    """SM clock and clock-event reasons read through NVML (ctypes, read-only)
+    every millisecond on a background thread."""
+
+    SW_POWER_CAP, HW_SLOWDOWN, SW_THERMAL, HW_THERMAL, HW_POWER_BRAKE = 0x4, 0x8, 0x20, 0x40, 0x80
+
+    def __init__(self, index: int, bus_id):
+        import ctypes
+        import threading
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        rc = 1
+        if bus_id:
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus_id.encode(), ctypes.byref(self.h))
+        if rc != 0:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h))
+        if rc != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        ok = self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0
+        self.max_mhz = mx.value if ok else None
+        self.samples = []
+        self.run = True
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
+
+    def _loop(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(0), ct.c_ulonglong(0)
+        while self.run:
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0 and \
+                    self.reasons_fn(self.h, ct.byref(rs)) == 0:
+                self.samples.append((mhz.value, rs.value))
+            time.sleep(0.001)
+
+    def stop(self):
+        self.run = False
+        self.t.join(timeout=5)
+        self.lib.nvmlShutdown()
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"],
+                    "samples": 0, "source": "nvml"}
+        reasons = set()
+        names = [(self.HW_SLOWDOWN, "hw_slowdown"), (self.HW_THERMAL, "hw_thermal_slowdown"),
+                 (self.SW_THERMAL, "sw_thermal_slowdown"), (self.SW_POWER_CAP, "sw_power_cap"),
+                 (self.HW_POWER_BRAKE, "hw_power_brake_slowdown")]
+        for _, r in self.samples:
+            for bit, name in names:
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml, 1 ms"}
+
+
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """Clock and throttle sampling during the timed region: NVML every
+    millisecond when libnvidia-ml loads, else nvidia-smi every 20 ms."""
 
     def __init__(self, index: int):
+        self.nv = None
+        bus_id = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(index)
+            bus_id = "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        except Exception:
+            bus_id = None
+        try:
+            self.nv = _NvmlClocks(index, bus_id)
+            return
+        except Exception:
+            self.nv = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        sel = [f"--id={bus_id}"] if bus_id else [f"--id={index}"]
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+            self.p = subprocess.Popen(["nvidia-smi", *sel, f"--query-gpu={q}",
                                        "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
     def stop(self):
+        if self.nv is not None:
+            return self.nv.stop()
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -176,7 +252,7 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "source": "nvidia-smi, 20 ms"}
 
 
 # --------------------------------------------------------------------------
