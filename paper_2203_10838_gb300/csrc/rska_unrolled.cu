@@ -680,6 +680,11 @@ __device__ __forceinline__ WarpRows make_rows(const UnrolledArgs& a, const ProbC
 template <int NZ>
 __device__ __forceinline__ void load_row(const float4* rowp, float4 (&r)[NZ], int lane, int n4,
                                          int64_t n) {
+  if (n4 == 32 * NZ && (n & 3) == 0) {  // every lane's every column inside the row (uniform)
+#pragma unroll
+    for (int j = 0; j < NZ; ++j) r[j] = rowp[lane + 32 * j];
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < NZ; ++j) {
     const int col = lane + 32 * j;
