@@ -502,9 +502,31 @@ def run_gpu(args):
             c0 = time.perf_counter()
             iters, err = s1.solve_until(200000, 100, 1e-6, xhat=xh1)
             tt_s = time.perf_counter() - c0
+        # the roof of this configuration: A (2 MB) stays in L2, so the measured
+        # L2 read bandwidth (in-repo probe over a 16 MB buffer) bounds it
+        from paper_2203_10838_gb300.rska import rska_probe_l2_read
+        ctas = 2 * torch.cuda.get_device_properties(dev).multi_processor_count
+        pbuf = torch.ones((16 << 20) // 4, dtype=torch.float32, device=dev)
+        psink = torch.zeros(ctas, dtype=torch.float32, device=dev)
+        rska_probe_l2_read(pbuf, 2, ctas, psink, stream=stream)
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        rska_probe_l2_read(pbuf, 8, ctas, psink, stream=stream)
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        l2_gbs = ctas * 8 * pbuf.numel() * 4 / (q0.elapsed_time(q1) / 1000.0) / 1e9
+        c1_bytes = float(iters) * 10 * (4 * 500 + 12)
+        c1_gbs = c1_bytes / tt_s / 1e9
         tta = {"config": "1000x500, 25 nnz, lambda=1, eta=10, t=alpha*", "tol": 1e-6,
                "iterations": iters, "ms": tt_s * 1000.0, "rel_err": err,
-               "check_every": 100}
+               "check_every": 100,
+               "roofline": {"bound": "l2", "achieved": c1_gbs, "peak": l2_gbs, "unit": "GB/s",
+                            "frac": c1_gbs / l2_gbs,
+                            "peak_kind": "measured in this run (rska_probe_l2_read, 16 MB "
+                                         "buffer, L2-cached loads)",
+                            "note": "row bytes of the iterations over the whole time to 1e-6 "
+                                    "(FP64 checks included); latency-bound: 20 KB per iteration"}}
 
     # batch-size sweep of the same system (the eta axis of Sec. 5.2 at scale)
     sweep = None
@@ -1135,7 +1157,15 @@ def run_mrhs(args):
                                     if form == 2 else
                                     "whole iteration (gather, residual GEMM, scale, update GEMM)"),
                          "flops_per_iteration": 4.0 * MR_ETA * MR_N * MR_R,
-                         "executed_mma_flops_factor": (terms + terms_update) / 2.0},
+                         "executed_mma_flops_factor": (terms + terms_update) / 2.0,
+                         # the other roof: DRAM bytes of a launch (committed ncu
+                         # figure) over the step time, against the HBM copy peak
+                         "hbm": (None if form != 2 or committed_traffic("mrhs_tmem_kernel", MR_K) is None
+                                 else {"gbs": committed_traffic("mrhs_tmem_kernel", MR_K) / (ms / 1000.0) / 1e9,
+                                       "frac": committed_traffic("mrhs_tmem_kernel", MR_K) / (ms / 1000.0)
+                                       / 1e9 / load_peaks()[0],
+                                       "binds": "tensor pipe (Z^T stays in tensor memory; DRAM carries "
+                                                "only the sampled rows of A)"})},
             "accuracy": {"rel_residual_median": float(np.median(rr)),
                          "rel_residual_max": float(rr.max()),
                          "rel_error_median": float(np.median(re)),

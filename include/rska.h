@@ -546,6 +546,20 @@ int rska_solve_noalloc(const float *A, int64_t m, int64_t n, int64_t lda, const 
                        float *x_out, float *z_out, void *stream);
 
 /* rska_strerror -- static English text for a return code. */
+/*
+ * rska_probe_l2_read -- HOST, asynchronous on `stream`: the measurement probe
+ * of the L2 read bandwidth, the roof of a configuration whose matrix stays in
+ * L2 (Sec. 5 runs the 1000 x 500 system, 2 MB of A).  Launches `ctas` CTAs of
+ * 512 threads that each read the caller's device buffer `buf` (`bytes`, a
+ * multiple of 16, 16-byte aligned, small enough to stay in L2) `reps` times
+ * with L2-cached loads; the caller times the launch (after a warm-up launch)
+ * and divides ctas * reps * bytes by the time.  `sink` (device, `ctas`
+ * floats) is written only to keep the loads alive.  Returns RSKA_EINVAL for a
+ * bad argument, RSKA_ECUDA when the launch fails.
+ */
+int rska_probe_l2_read(const void *buf, int64_t bytes, int32_t reps, int32_t ctas, float *sink,
+                       void *stream);
+
 const char *rska_strerror(int code);
 
 #ifdef __cplusplus

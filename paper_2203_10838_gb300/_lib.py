@@ -69,6 +69,7 @@ def _declare(lib):
         "rska_mrhs_reset": ([P], c_int),
         "rska_mrhs_destroy": ([P], c_int),
         "rska_solve_noalloc": ([P, i64, i64, i64, P, f32, i32, f32, u64, i64, P, P, P], c_int),
+        "rska_probe_l2_read": ([P, i64, i32, i32, P, P], c_int),
         "rska_strerror": ([c_int], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():

@@ -226,6 +226,15 @@ def rska_solve_noalloc(A: torch.Tensor, b: torch.Tensor, lam: float, eta: int, t
     return x, z
 
 
+def rska_probe_l2_read(buf: torch.Tensor, reps: int, ctas: int, sink: torch.Tensor,
+                       stream=None):
+    """Launch the L2 read-bandwidth probe over the device tensor `buf`
+    (asynchronous on `stream`); the caller times it."""
+    check(lib().rska_probe_l2_read(_dptr(buf), buf.numel() * buf.element_size(), int(reps),
+                                   int(ctas), _dptr(sink), _stream_ptr(stream)),
+          "rska_probe_l2_read")
+
+
 class BatchSolver:
     """Many independent problems in one persistent launch (rska_batch_*).
 

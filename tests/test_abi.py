@@ -124,3 +124,19 @@ def test_mrhs_null_context_is_rejected(L):
     assert L.rska_mrhs_destroy(None) == 1
     v = ctypes.c_int64()
     assert L.rska_mrhs_query(None, 0, ctypes.byref(v)) == 1
+
+
+@pytest.mark.parametrize("args", [
+    dict(buf=None),                       # null buffer
+    dict(sink=None),                      # null sink
+    dict(nbytes=8),                       # fewer than 16 bytes
+    dict(nbytes=1000),                    # not a multiple of 16
+    dict(reps=0),
+    dict(ctas=0),
+    dict(buf=ctypes.c_void_p(0x10008)),   # not 16-byte aligned
+])
+def test_l2_probe_rejects_bad_arguments_before_launching(L, args):
+    p = dict(buf=ctypes.c_void_p(0x10000), nbytes=1 << 20, reps=1, ctas=4,
+             sink=ctypes.c_void_p(0x20000))
+    p.update(args)
+    assert L.rska_probe_l2_read(p["buf"], p["nbytes"], p["reps"], p["ctas"], p["sink"], None) == 1
