@@ -126,6 +126,54 @@ __device__ __forceinline__ float4 mask_tail(float4 v, int64_t gc, int64_t n) {
   return r;
 }
 
+// z in tensor memory.  Each consumer thread keeps its ZREG float4 columns in
+// its warp's lane quarter (warp % 4), in the column block warp / 4; the
+// loads and stores are warp-wide (every lane of the warp executes them).
+constexpr uint32_t kZCols = 128;  // allocated columns (16 ZREG <= 96 used)
+
+__device__ __forceinline__ void tm_st4(uint32_t taddr, float4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+               "r"(__float_as_uint(v.w))
+               : "memory");
+}
+
+__device__ __forceinline__ void tm_ld4(uint32_t taddr, uint32_t (&u)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3])
+               : "r"(taddr));
+}
+
+// The loaded registers are tied to the wait, so no use moves above it.
+template <int ZREG>
+__device__ __forceinline__ void tm_load_z(uint32_t tz, float4 (&z)[ZREG]) {
+  uint32_t u[ZREG][4];
+#pragma unroll
+  for (int r = 0; r < ZREG; ++r) tm_ld4(tz + 4u * r, u[r]);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int r = 0; r < ZREG; ++r) {
+    asm volatile("" : "+r"(u[r][0]), "+r"(u[r][1]), "+r"(u[r][2]), "+r"(u[r][3]));
+    z[r] = make_float4(__uint_as_float(u[r][0]), __uint_as_float(u[r][1]),
+                       __uint_as_float(u[r][2]), __uint_as_float(u[r][3]));
+  }
+}
+
+template <int ZREG>
+__device__ __forceinline__ void tm_store_z(uint32_t tz, const float4 (&z)[ZREG]) {
+#pragma unroll
+  for (int r = 0; r < ZREG; ++r) tm_st4(tz + 4u * r, z[r]);
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tm_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tm_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
 // Bounded wait on an mbarrier phase: false after limit_ns, or once *abort is
 // set (when abort is given).  The timer is read after every poll, so even a
 // limit of a microsecond is enforced.
@@ -154,6 +202,7 @@ __global__ void __launch_bounds__(NT, 1)
   __shared__ volatile int s_abort;        // consumers -> producer: stop issuing
   __shared__ volatile int s_pdone;        // producer -> consumers: no more copies
   __shared__ volatile long long s_prod;   // rows issued so far
+  __shared__ uint32_t s_tmem;
 
   if (a.stop != nullptr && ld_relaxed_s32(a.stop) != 0) return;
 
@@ -169,8 +218,7 @@ __global__ void __launch_bounds__(NT, 1)
   const uint32_t rowbytes = (uint32_t)(n4 * 16);
   const int64_t total_rows = (int64_t)rpi * a.K;
 
-  unsigned char* ring = smem;                                                     // slots x rowbytes_pad
-  float4* zsh = reinterpret_cast<float4*>(smem + (size_t)slots * rowbytes_pad);  // ZREG x NC
+  unsigned char* ring = smem;  // slots x rowbytes_pad
 
   if (tid < 2 * G * 16) (&wpart[0][0][0])[tid] = 0.f;
   if (tid == 0) {
@@ -183,7 +231,16 @@ __global__ void __launch_bounds__(NT, 1)
     s_prod = 0;
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&s_tmem)),
+                 "r"(kZCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tm_fence_before();
   __syncthreads();
+  tm_fence_after();
 
   // ------------------------------------------------------------ producer --
   if (warp == NCW) {
@@ -254,19 +311,36 @@ __global__ void __launch_bounds__(NT, 1)
   const float lam = a.lambda;
   const float coef = a.coef;
 
-  // column ownership: float4 columns t + NC*r
+  // column ownership: float4 columns t + NC*r; this thread's z in tensor
+  // memory at lane 32 (warp % 4) + lane, columns 4 ZREG (warp / 4) + 4 r
+  const uint32_t tz = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 4u * ZREG * (uint32_t)(warp >> 2);
   float4 xr[ZREG];
   float4 dl[ZREG];
+  {
+    float4 zi[ZREG];
 #pragma unroll
-  for (int r = 0; r < ZREG; ++r) {
-    const int64_t col = tid + (int64_t)NC * r;
-    float4 zv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (col < n4) zv = reinterpret_cast<const float4*>(a.z)[col];
-    zsh[(size_t)r * NC + tid] = zv;
-    xr[r] = (col < n4) ? mask_tail(soft_shrink4(zv, lam), col, a.n)
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
-    dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < ZREG; ++r) {
+      const int64_t col = tid + (int64_t)NC * r;
+      float4 zv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (col < n4) zv = reinterpret_cast<const float4*>(a.z)[col];
+      zi[r] = zv;
+      xr[r] = (col < n4) ? mask_tail(soft_shrink4(zv, lam), col, a.n)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+      dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    tm_store_z<ZREG>(tz, zi);
   }
+  // tensor memory is freed by warp 0 once every consumer is done with it
+  auto free_z = [&]() {
+    tm_fence_before();
+    consumer_sync();
+    if (warp == 0) {
+      tm_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem),
+                   "r"(kZCols)
+                   : "memory");
+    }
+  };
 
   int64_t cons = 0;  // rows consumed
   int cslot = 0;     // slot of row `cons` and the parity of its current use,
@@ -289,6 +363,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
     consumer_sync();
+    free_z();
   };
 
   // ZREG = ceil(n4 / NC), so this thread's columns t + NC r with r < ZREG - 1
@@ -399,21 +474,24 @@ __global__ void __launch_bounds__(NT, 1)
 
     // ---- exchange: Delta = sum_p Delta_p ----
     if (single) {
+      float4 zc[ZREG];
+      tm_load_z<ZREG>(tz, zc);
 #pragma unroll
       for (int r = 0; r < ZREG; ++r) {
         const int64_t col = tid + (int64_t)NC * r;
         if (r < ZREG - 1 || last_ok) {
-          float4 zv = zsh[(size_t)r * NC + tid];
+          float4 zv = zc[r];
           zv.x -= dl[r].x;
           zv.y -= dl[r].y;
           zv.z -= dl[r].z;
           zv.w -= dl[r].w;
           if (r == ZREG - 1 && last_tail) zv = mask_tail(zv, col, a.n);
-          zsh[(size_t)r * NC + tid] = zv;
+          zc[r] = zv;
           xr[r] = shrink4_clamp(zv, lam);
         }
         dl[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      tm_store_z<ZREG>(tz, zc);
       continue;
     }
     const int buf = (int)(j % 3);
@@ -473,36 +551,42 @@ __global__ void __launch_bounds__(NT, 1)
       return;
     }
     const float4* dtot = reinterpret_cast<const float4*>(dacc);
+    float4 zc[ZREG];
+    tm_load_z<ZREG>(tz, zc);
 #pragma unroll
     for (int r = 0; r < ZREG; ++r) {
       const int64_t col = tid + (int64_t)NC * r;
       if (r < ZREG - 1 || last_ok) {
         const float4 d = __ldcg(dtot + col);
-        float4 zv = zsh[(size_t)r * NC + tid];
+        float4 zv = zc[r];
         zv.x -= d.x;
         zv.y -= d.y;
         zv.z -= d.z;
         zv.w -= d.w;
         if (r == ZREG - 1 && last_tail) zv = mask_tail(zv, col, a.n);
-        zsh[(size_t)r * NC + tid] = zv;
+        zc[r] = zv;
         xr[r] = shrink4_clamp(zv, lam);
       }
     }
+    tm_store_z<ZREG>(tz, zc);
   }
 
   if (p == 0) {
+    float4 zc[ZREG];
+    tm_load_z<ZREG>(tz, zc);
     float4* zo = reinterpret_cast<float4*>(a.z);
     float4* xo = reinterpret_cast<float4*>(a.x);
 #pragma unroll
     for (int r = 0; r < ZREG; ++r) {
       const int64_t col = tid + (int64_t)NC * r;
       if (col < n4) {
-        zo[col] = zsh[(size_t)r * NC + tid];
+        zo[col] = zc[r];
         xo[col] = xr[r];
       }
     }
     if (tid == 0) *a.kdev = k0 + a.K;
   }
+  free_z();
 }
 
 template <int ZREG>
@@ -550,7 +634,7 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   }
   const int64_t rowbytes = n4 * 16;
   const int64_t rowbytes_pad = (rowbytes + 127) / 128 * 128;
-  const size_t fixed = (size_t)z * NC * 16 + 2048;
+  const size_t fixed = 2048;  // z lives in tensor memory
   if (fixed + 2 * rowbytes_pad > smem_optin) return false;
   int64_t slots = (int64_t)((smem_optin - fixed) / rowbytes_pad);
   slots = std::min<int64_t>(slots, SLOTS_MAX);
@@ -559,7 +643,7 @@ bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t sm
   g->zreg = z;
   g->slots = (int)slots;
   g->rowbytes_pad = (int)rowbytes_pad;
-  g->smem = (size_t)slots * rowbytes_pad + (size_t)z * NC * 16;
+  g->smem = (size_t)slots * rowbytes_pad;
   return true;
 }
 
