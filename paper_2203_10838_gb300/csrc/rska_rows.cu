@@ -8,8 +8,11 @@
 // update Delta_p (registers).  The only exchange per iteration is the sum of
 // the P partial updates: each CTA adds Delta_p into a global accumulator with
 // 16-byte vector reductions, passes one grid barrier, and reads the total
-// back; every CTA keeps a full copy of z = x^* (shared memory) and of
+// back; every CTA keeps a full copy of z = x^* (tensor memory, which the
+// kernel uses for nothing else, so all of shared memory is ring) and of
 // x = S_lambda(z) (registers) and applies z -= Delta, x = S_lambda(z) itself.
+// Rows are reduced two at a time; the grid is the fewest CTAs that keep the
+// busiest CTA's number of such rounds.
 //
 // Warp roles.  Warps 0..14 consume rows (each thread owns float4 columns
 // t + 480 r); warp 15 is the producer: it reads tau, b and 1/||a||^2 of the
