@@ -674,14 +674,26 @@ __global__ void __launch_bounds__(BT, 1) rska_batched_kernel(BatchArgs a) {
       int64_t iters = 0;
       double relres = -1.0;
       bool fail = false;
+      // the smallest instantiation that covers the row: columns a lane does
+      // not own still cost issue slots and lengthen the dot's chains
       if (nz <= 1)
         consume_problem<1>(a, S, smem, p, &iters, &relres, &fail);
       else if (nz <= 2)
         consume_problem<2>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 3)
+        consume_problem<3>(a, S, smem, p, &iters, &relres, &fail);
       else if (nz <= 4)
         consume_problem<4>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 6)
+        consume_problem<6>(a, S, smem, p, &iters, &relres, &fail);
       else if (nz <= 8)
         consume_problem<8>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 10)
+        consume_problem<10>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 12)
+        consume_problem<12>(a, S, smem, p, &iters, &relres, &fail);
+      else if (nz <= 14)
+        consume_problem<14>(a, S, smem, p, &iters, &relres, &fail);
       else if (nz <= 16)
         consume_problem<16>(a, S, smem, p, &iters, &relres, &fail);
       else
