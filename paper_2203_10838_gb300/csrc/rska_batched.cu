@@ -674,30 +674,27 @@ __global__ void __launch_bounds__(BT, 1) rska_batched_kernel(BatchArgs a) {
       int64_t iters = 0;
       double relres = -1.0;
       bool fail = false;
-      // the smallest instantiation that covers the row: columns a lane does
-      // not own still cost issue slots and lengthen the dot's chains
-      if (nz <= 1)
-        consume_problem<1>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 2)
-        consume_problem<2>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 3)
-        consume_problem<3>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 4)
-        consume_problem<4>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 6)
-        consume_problem<6>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 8)
-        consume_problem<8>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 10)
-        consume_problem<10>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 12)
-        consume_problem<12>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 14)
-        consume_problem<14>(a, S, smem, p, &iters, &relres, &fail);
-      else if (nz <= 16)
-        consume_problem<16>(a, S, smem, p, &iters, &relres, &fail);
-      else
-        consume_problem<BMAXNZ>(a, S, smem, p, &iters, &relres, &fail);
+      // one instantiation per width: columns a lane does not own still cost
+      // issue slots and lengthen the dot's chains
+      switch (nz) {
+        case 1: consume_problem<1>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 2: consume_problem<2>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 3: consume_problem<3>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 4: consume_problem<4>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 5: consume_problem<5>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 6: consume_problem<6>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 7: consume_problem<7>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 8: consume_problem<8>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 9: consume_problem<9>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 10: consume_problem<10>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 11: consume_problem<11>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 12: consume_problem<12>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 13: consume_problem<13>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 14: consume_problem<14>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 15: consume_problem<15>(a, S, smem, p, &iters, &relres, &fail); break;
+        case 16: consume_problem<16>(a, S, smem, p, &iters, &relres, &fail); break;
+        default: consume_problem<BMAXNZ>(a, S, smem, p, &iters, &relres, &fail); break;
+      }
       // problem finished (or failed): publish results, release the producer
       if (tid == 0) {
         S.stop = 1;
