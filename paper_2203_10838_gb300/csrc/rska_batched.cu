@@ -307,6 +307,9 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
   float4* dsh = xsh + BMAXNZ * 32;
   float4* ext = reinterpret_cast<float4*>(smem + BEXT_OFF);  // 2 x BHOLDNZ * 32 float4
   const uint32_t slot_bytes = (uint32_t)n4 * 16u;
+  // up to 16 float4 per lane a problem runs the instantiation of its own
+  // width, NZ = ceil(n4 / 32): only a lane's last column can lie past the row
+  constexpr bool kExact = NZ <= 16;
   const int RS = min(BRS_MAX, (int)(BRING_WARP / slot_bytes));  // ring slots of this warp
   unsigned char* ring = smem + BRING_OFF + (size_t)warp * BRING_WARP;
   // rows of this warp per iteration
@@ -352,7 +355,11 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
       const int col = lane + 32 * j;
-      if (col < n4) cp_async16(dst + col, src + col);
+      if (!kExact || j == NZ - 1) {
+        if (col < n4) cp_async16(dst + col, src + col);
+      } else {
+        cp_async16(dst + col, src + col);
+      }
     }
     cp_async_commit();
     ++issued;
@@ -394,9 +401,9 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
         if constexpr (kHold) rv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (col < n4) {
+        if ((kExact && j < NZ - 1) || col < n4) {
           float4 v = rowp[col];
-          if (col == n4 - 1) v = mask_tail(v, col, n);
+          if ((!kExact || j == NZ - 1) && col == n4 - 1) v = mask_tail(v, col, n);
           if constexpr (kHold) rv[j] = v;
           dp[j & 3] = fmaf(v.x, xr[j].x, dp[j & 3]);
           dp[j & 3] = fmaf(v.y, xr[j].y, dp[j & 3]);
@@ -415,7 +422,7 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
-        if (col < n4) {
+        if ((kExact && j < NZ - 1) || col < n4) {
           float4 v;
           if constexpr (kHold) {
             v = rv[j];
