@@ -451,7 +451,7 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
 #pragma unroll
       for (int j = 0; j < NZ; ++j) {
         const int col = lane + 32 * j;
-        if (col < n4) {
+        if ((kExact && j < NZ - 1) || col < n4) {
           if (warp >= 4) {
             const float4 o = dst[col];
             dst[col] = make_float4(o.x + dl[j].x, o.y + dl[j].y, o.z + dl[j].z, o.w + dl[j].w);
@@ -503,7 +503,7 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
 #pragma unroll
     for (int j = 0; j < NZ; ++j) {
       const int col = lane + 32 * j;
-      xr[j] = (col < n4) ? xsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+      xr[j] = ((kExact && j < NZ - 1) || col < n4) ? xsh[col] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const bool last = (k + 1 == kmax);
     if ((k + 1) % C != 0 && !last) continue;
