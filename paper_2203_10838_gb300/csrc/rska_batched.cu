@@ -493,7 +493,7 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
       zv.y -= dv.y;
       zv.z -= dv.z;
       zv.w -= dv.w;
-      zv = mask_tail(zv, c4, n);
+      if (c4 == n4 - 1) zv = mask_tail(zv, c4, n);
       zsh[c4] = zv;
       xsh[c4] = soft_shrink4(zv, lam);
       dsh[c4] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -538,13 +538,14 @@ __device__ void consume_problem(const BatchArgs& a, BatchShared& S, unsigned cha
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int c4 = lane + 32 * (j0 + u);
-            v[u] = (j0 + u < NZ && c4 < n4) ? __ldg(row + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (c4 == n4 - 1) v[u] = mask_tail(v[u], c4, n);
+            const bool in = (j0 + u < NZ) && ((kExact && j0 + u < NZ - 1) || c4 < n4);
+            v[u] = in ? __ldg(row + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((!kExact || j0 + u == NZ - 1) && c4 == n4 - 1) v[u] = mask_tail(v[u], c4, n);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int c4 = lane + 32 * (j0 + u);
-            if (j0 + u < NZ && c4 < n4) {
+            if ((j0 + u < NZ) && ((kExact && j0 + u < NZ - 1) || c4 < n4)) {
               const float4 xv = xsh[c4];
               dot2_acc(v[u].x, xv.x, ph, pl);
               dot2_acc(v[u].y, xv.y, ph, pl);
