@@ -433,8 +433,10 @@ int rska_mrhs_setup(rska_mrhs **out, const void *A, int64_t m, int64_t n, int64_
  * once, else EUNSUPPORTED).  what = 6: terms of the scaled residual in the
  * second product (1 or 2; 0 = the same as option 0).  what = 7: gather
  * schedule of the persistent form: 0 the helper warps copy the next
- * iteration's rows of A while the residual product runs, 1 (the default)
- * as soon as the grid barrier has passed.
+ * iteration's rows of A while the residual product runs, 1 as soon as the
+ * grid barrier has passed, 2 + k (k = 0..3) once chunk k of the scaled
+ * residual (64 rows of tau) is formed after the barrier (k is clamped to
+ * the last chunk); 0..5, default 2.
  * Setting option 1, 4, 5 (non-zero) or 7 pins the schedule; otherwise the
  * first rska_mrhs_solve of at least 128 iterations picks it (rska_mrhs_tune).
  * EINVAL for an unknown `what` or value.
@@ -473,7 +475,8 @@ int rska_mrhs_tune(rska_mrhs *h, int32_t iters, int32_t *code_out, double *us_pe
  * size eta on a GPU with num_sms SMs.  Each is a code: bits 0-1 the form
  * (1 staged kernels, 2 persistent kernel); staged: bits 8-15 the split of the
  * first product over n (0 = one wave), bit 16 programmatic dependent
- * launches; persistent: bit 17 the gather schedule.  Writes up to `max` codes
+ * launches; persistent: bits 17-19 the gather schedule (as option 7 of
+ * rska_mrhs_set_option; 0, 1 and one per 64-row chunk of eta).  Writes up to `max` codes
  * and the total count (count_out).  Errors: EINVAL.
  */
 int rska_tune_candidates(int64_t n, int64_t R, int32_t eta, int32_t num_sms, int32_t *codes_out,

@@ -539,9 +539,10 @@ struct rska_mrhs {
   unsigned long long* pbar = nullptr;
   int32_t* pidx = nullptr;           // tau of one persistent launch
   int64_t pidx_cap = 0;
-  int gather_sched = 1;              // persistent form: gather with the residual product (0) or
-                                     // after the grid barrier (1, the faster on the 16384 x 8192,
-                                     // R = 512, eta = 256 problem)
+  int gather_sched = 2;              // persistent form: gather with the residual product (0),
+                                     // right after the grid barrier (1), or once chunk k of the
+                                     // scaled residual is formed (2 + k); 2 is the fastest on the
+                                     // 16384 x 8192, R = 512, eta = 256 problem
   // autotuner: the schedule in use comes from it while the options that
   // choose a schedule (1, 4, 5, 7) are left automatic
   bool pinned = false;               // a schedule option was set explicitly
@@ -1128,7 +1129,7 @@ int rska_mrhs_set_option(rska_mrhs* h, int what, int64_t value) {
       h->nsplit_r = (int)value;
       return RSKA_OK;
     case 7:
-      if (value != 0 && value != 1) return RSKA_EINVAL;
+      if (value < 0 || value > 5) return RSKA_EINVAL;
       h->gather_sched = (int)value;
       h->pinned = true;
       return RSKA_OK;

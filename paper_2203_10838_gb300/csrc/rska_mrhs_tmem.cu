@@ -62,6 +62,17 @@ constexpr uint32_t kRingSlot = 32768;  // one ring slot: high part (16 KB) + low
 constexpr uint32_t kStage = 16384;     // gather staging buffer: one row piece of 8192 BF16
 constexpr uint32_t kTmemCols = 512;    // Z^T in columns 0..255, the residual product from 256
 constexpr uint32_t kTmemRes = 256;
+// Register split: the block is launched with kLaunchRegs per thread (the
+// count ptxas gives under the launch bounds; the launch refuses a build with
+// any other count, since the epilogue's increase would then wait for
+// registers that nobody releases).  Warps 0-3 hand registers back and the
+// two epilogue warpgroups take them: 4 x 32 x kLowRegs + 8 x 32 x kHighRegs
+// is exactly the launch's total, and the epilogue runs without spills.
+constexpr int kLaunchRegs = 168;
+constexpr int kLowRegs = 88;
+constexpr int kHighRegs = 208;
+static_assert(128 * kLowRegs + 256 * kHighRegs == kThreads * kLaunchRegs,
+              "the register split must add up to the launch's registers");
 
 // kind::f16 instruction descriptor: D FP32, A and B BF16, M = 128, N = n;
 // b_mn: B read MN-major.
@@ -188,6 +199,7 @@ struct alignas(8) Bars {
   uint64_t gathered;    // both helper warps finished the next iteration's gather
   uint64_t fin;         // every MMA of this CTA complete (exit drain)
   uint64_t stage;       // gather staging buffer filled (bulk copy)
+  uint64_t rchunk;      // the eight epilogue warps formed chunk kq of R' (one phase per iteration)
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -215,6 +227,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int rs = blockIdx.x / a.n_slices;
   const int cs = blockIdx.x % a.n_slices;
   const int rchunks = eta_p / 64;                        // scaled-residual chunks
+  // gather schedules 2.. start the next gather once chunk kq of the scaled
+  // residual is formed (its reads of the accumulator have landed)
+  const int kq = a.gather_sched >= 2 ? min(a.gather_sched - 2, rchunks - 1) : -1;
   const int cnt = a.cnt;
 
   if (tid == 0) {
@@ -229,6 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mb_init(&bars.gathered, 2);
     mb_init(&bars.fin, 1);
     mb_init(&bars.stage, 1);
+    mb_init(&bars.rchunk, kEpiWarps);
     s_abort = 0;
     s_flag = 1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -249,6 +265,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     s_abort = 1;
   };
 
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kLowRegs));
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kHighRegs));
+  }
   if (warp == 0) {
     // ------------------------------------------------ TMA producer --------
     int issued = 0;  // iterations whose A_tau slice was requested
@@ -427,12 +448,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       // iteration i - 1): schedule 1 starts the gather then; schedule 0 waits
       // for this CTA's update of iteration i - 1 (which follows that
       // barrier), so the gather runs with iteration i's residual product,
-      // while the tensor pipe, not memory, is busy
+      // while the tensor pipe, not memory, is busy; schedules 2.. wait until
+      // chunk kq of iteration i - 1's scaled residual is formed, so the
+      // first reads of the reduced residual do not share the memory system
+      // with the gather (the epilogue cannot complete the next phase of
+      // rchunk before this gather ends: that phase follows grid barrier
+      // i + 1, which waits for it)
       int ok = 1;
-      if (lane == 0)
-        ok = (i == 0 || a.gather_sched == 1)
-                 ? wait_phase(&bars.passed, (uint32_t)(i & 1), a.limit_ns, &s_abort)
-                 : wait_phase(&bars.upd_done, (uint32_t)((i - 1) & 1), a.limit_ns, &s_abort);
+      if (lane == 0) {
+        if (i == 0 || a.gather_sched == 1) {
+          ok = wait_phase(&bars.passed, (uint32_t)(i & 1), a.limit_ns, &s_abort);
+        } else if (a.gather_sched == 0) {
+          ok = wait_phase(&bars.upd_done, (uint32_t)((i - 1) & 1), a.limit_ns, &s_abort);
+        } else {
+          ok = wait_phase(&bars.passed, (uint32_t)(i & 1), a.limit_ns, &s_abort) &&
+               wait_phase(&bars.rchunk, (uint32_t)((i - 1) & 1), a.limit_ns, &s_abort);
+        }
+      }
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       stage(i + 1);
@@ -530,11 +562,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       // thread's four consecutive s are one 16-byte piece and a warp's 32
       // right-hand sides one 512-byte run
       float* resb = a.Res + ((int64_t)(i % 3) * a.r_slices + rs) * eta_p * kSliceR + 4 * row;
+      // The 32 CTAs of a slice add into the same lines; each starts at the
+      // 32-column group given by its column slice, so at any moment about a
+      // quarter of them target one line (reductions to one line serialize
+      // in L2; the read-back below keeps one order, as reads of a line by
+      // many SMs at once are served together).
       if (!bad) {
         tc_fence_after();
         for (int j = 0; j < 4; ++j) {
-          const int col = 128 * half + 32 * j;
-          if (col >= eta_p) break;
+          const int col = 128 * half + 32 * ((j + cs) & 3);
+          if (col >= eta_p) continue;
           float v[32];
           tmem_ld32(tl + kTmemRes + (uint32_t)col, v);
 #pragma unroll
@@ -579,7 +616,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             store_split_row(rsl, rsl + 16384, row, half, v, a.nsplit_r == 2);
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) mb_arrive(&bars.full[slot]);
+            if (lane == 0) {
+              mb_arrive(&bars.full[slot]);
+              if (qq == kq) mb_arrive(&bars.rchunk);
+            }
           }
           ++u;
         }
@@ -646,7 +686,11 @@ bool mrhs_tmem_fits(int64_t n_p, int64_t R_p, int64_t eta_p, int num_sms) {
 
 cudaError_t launch_mrhs_tmem(const CUtensorMap& mapG, const MrhsTmemArgs& a, cudaStream_t s) {
   const size_t smem = mrhs_tmem_smem(a.eta_p);
-  cudaError_t e = cudaFuncSetAttribute(mrhs_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncAttributes fa = {};
+  cudaError_t e = cudaFuncGetAttributes(&fa, mrhs_tmem_kernel);
+  if (e != cudaSuccess) return e;
+  if (fa.numRegs != kLaunchRegs) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(mrhs_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

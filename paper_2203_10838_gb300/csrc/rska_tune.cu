@@ -30,9 +30,11 @@ int tune_candidates(int64_t n_p, int64_t R_p, int64_t eta_p64, int num_sms, bool
     if (ks > 0 && ks > kblocks) continue;
     for (int pdl = 1; pdl >= 0; --pdl) add(tune_code(kFormStaged, ks, pdl, 0));
   }
-  // persistent: both gather schedules
+  // persistent: the gather schedules (with the residual product, right
+  // after the grid barrier, or after chunk k of the scaled residual, for
+  // each of its eta_p64 / 64 chunks)
   if (persistent_ok && mrhs_tmem_fits(n_p, R_p, eta_p64, num_sms))
-    for (int g = 0; g <= 1; ++g) add(tune_code(kFormPersistent, 0, 0, g));
+    for (int g = 0; g < 2 + eta_p64 / 64; ++g) add(tune_code(kFormPersistent, 0, 0, g));
   return cnt;
 }
 

@@ -9,8 +9,9 @@ namespace rska {
 
 // A candidate schedule as one int32: bits 0-1 the form (1 staged kernels, 2
 // persistent kernel); staged: bits 8-15 the split of the first product over n
-// (0 = one wave), bit 16 programmatic dependent launches; persistent: bit 17
-// the gather schedule (0 with the residual product, 1 after the barrier).
+// (0 = one wave), bit 16 programmatic dependent launches; persistent: bits
+// 17-19 the gather schedule (0 with the residual product, 1 right after the
+// grid barrier, 2 + k after chunk k of the scaled residual is formed).
 constexpr int32_t kFormStaged = 1;
 constexpr int32_t kFormPersistent = 2;
 
@@ -20,7 +21,7 @@ inline int32_t tune_code(int form, int ksplit, int pdl, int gsched) {
 inline int tune_form(int32_t c) { return c & 3; }
 inline int tune_ksplit(int32_t c) { return (c >> 8) & 0xff; }
 inline int tune_pdl(int32_t c) { return (c >> 16) & 1; }
-inline int tune_gsched(int32_t c) { return (c >> 17) & 1; }
+inline int tune_gsched(int32_t c) { return (c >> 17) & 7; }
 
 // Candidates for a problem with n_p (multiple of 256), R_p (multiple of
 // 256), eta_p64 (eta rounded up to 64) on num_sms SMs; persistent_ok says

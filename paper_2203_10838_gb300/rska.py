@@ -328,7 +328,7 @@ def decode_schedule(code: int) -> dict:
     """A schedule code of rska_mrhs_tune / rska_tune_candidates as a dict."""
     form = code & 3
     if form == 2:
-        return {"form": "persistent", "gather_sched": (code >> 17) & 1}
+        return {"form": "persistent", "gather_sched": (code >> 17) & 7}
     return {"form": "staged", "ksplit": (code >> 8) & 0xff, "pdl": (code >> 16) & 1}
 
 

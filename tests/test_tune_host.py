@@ -17,14 +17,16 @@ def rska():
 def test_candidates_of_the_benchmark_configuration(rska):
     # 16384 x 8192, 512 right-hand sides, eta = 256 on 152 SMs: the staged form
     # with four splits x programmatic launch on/off, and the persistent form
-    # (32 column slices x 4 right-hand-side slices = 128 CTAs) with both
+    # (32 column slices x 4 right-hand-side slices = 128 CTAs) with six
     # gather schedules
     codes = rska.tune_candidates(8192, 512, 256, 152)
-    assert len(codes) == len(set(codes)) == 10
+    assert len(codes) == len(set(codes)) == 14
     dec = [rska.decode_schedule(c) for c in codes]
     staged = {(d["ksplit"], d["pdl"]) for d in dec if d["form"] == "staged"}
     assert staged == {(k, p) for k in (0, 16, 32, 64) for p in (0, 1)}
-    assert {d["gather_sched"] for d in dec if d["form"] == "persistent"} == {0, 1}
+    # with the residual product, after the barrier, after each of the
+    # scaled residual's four 64-row chunks
+    assert {d["gather_sched"] for d in dec if d["form"] == "persistent"} == {0, 1, 2, 3, 4, 5}
 
 
 def test_candidates_respect_each_form_s_limits(rska):
@@ -37,7 +39,8 @@ def test_candidates_respect_each_form_s_limits(rska):
     # n = 300 (8 blocks of 64 columns): splits above 8 are left out
     dec = [rska.decode_schedule(c) for c in rska.tune_candidates(300, 40, 100, 152)]
     assert {d.get("ksplit") for d in dec if d["form"] == "staged"} == {0}
-    assert sum(d["form"] == "persistent" for d in dec) == 2
+    # eta = 100 pads to two 64-row chunks: gather schedules 0, 1, 2 and 3
+    assert sorted(d["gather_sched"] for d in dec if d["form"] == "persistent") == [0, 1, 2, 3]
     # every candidate fits in the table that rska_mrhs_tune uses
     for n, R, eta in [(8192, 512, 256), (1, 1, 1), (100000, 4096, 4096)]:
         assert 1 <= len(rska.tune_candidates(n, R, eta, 152)) <= 32
