@@ -502,6 +502,8 @@ def run_gpu(args):
             c0 = time.perf_counter()
             iters, err = s1.solve_until(200000, 100, 1e-6, xhat=xh1)
             tt_s = time.perf_counter() - c0
+            tta_kernel = {1: "rska_persistent_kernel", 2: "rska_rows_kernel",
+                          3: "rska_small_kernel"}[s1.query("kernel")]
         # the roof of this configuration: A (2 MB) stays in L2, so the measured
         # L2 read bandwidth (in-repo probe over a 16 MB buffer) bounds it
         from paper_2203_10838_gb300.rska import rska_probe_l2_read
@@ -520,7 +522,7 @@ def run_gpu(args):
         c1_gbs = c1_bytes / tt_s / 1e9
         tta = {"config": "1000x500, 25 nnz, lambda=1, eta=10, t=alpha*", "tol": 1e-6,
                "iterations": iters, "ms": tt_s * 1000.0, "rel_err": err,
-               "check_every": 100,
+               "check_every": 100, "kernel": tta_kernel,
                "roofline": {"bound": "l2", "achieved": c1_gbs, "peak": l2_gbs, "unit": "GB/s",
                             "frac": c1_gbs / l2_gbs,
                             "peak_kind": "measured in this run (rska_probe_l2_read, 16 MB "

@@ -189,7 +189,8 @@ int rska_destroy(rska_ctx *ctx);
  *          4: dynamic shared memory bytes per CTA of the kernel in use
  *          5: row steps per thread held in registers (0 when the shared
  *             memory tile holds all of tau_k)
- *          6: solver kernel in use: 1 column-split, 2 row-split
+ *          6: solver kernel in use: 1 column-split, 2 row-split, 3 one-CTA
+ *             small-system kernel
  *          7: microseconds the last setup spent allocating device memory
  *             (host clock; 0 after rska_load_host)
  *          8: microseconds of the copy (host buffers only), FP64 row norms
@@ -207,10 +208,16 @@ int rska_query(rska_ctx *ctx, int what, int64_t *value_out);
  *             (default 2,000,000; 0: a wait that is not satisfied at its first
  *             poll expires, which exercises the failure path)
  *          2: solver kernel: 0 automatic (row-split when n <= 11520, else
- *             column-split), 1 column-split, 2 row-split
+ *             column-split; the one-CTA small-system kernel where the
+ *             row-split plan is a single CTA and it fits), 1 column-split,
+ *             2 row-split, 3 one-CTA small-system kernel (n <= 1024,
+ *             eta <= 256, one iteration of rows in shared memory; else
+ *             EUNSUPPORTED)
  * The row-split kernel gives each CTA whole rows of tau_k (TMA bulk copies)
  * and exchanges one n-vector per iteration; the column-split kernel gives
- * each CTA a slice of every row and exchanges eta dots per iteration.
+ * each CTA a slice of every row and exchanges eta dots per iteration; the
+ * small-system kernel runs on one CTA, gives each row of tau_k to one warp
+ * and keeps D iterations of rows in flight.
  */
 int rska_set_option(rska_ctx *ctx, int what, int64_t value);
 

@@ -93,20 +93,33 @@ int plan(Ctx* c) {
       rska::plan_solve(c->n, c->eta, c->num_sms, c->grid_override, (size_t)optin, &c->geom);
   const bool rows_ok =
       rska::plan_rows(c->n, c->eta, c->num_sms, c->grid_override, (size_t)optin, &c->rgeom);
+  const bool small_ok = rska::plan_small(c->n, c->eta, (size_t)optin, &c->sgeom);
+  c->use_small = false;
   if (c->kernel_choice == 1) {
     if (!col_ok) return RSKA_EUNSUPPORTED;
     c->use_rows = false;
   } else if (c->kernel_choice == 2) {
     if (!rows_ok) return RSKA_EUNSUPPORTED;
     c->use_rows = true;
+  } else if (c->kernel_choice == 3) {
+    if (!small_ok) return RSKA_EUNSUPPORTED;
+    c->use_rows = false;
+    c->use_small = true;
   } else {
     if (!col_ok && !rows_ok) return RSKA_EUNSUPPORTED;
     c->use_rows = rows_ok;
+    // where the row-split plan is a single CTA, the one-CTA kernel that
+    // gives each row to one warp is the faster form
+    if (rows_ok && c->rgeom.grid == 1 && small_ok) {
+      c->use_rows = false;
+      c->use_small = true;
+    }
   }
   return RSKA_OK;
 }
 
 cudaError_t launch_any(Ctx* c, const rska::SolveArgs& a) {
+  if (c->use_small) return rska::launch_small(a, c->sgeom, c->stream);
   return c->use_rows ? rska::launch_rows(a, c->rgeom, c->stream)
                      : rska::launch_solve(a, c->geom, c->stream);
 }
@@ -659,13 +672,16 @@ int rska_query(rska_ctx* h, int what, int64_t* value_out) {
   if (!h || !value_out) return RSKA_EINVAL;
   const rska::SolveGeometry& g = h->c.geom;
   switch (what) {
-    case 0: *value_out = h->c.use_rows ? h->c.rgeom.grid : g.grid; return RSKA_OK;
+    case 0: *value_out = h->c.use_small ? 1 : h->c.use_rows ? h->c.rgeom.grid : g.grid; return RSKA_OK;
     case 1: *value_out = rska::kSolveThreads; return RSKA_OK;
     case 2: *value_out = g.rows_res; return RSKA_OK;
     case 3: *value_out = g.w4max; return RSKA_OK;
-    case 4: *value_out = (int64_t)(h->c.use_rows ? h->c.rgeom.smem : g.smem); return RSKA_OK;
+    case 4:
+      *value_out = (int64_t)(h->c.use_small ? h->c.sgeom.smem
+                                            : h->c.use_rows ? h->c.rgeom.smem : g.smem);
+      return RSKA_OK;
     case 5: *value_out = g.rreg; return RSKA_OK;
-    case 6: *value_out = h->c.use_rows ? 2 : 1; return RSKA_OK;
+    case 6: *value_out = h->c.use_small ? 3 : h->c.use_rows ? 2 : 1; return RSKA_OK;
     case 7:
     case 8:
     case 9:
@@ -694,7 +710,7 @@ int rska_set_option(rska_ctx* h, int what, int64_t value) {
       c->limit_ns = (uint64_t)value * 1000ull;
       return RSKA_OK;
     case 2: {
-      if (value < 0 || value > 2) return RSKA_EINVAL;
+      if (value < 0 || value > 3) return RSKA_EINVAL;
       const int old = c->kernel_choice;
       c->kernel_choice = (int)value;
       int rc = plan(c);

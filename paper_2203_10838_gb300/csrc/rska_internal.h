@@ -17,6 +17,9 @@ constexpr int64_t kPresampleDraws = 1 << 21;  // draws pre-sampled per launch (a
 constexpr int kUnrolledMaxZ = 4;        // unrolled-gradient kernels: float4 columns per thread (n <= 4096)
 constexpr int kBatchMaxZ = 3;           // batched kernel: float4 columns per consumer thread (n <= 2688)
 constexpr int kRowsMaxZ = 6;            // row-split kernel: float4 columns per consumer thread (n <= 11520)
+constexpr int kSmallMaxNZ = 8;          // one-CTA small-system kernel: float4 columns per lane (n <= 1024)
+constexpr int kSmallMaxEta = 256;       // ... rows per iteration
+constexpr int kSmallMaxSlots = 8;       // ... iterations in its shared-memory ring
 
 // Launch geometry of the persistent single-system solver.
 struct SolveGeometry {
@@ -35,6 +38,13 @@ struct RowsGeometry {
   int slots = 0;         // shared-memory row slots of the TMA ring
   int rowbytes_pad = 0;  // bytes per slot
   size_t smem = 0;
+};
+
+// Launch geometry of the one-CTA small-system solver.
+struct SmallGeometry {
+  int slots = 0;         // iteration slots of the ring (1..kSmallMaxSlots)
+  int nz = 0;            // float4 columns per lane (ceil(n4 / 32))
+  size_t smem = 0;       // dynamic shared memory
 };
 
 struct SolveArgs {
@@ -111,8 +121,10 @@ struct Ctx {
   uint64_t limit_ns = 2000000000ull;
   SolveGeometry geom;
   RowsGeometry rgeom;
-  int kernel_choice = 0;       // 0 automatic, 1 column-split, 2 row-split
+  SmallGeometry sgeom;
+  int kernel_choice = 0;       // 0 automatic, 1 column-split, 2 row-split, 3 one-CTA small
   bool use_rows = false;
+  bool use_small = false;
 };
 
 // launchers (return cudaError_t of the launch)
@@ -144,6 +156,10 @@ cudaError_t launch_presample(const SolveArgs& a, cudaStream_t s);
 bool plan_rows(int64_t n, int32_t eta, int num_sms, int grid_override, size_t smem_optin,
                RowsGeometry* g);
 cudaError_t launch_rows(const SolveArgs& a, const RowsGeometry& g, cudaStream_t s);
+// The small-system kernel: n <= 1024, eta <= 256, one iteration of rows in
+// shared memory at least; pre-sampled indices (tstride != 0) only.
+bool plan_small(int64_t n, int32_t eta, size_t smem_optin, SmallGeometry* g);
+cudaError_t launch_small(const SolveArgs& a, const SmallGeometry& g, cudaStream_t s);
 cudaError_t launch_metrics(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
                            const float* z, float lambda, const float* xhat, double* acc,
                            const int* stop, cudaStream_t s);

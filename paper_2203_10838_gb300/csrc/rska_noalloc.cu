@@ -109,8 +109,12 @@ extern "C" int rska_solve_noalloc(const float* A, int64_t m, int64_t n, int64_t 
     return RSKA_ECUDA;
   rska::RowsGeometry rg;
   rska::SolveGeometry cg;
+  rska::SmallGeometry sg;
   const bool use_rows = rska::plan_rows(n, eta, sms, 0, (size_t)optin, &rg);
   if (!use_rows && !rska::plan_solve(n, eta, sms, 0, (size_t)optin, &cg)) return RSKA_EUNSUPPORTED;
+  // the same automatic choice as a context: the one-CTA kernel where the
+  // row-split plan is a single CTA
+  const bool use_small = use_rows && rg.grid == 1 && rska::plan_small(n, eta, (size_t)optin, &sg);
 
   double* nu = reinterpret_cast<double*>(base + L.nu);
   float* inv_nu = reinterpret_cast<float*>(base + L.inv_nu);
@@ -165,7 +169,9 @@ extern "C" int rska_solve_noalloc(const float* A, int64_t m, int64_t n, int64_t 
   a.limit_ns = 2000000000ull;
   for (int64_t done = 0; done < K && e == cudaSuccess; done += L.chunk) {
     a.K = (K - done < L.chunk) ? (K - done) : L.chunk;
-    e = use_rows ? rska::launch_rows(a, rg, s) : rska::launch_solve(a, cg, s);
+    e = use_small ? rska::launch_small(a, sg, s)
+        : use_rows  ? rska::launch_rows(a, rg, s)
+                    : rska::launch_solve(a, cg, s);
   }
   if (e == cudaSuccess && x_out)
     e = cudaMemcpyAsync(x_out, x, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);

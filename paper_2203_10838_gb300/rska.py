@@ -16,7 +16,7 @@ QUERY = {"grid": 0, "threads": 1, "rows_resident": 2, "w4max": 3, "smem": 4, "rr
          "kernel": 6, "setup_alloc_us": 7, "setup_norms_us": 8, "setup_alias_us": 9,
          "setup_total_us": 10}
 OPTION = {"grid": 0, "watchdog_us": 1, "kernel": 2}
-KERNEL = {"auto": 0, "column": 1, "rows": 2}
+KERNEL = {"auto": 0, "column": 1, "rows": 2, "small": 3}
 
 
 def _stream_ptr(stream) -> ctypes.c_void_p:

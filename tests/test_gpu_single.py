@@ -89,22 +89,65 @@ CASES = {
     # a grid larger than eta: the row-split kernel has CTAs that own no rows
     # and only take part in the exchange
     "idle_ctas_grid8_eta3": (200, 300, 8, 3, 0.5, 2.0, 11, 100, 8, 0.0),
+    # one iteration's rows are 128 KB: the small-system kernel's ring holds a
+    # single iteration (the next rows are fetched after the current one)
+    "one_slot_ring_eta64": (1000, 500, 25, 64, 1.0, 8.0, 12, 200, None, 0.0),
 }
 
 
 ROWS_OK = {k for k, v in CASES.items() if v[1] <= 10240}
+# the one-CTA small-system kernel: n <= 1024 and eta <= 256 (every such case
+# here also fits one iteration of rows in shared memory)
+SMALL_OK = {k for k, v in CASES.items() if v[1] <= 1024 and v[3] <= 256}
+KERNEL_ID = {"column": 1, "rows": 2, "small": 3}
 
 
-@pytest.mark.parametrize("kernel", ["column", "rows"])
+@pytest.mark.parametrize("kernel", ["column", "rows", "small"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_parity_against_oracle(env, name, kernel):
     if kernel == "rows" and name not in ROWS_OK:
         pytest.skip("row-split kernel covers n <= 10240")
+    if kernel == "small" and name not in SMALL_OK:
+        pytest.skip("the small-system kernel covers n <= 1024, eta <= 256")
     m, n, s, eta, lam, t, seed, K, grid, noise = CASES[name]
     rx, rz, info = run_case(env, m, n, s, eta, lam, t, seed, K, grid=grid, noise=noise,
                             kernel=kernel)
-    assert info["kernel"] == (2 if kernel == "rows" else 1)
+    assert info["kernel"] == KERNEL_ID[kernel]
     assert rx <= REL_TOL and rz <= REL_TOL, (name, rx, rz, info)
+
+
+@pytest.mark.parametrize("name,expected", [("c1_full", 3), ("single_column", 3),
+                                           ("one_slot_ring_eta64", 3),
+                                           ("wide_n_many_ctas", 2)])
+def test_automatic_choice_of_the_small_system_kernel(env, name, expected):
+    """Where the row-split plan is a single CTA (one iteration's rows at most
+    128 KB) and the system fits, the automatic choice is the one-CTA kernel
+    that gives each row to one warp; larger systems keep the row-split grid."""
+    m, n, s, eta, lam, t, seed, K, grid, noise = CASES[name]
+    rx, rz, info = run_case(env, m, n, s, eta, lam, t, seed, min(K, 300), grid=grid,
+                            noise=noise)
+    assert info["kernel"] == expected, info
+    assert rx <= REL_TOL and rz <= REL_TOL, (name, rx, rz, info)
+
+
+def test_small_system_kernel_resumes_across_calls(env):
+    """Three solves of 700, 1 and 1299 iterations continue one index stream
+    and one iterate (the device iteration counter and z carry over): the
+    same result as the oracle's 2000 iterations."""
+    torch, orc, Solver = env
+    m, n, s, eta, lam, t, seed = 1000, 500, 25, 10, 1.0, 1.0, 4
+    prob = gaussian_problem(m, n, s, seed=1234)
+    with Solver(torch.from_numpy(prob.A).cuda(), torch.from_numpy(prob.b).cuda(), lam, eta, t,
+                seed, n=n) as sol:
+        for K in (700, 1, 1299):
+            sol.solve(K)
+        assert sol.query("kernel") == 3
+        x, z = [v.cpu().numpy().astype(np.float64) for v in sol.get_x()]
+    nu = orc.row_norms(prob.A)
+    thr, alias = orc.alias_build(nu)
+    tau = orc.sample(thr, alias, seed=seed, eta=eta, k0=0, K=2000)
+    zr = orc.rska_fixed(prob.A, prob.b.astype(np.float64), lam, t, eta, tau, nu=nu)
+    assert rel(z, zr) <= REL_TOL and rel(x, orc.soft_shrink(zr, lam)) <= REL_TOL
 
 
 @pytest.mark.parametrize("n,kernel_expected", [(11520, 2), (11521, 1)])

@@ -43,6 +43,55 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
+def test_small_system_kernel_wait_limit_runs_out_and_context_recovers(env):
+    """The one-CTA small-system kernel has no grid barrier; its waits are the
+    ring's: the consumers' wait for a slot's rows and the producer's wait for
+    a released slot, each probed once without blocking before it spins.
+    With a zero limit the first wait whose phase is not complete at that
+    probe runs out (the consumers reach their first wait while the first
+    rows are still being fetched; and whichever side is faster waits for the
+    other within a few iterations), the kernel records ETIMEOUT, drains the
+    copies it issued and returns; after rska_reset the context solves as the
+    oracle does.  The expiry depends on timing, so up to five launches of
+    2000 iterations are given to show it."""
+    torch, orc = env
+    from paper_2203_10838_gb300._lib import RSKAError
+    from paper_2203_10838_gb300.rska import KERNEL, Solver
+    m, n, s, eta, lam, t, seed, K = 1000, 500, 25, 10, 1.0, 1.0, 3, 300
+    prob = gaussian_problem(m, n, s, seed=901)
+    A = torch.from_numpy(prob.A).cuda()
+    b = torch.from_numpy(prob.b).cuda()
+    with Solver(A, b, lam, eta, t, seed, n=n) as sol:
+        sol.set_option("kernel", KERNEL["small"])
+        sol.set_option("watchdog_us", 0)
+        code = None
+        for _ in range(5):
+            sol.solve(2000)
+            try:
+                sol.get_x()
+            except RSKAError as e:
+                code = e.code
+                break
+            sol.reset()
+        assert code == ETIMEOUT
+        with pytest.raises(RSKAError) as ei:
+            sol.solve(1)
+        assert ei.value.code == ETIMEOUT
+        sol.reset()
+        sol.set_option("watchdog_us", DEFAULT_LIMIT_US)
+        sol.solve(K)
+        x, z = [v.cpu().numpy().astype(np.float64) for v in sol.get_x()]
+        idx = sol.get_indices(0, K).cpu().numpy()
+        assert sol.query("kernel") == KERNEL["small"]
+    nu = orc.row_norms(prob.A)
+    thr, alias = orc.alias_build(nu)
+    tau = orc.sample(thr, alias, seed=seed, eta=eta, k0=0, K=K)
+    np.testing.assert_array_equal(idx, tau)
+    zr = orc.rska_fixed(prob.A, prob.b.astype(np.float64), lam, t, eta, tau, nu=nu)
+    assert rel(z, zr) <= 1e-4
+    assert rel(x, orc.soft_shrink(zr, lam)) <= 1e-4
+
+
 @pytest.mark.parametrize("kernel", ["rows", "column"])
 def test_single_system_wait_limit_runs_out_and_context_recovers(env, kernel):
     torch, orc = env

@@ -70,6 +70,15 @@ def run_weighted(env, m, n, s, eta, lam, t, seed, K, couple, kernel, grid=None, 
     return rel(x, xr), rel(z, zr), used
 
 
+@pytest.mark.parametrize("couple", [False, True])
+def test_weighted_parity_small_system_kernel(env, couple):
+    # 600 x 250 (the last float4 of a row is partly valid), eta = 12, on the
+    # one-CTA kernel: the weights reach it through the per-row scale
+    rx, rz, used = run_weighted(env, 600, 250, 10, 12, 0.5, 1.0, 3, 300, couple, "small")
+    assert used == 3
+    assert rx <= REL_TOL and rz <= REL_TOL, (couple, rx, rz)
+
+
 @pytest.mark.parametrize("kernel", ["rows", "column"])
 @pytest.mark.parametrize("couple", [False, True])
 def test_weighted_parity(env, couple, kernel):
