@@ -128,8 +128,10 @@ int rska_solve(rska_ctx *ctx, int64_t K);
  * chunk compute in FP64 either the relative error ||x - xhat|| / ||xhat|| (xhat
  * given, device, n floats) or the relative residual ||Ax - b|| / ||b|| (xhat
  * NULL), and stop once it is <= tol or max_iters iterations have run.  All
- * chunks are enqueued at once; a device flag makes the chunks after the stop
- * return immediately.  Synchronizes.  iters_out (HOST, nullable) receives the
+ * chunks are enqueued in growing waves; a device flag makes the chunks after
+ * the stop return immediately (with the one-CTA small-system kernel and xhat
+ * given, the test runs at the end of each chunk's own launch).  Synchronizes.
+ * iters_out (HOST, nullable) receives the
  * iterations actually run by this call; metric_out (HOST, nullable) the last
  * measured value.
  */

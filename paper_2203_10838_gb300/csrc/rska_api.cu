@@ -386,6 +386,10 @@ int rska_solve_until(rska_ctx* h, int64_t max_iters, int64_t check_every, double
   int64_t* k_stop = reinterpret_cast<int64_t*>(c->macc + 6);
   if (e == cudaSuccess) e = cudaMemsetAsync(k_stop, 0xff, sizeof(int64_t), s);
   const int64_t step = (check_every < c->chunk) ? check_every : c->chunk;
+  // The one-CTA small-system kernel runs the test against xhat at the end of
+  // its own launch (one launch per chunk); otherwise each chunk is followed
+  // by the metrics pass over A and the test.
+  const bool fused = c->use_small && xhat != nullptr;
   // Enqueue chunk + check pairs in waves; between waves read the stop flag,
   // so a run that stops early does not pay for enqueueing the whole budget.
   int64_t done = 0;
@@ -395,11 +399,17 @@ int rska_solve_until(rska_ctx* h, int64_t max_iters, int64_t check_every, double
     for (int64_t w = 0; w < wave && done < max_iters && e == cudaSuccess; ++w) {
       const int64_t K = (max_iters - done < step) ? (max_iters - done) : step;
       rska::SolveArgs a = solve_args(c, K, c->stop);
+      if (fused) {
+        a.xhat = xhat;
+        a.macc = c->macc;
+        a.k_stop = k_stop;
+        a.tol = tol;
+      }
       e = launch_any(c, a);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && !fused)
         e = rska::launch_metrics(c->A, c->m, c->n, c->lda, c->b, c->z, c->lambda, xhat, c->macc,
                                  c->stop, s);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && !fused)
         e = rska::launch_metrics_finish(c->macc, xhat != nullptr, tol, c->stop, k_stop, c->kdev,
                                         s);
       done += K;

@@ -75,6 +75,14 @@ struct SolveArgs {
                                // only, no pre-sampling)
   int64_t K;
   uint64_t limit_ns;
+  // one-CTA small-system kernel only: the stopping test of rska_solve_until
+  // run at the end of the launch when xhat is given (relative error of
+  // x = S_lambda(z) to xhat in FP64 into macc[2], macc[3], macc[5]; at or
+  // below tol it sets *stop and k_stop = the iteration count)
+  const float* xhat = nullptr;
+  double* macc = nullptr;
+  int64_t* k_stop = nullptr;
+  double tol = -1.0;
 };
 
 struct Ctx {

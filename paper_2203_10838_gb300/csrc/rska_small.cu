@@ -9,7 +9,8 @@
 // pair of rows.  Here a row belongs to one warp:
 //
 //  - The producer warp copies all eta rows of iteration j (one bulk copy per
-//    row), with b and 1/||a||^2 at tau_j, into slot j mod D of a ring of D
+//    row; tau_j, b and 1/||a||^2 at tau_j from the pre-sampled arrays, read
+//    two iterations ahead) into slot j mod D of a ring of D
 //    iteration slots as soon as the consumers have released that slot, so
 //    up to D iterations are in flight (D = 1 when only one fits: the rows
 //    of the next iteration are then fetched after this one is done).
@@ -24,7 +25,9 @@
 //    goes back to the producer.
 //
 // Two barriers per iteration and none per row; no exchange through global
-// memory and no grid barrier.  Every wait is bounded.
+// memory and no grid barrier.  Given xhat, the launch ends with the stopping
+// test of rska_solve_until (relative error of x to xhat, FP64), so a chunk
+// of a run to a tolerance is one launch.  Every wait is bounded.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
   __shared__ volatile int s_abort;      // consumers -> producer: stop issuing
   __shared__ volatile int s_pdone;      // producer -> consumers: no more copies
   __shared__ volatile long long s_prod; // iterations whose copies were issued
+  __shared__ double s_red[2 * kSmCW];   // per-warp sums of the stopping test
 
   if (a.stop != nullptr && ld_relaxed_s32(a.stop) != 0) return;
 
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
     // z -= sum_s c_s a_s for this thread's column, in draw order
     if (owner) {
       float4 dz = zero4;
+#pragma unroll 4
       for (int s = 0; s < eta; ++s) {
         float4 v = slot[(size_t)s * n4 + tid];
         if (own_tail) v = sm_tail(v, tid, a.n);
@@ -312,11 +317,55 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
     xr[NZ - 1] = last_ok ? xs[lastc] : zero4;
   }
 
+  const float4 xo = sm_shrink(zo, lam);
   if (owner) {
     reinterpret_cast<float4*>(a.z)[tid] = zo;
-    reinterpret_cast<float4*>(a.x)[tid] = sm_shrink(zo, lam);
+    reinterpret_cast<float4*>(a.x)[tid] = xo;
   }
   if (tid == 0) *a.kdev = k0 + a.K;
+  if (a.xhat != nullptr) {
+    // the stopping test: ||x - xhat|| / ||xhat|| in FP64, summed per warp
+    // and then over the warps in a fixed order
+    double ee = 0.0, hh = 0.0;
+    if (owner) {
+      const float xv[4] = {xo.x, xo.y, xo.z, xo.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t e = 4 * (int64_t)tid + c;
+        if (e < a.n) {
+          const double h = (double)__ldg(a.xhat + e);
+          const double d = (double)xv[c] - h;
+          ee = fma(d, d, ee);
+          hh = fma(h, h, hh);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      ee += __shfl_xor_sync(0xffffffffu, ee, o);
+      hh += __shfl_xor_sync(0xffffffffu, hh, o);
+    }
+    if (lane == 0) {
+      s_red[2 * warp] = ee;
+      s_red[2 * warp + 1] = hh;
+    }
+    csync();
+    if (tid == 0) {
+      double se = 0.0, sh = 0.0;
+      for (int w = 0; w < kSmCW; ++w) {
+        se += s_red[2 * w];
+        sh += s_red[2 * w + 1];
+      }
+      const double err = sqrt(se) / (sh > 0.0 ? sqrt(sh) : 1e-30);
+      a.macc[2] = se;
+      a.macc[3] = sh;
+      a.macc[5] = err;
+      if (a.stop != nullptr && a.tol >= 0.0 && err <= a.tol) {
+        *const_cast<int*>(a.stop) = 1;
+        if (a.k_stop != nullptr) *a.k_stop = k0 + a.K;
+      }
+    }
+  }
 }
 
 template <int NZ>
@@ -349,6 +398,7 @@ bool plan_small(int64_t n, int32_t eta, size_t smem_optin, SmallGeometry* g) {
 
 cudaError_t launch_small(const SolveArgs& a, const SmallGeometry& g, cudaStream_t s) {
   if (a.tstride == 0) return cudaErrorInvalidValue;  // pre-sampled indices only
+  if (a.xhat != nullptr && a.macc == nullptr) return cudaErrorInvalidValue;
   cudaError_t e = launch_presample(a, s);
   if (e != cudaSuccess) return e;
   switch (g.nz) {

@@ -226,6 +226,11 @@ def test_solve_until_reaches_tolerance(env):
         iters, err = sol.solve_until(200000, 100, 1e-6, xhat=xh)
         _, z = sol.get_x()
         assert sol.iteration == iters
+        # the small-system kernel runs this test inside its launch; the
+        # separate metrics pass gives the same error for the final iterate
+        assert sol.query("kernel") == 3
+        _, re_api = sol.metrics(xh)
+        assert abs(err - re_api) <= 1e-12 * re_api
     assert iters % 100 == 0 and 0 < iters < 200000
     assert err <= 1e-6
     _, re_o = orc.metrics(prob.A[:, :n], prob.b.astype(np.float64),
