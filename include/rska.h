@@ -130,7 +130,9 @@ int rska_solve(rska_ctx *ctx, int64_t K);
  * NULL), and stop once it is <= tol or max_iters iterations have run.  All
  * chunks are enqueued in growing waves; a device flag makes the chunks after
  * the stop return immediately (with the one-CTA small-system kernel and xhat
- * given, the test runs at the end of each chunk's own launch).  Synchronizes.
+ * given, the kernel runs the test itself every check_every iterations and
+ * ends its launch at the first test that passes; one launch then covers up
+ * to 16 checks).  Synchronizes.
  * iters_out (HOST, nullable) receives the
  * iterations actually run by this call; metric_out (HOST, nullable) the last
  * measured value.

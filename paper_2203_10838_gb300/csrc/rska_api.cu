@@ -386,10 +386,13 @@ int rska_solve_until(rska_ctx* h, int64_t max_iters, int64_t check_every, double
   int64_t* k_stop = reinterpret_cast<int64_t*>(c->macc + 6);
   if (e == cudaSuccess) e = cudaMemsetAsync(k_stop, 0xff, sizeof(int64_t), s);
   const int64_t step = (check_every < c->chunk) ? check_every : c->chunk;
-  // The one-CTA small-system kernel runs the test against xhat at the end of
-  // its own launch (one launch per chunk); otherwise each chunk is followed
-  // by the metrics pass over A and the test.
+  // The one-CTA small-system kernel runs the test against xhat itself every
+  // `step` iterations and ends its launch at the first test that passes, so
+  // one launch covers up to 16 checked chunks; otherwise each chunk is
+  // followed by the metrics pass over A and the test.
   const bool fused = c->use_small && xhat != nullptr;
+  const int64_t per_launch =
+      fused ? step * std::max<int64_t>(1, std::min<int64_t>(16, c->chunk / step)) : step;
   // Enqueue chunk + check pairs in waves; between waves read the stop flag,
   // so a run that stops early does not pay for enqueueing the whole budget.
   int64_t done = 0;
@@ -397,13 +400,14 @@ int rska_solve_until(rska_ctx* h, int64_t max_iters, int64_t check_every, double
   int stopped = 0;
   while (e == cudaSuccess && done < max_iters && !stopped) {
     for (int64_t w = 0; w < wave && done < max_iters && e == cudaSuccess; ++w) {
-      const int64_t K = (max_iters - done < step) ? (max_iters - done) : step;
+      const int64_t K = (max_iters - done < per_launch) ? (max_iters - done) : per_launch;
       rska::SolveArgs a = solve_args(c, K, c->stop);
       if (fused) {
         a.xhat = xhat;
         a.macc = c->macc;
         a.k_stop = k_stop;
         a.tol = tol;
+        a.check_every = step;
       }
       e = launch_any(c, a);
       if (e == cudaSuccess && !fused)

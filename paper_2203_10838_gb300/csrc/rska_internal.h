@@ -76,13 +76,16 @@ struct SolveArgs {
   int64_t K;
   uint64_t limit_ns;
   // one-CTA small-system kernel only: the stopping test of rska_solve_until
-  // run at the end of the launch when xhat is given (relative error of
-  // x = S_lambda(z) to xhat in FP64 into macc[2], macc[3], macc[5]; at or
-  // below tol it sets *stop and k_stop = the iteration count)
+  // run inside the launch when xhat is given, every check_every iterations
+  // (0: only after the last) and after the last (relative error of
+  // x = S_lambda(z) to xhat in FP64 into macc[2], macc[3], macc[5]); at or
+  // below tol it sets *stop and k_stop = the iteration count and the launch
+  // ends there (the device iteration counter then counts the iterations run)
   const float* xhat = nullptr;
   double* macc = nullptr;
   int64_t* k_stop = nullptr;
   double tol = -1.0;
+  int64_t check_every = 0;
 };
 
 struct Ctx {

@@ -25,9 +25,11 @@
 //    goes back to the producer.
 //
 // Two barriers per iteration and none per row; no exchange through global
-// memory and no grid barrier.  Given xhat, the launch ends with the stopping
-// test of rska_solve_until (relative error of x to xhat, FP64), so a chunk
-// of a run to a tolerance is one launch.  Every wait is bounded.
+// memory and no grid barrier.  Given xhat, the launch runs the stopping test
+// of rska_solve_until itself (relative error of x to xhat, FP64) every
+// check_every iterations and after its last one, and ends at the first test
+// that passes, so a run to a tolerance takes a few launches.  Every wait is
+// bounded.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -263,6 +265,49 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
     csync();
   };
 
+  // The stopping test: ||x - xhat|| / ||xhat|| in FP64 for the current x;
+  // per-warp sums, then every consumer thread adds the warps' sums in one
+  // fixed order, so all of them take the same decision.
+  auto rel_err = [&]() -> double {
+    double ee = 0.0, hh = 0.0;
+    if (owner) {
+      const float4 xo = sm_shrink(zo, lam);
+      const float xv[4] = {xo.x, xo.y, xo.z, xo.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t e = 4 * (int64_t)tid + c;
+        if (e < a.n) {
+          const double h = (double)__ldg(a.xhat + e);
+          const double d = (double)xv[c] - h;
+          ee = fma(d, d, ee);
+          hh = fma(h, h, hh);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      ee += __shfl_xor_sync(0xffffffffu, ee, o);
+      hh += __shfl_xor_sync(0xffffffffu, hh, o);
+    }
+    csync();  // the previous test's sums have been read
+    if (lane == 0) {
+      s_red[2 * warp] = ee;
+      s_red[2 * warp + 1] = hh;
+    }
+    csync();
+    double se = 0.0, sh = 0.0;
+    for (int w = 0; w < kSmCW; ++w) {
+      se += s_red[2 * w];
+      sh += s_red[2 * w + 1];
+    }
+    if (tid == 0) {
+      a.macc[2] = se;
+      a.macc[3] = sh;
+    }
+    return sqrt(se) / (sh > 0.0 ? sqrt(sh) : 1e-30);
+  };
+
+  int64_t kend = a.K;  // iterations run by this launch
   for (int64_t j = 0; j < a.K; ++j) {
     const int sl = (int)(j % slots);
     const uint32_t par = (uint32_t)((j / slots) & 1);
@@ -315,57 +360,30 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
 #pragma unroll
     for (int i = 0; i < NZ - 1; ++i) xr[i] = xs[lane + 32 * i];
     xr[NZ - 1] = last_ok ? xs[lastc] : zero4;
+    // given xhat: the test every check_every iterations and after the last
+    const int64_t done = j + 1;
+    if (a.xhat != nullptr &&
+        ((a.check_every > 0 && done % a.check_every == 0) || done == a.K)) {
+      const double err = rel_err();
+      if (tid == 0) a.macc[5] = err;
+      if (a.stop != nullptr && a.tol >= 0.0 && err <= a.tol) {
+        if (tid == 0) {
+          *const_cast<int*>(a.stop) = 1;
+          if (a.k_stop != nullptr) *a.k_stop = k0 + done;
+        }
+        kend = done;
+        break;
+      }
+    }
   }
+  if (kend < a.K) bail(kend);  // stopped early: the producer stops, its copies land
 
   const float4 xo = sm_shrink(zo, lam);
   if (owner) {
     reinterpret_cast<float4*>(a.z)[tid] = zo;
     reinterpret_cast<float4*>(a.x)[tid] = xo;
   }
-  if (tid == 0) *a.kdev = k0 + a.K;
-  if (a.xhat != nullptr) {
-    // the stopping test: ||x - xhat|| / ||xhat|| in FP64, summed per warp
-    // and then over the warps in a fixed order
-    double ee = 0.0, hh = 0.0;
-    if (owner) {
-      const float xv[4] = {xo.x, xo.y, xo.z, xo.w};
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int64_t e = 4 * (int64_t)tid + c;
-        if (e < a.n) {
-          const double h = (double)__ldg(a.xhat + e);
-          const double d = (double)xv[c] - h;
-          ee = fma(d, d, ee);
-          hh = fma(h, h, hh);
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      ee += __shfl_xor_sync(0xffffffffu, ee, o);
-      hh += __shfl_xor_sync(0xffffffffu, hh, o);
-    }
-    if (lane == 0) {
-      s_red[2 * warp] = ee;
-      s_red[2 * warp + 1] = hh;
-    }
-    csync();
-    if (tid == 0) {
-      double se = 0.0, sh = 0.0;
-      for (int w = 0; w < kSmCW; ++w) {
-        se += s_red[2 * w];
-        sh += s_red[2 * w + 1];
-      }
-      const double err = sqrt(se) / (sh > 0.0 ? sqrt(sh) : 1e-30);
-      a.macc[2] = se;
-      a.macc[3] = sh;
-      a.macc[5] = err;
-      if (a.stop != nullptr && a.tol >= 0.0 && err <= a.tol) {
-        *const_cast<int*>(a.stop) = 1;
-        if (a.k_stop != nullptr) *a.k_stop = k0 + a.K;
-      }
-    }
-  }
+  if (tid == 0) *a.kdev = k0 + kend;
 }
 
 template <int NZ>
