@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
   __shared__ volatile int s_abort;      // consumers -> producer: stop issuing
   __shared__ volatile int s_pdone;      // producer -> consumers: no more copies
   __shared__ volatile long long s_prod; // iterations whose copies were issued
-  __shared__ double s_red[2 * kSmCW];   // per-warp sums of the stopping test
+  __shared__ double s_red[2 * kSmCW];   // per-warp sums of the stopping test (owner warps)
 
   if (a.stop != nullptr && ld_relaxed_s32(a.stop) != 0) return;
 
@@ -265,46 +265,58 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
     csync();
   };
 
-  // The stopping test: ||x - xhat|| / ||xhat|| in FP64 for the current x;
-  // per-warp sums, then every consumer thread adds the warps' sums in one
-  // fixed order, so all of them take the same decision.
-  auto rel_err = [&]() -> double {
-    double ee = 0.0, hh = 0.0;
-    if (owner) {
-      const float4 xo = sm_shrink(zo, lam);
-      const float xv[4] = {xo.x, xo.y, xo.z, xo.w};
+  // The stopping test: ||x - xhat|| / ||xhat|| in FP64 for the current x.
+  // The warps that own columns reduce their sums by shuffles; thread 0 adds
+  // the warps' sums in a fixed order, records the error and decides, and an
+  // OR-reducing barrier hands the decision to every consumer (FP64 is slow
+  // on this GPU, so no thread repeats the others' work).  Returns 1 to stop.
+  const int own_warps = (n4 + 31) / 32;
+  auto stop_test = [&](int64_t done) -> int {
+    if (warp < own_warps) {
+      double ee = 0.0, hh = 0.0;
+      if (owner) {
+        const float4 xo = sm_shrink(zo, lam);
+        const float xv[4] = {xo.x, xo.y, xo.z, xo.w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int64_t e = 4 * (int64_t)tid + c;
-        if (e < a.n) {
-          const double h = (double)__ldg(a.xhat + e);
-          const double d = (double)xv[c] - h;
-          ee = fma(d, d, ee);
-          hh = fma(h, h, hh);
+        for (int c = 0; c < 4; ++c) {
+          const int64_t e = 4 * (int64_t)tid + c;
+          if (e < a.n) {
+            const double h = (double)__ldg(a.xhat + e);
+            const double d = (double)xv[c] - h;
+            ee = fma(d, d, ee);
+            hh = fma(h, h, hh);
+          }
         }
       }
-    }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      ee += __shfl_xor_sync(0xffffffffu, ee, o);
-      hh += __shfl_xor_sync(0xffffffffu, hh, o);
-    }
-    csync();  // the previous test's sums have been read
-    if (lane == 0) {
-      s_red[2 * warp] = ee;
-      s_red[2 * warp + 1] = hh;
+      for (int o = 16; o >= 1; o >>= 1) {
+        ee += __shfl_xor_sync(0xffffffffu, ee, o);
+        hh += __shfl_xor_sync(0xffffffffu, hh, o);
+      }
+      if (lane == 0) {
+        s_red[2 * warp] = ee;
+        s_red[2 * warp + 1] = hh;
+      }
     }
     csync();
-    double se = 0.0, sh = 0.0;
-    for (int w = 0; w < kSmCW; ++w) {
-      se += s_red[2 * w];
-      sh += s_red[2 * w + 1];
-    }
+    int stop_now = 0;
     if (tid == 0) {
+      double se = 0.0, sh = 0.0;
+      for (int w = 0; w < own_warps; ++w) {
+        se += s_red[2 * w];
+        sh += s_red[2 * w + 1];
+      }
+      const double err = sqrt(se) / (sh > 0.0 ? sqrt(sh) : 1e-30);
       a.macc[2] = se;
       a.macc[3] = sh;
+      a.macc[5] = err;
+      if (a.stop != nullptr && a.tol >= 0.0 && err <= a.tol) {
+        *const_cast<int*>(a.stop) = 1;
+        if (a.k_stop != nullptr) *a.k_stop = k0 + done;
+        stop_now = 1;
+      }
     }
-    return sqrt(se) / (sh > 0.0 ? sqrt(sh) : 1e-30);
+    return csync_or(stop_now);
   };
 
   int64_t kend = a.K;  // iterations run by this launch
@@ -364,13 +376,7 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
     const int64_t done = j + 1;
     if (a.xhat != nullptr &&
         ((a.check_every > 0 && done % a.check_every == 0) || done == a.K)) {
-      const double err = rel_err();
-      if (tid == 0) a.macc[5] = err;
-      if (a.stop != nullptr && a.tol >= 0.0 && err <= a.tol) {
-        if (tid == 0) {
-          *const_cast<int*>(a.stop) = 1;
-          if (a.k_stop != nullptr) *a.k_stop = k0 + done;
-        }
+      if (stop_test(done)) {
         kend = done;
         break;
       }
