@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(kSmT, 1) rska_small_kernel(SolveArgs a, int sl
   }
   float4 zo = owner ? zin[tid] : zero4;
 
-  // error exit: stop the producer, let every copy it issued land, leave
+  // early end (a wait that ran out, or the stopping test passed): stop the
+  // producer and let every copy it issued land before the CTA may end
   auto bail = [&](int64_t cons) {
     if (tid == 0) {
       s_abort = 1;
