@@ -92,6 +92,10 @@ CASES = {
     # one iteration's rows are 128 KB: the small-system kernel's ring holds a
     # single iteration (the next rows are fetched after the current one)
     "one_slot_ring_eta64": (1000, 500, 25, 64, 1.0, 8.0, 12, 200, None, 0.0),
+    # the small-system kernel's limits: eta = 256 (eight rows per producer lane)
+    # and n = 1024 (eight float4 columns per lane)
+    "small_eta_max": (2000, 64, 8, 256, 0.5, 16.0, 13, 100, None, 0.0),
+    "small_width_max": (500, 1024, 20, 20, 1.0, 4.0, 14, 200, None, 0.01),
 }
 
 
