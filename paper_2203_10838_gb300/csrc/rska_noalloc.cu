@@ -8,7 +8,6 @@
 // cudaMalloc, and code that must not synchronize the device the way
 // cudaMalloc/cudaFree may.  The array below is reserved on every GPU that
 // loads this library and stays reserved until the process exits.
-#include <cstring>
 #include <mutex>
 
 #include "rska_internal.h"
@@ -140,8 +139,7 @@ extern "C" int rska_solve_noalloc(const float* A, int64_t m, int64_t n, int64_t 
   if (e != cudaSuccess) return RSKA_ECUDA;
   if (st != 0) return st;
 
-  rska::SolveArgs a;
-  std::memset(&a, 0, sizeof(a));
+  rska::SolveArgs a{};  // every field zero or its default
   a.A = A;
   a.lda = lda;
   a.m = m;
